@@ -1,0 +1,170 @@
+"""FP64 CPU oracle for the split-step Crank-Nicolson GP solver.
+
+TEST INFRASTRUCTURE ONLY: the checker that the CUDA path is compared against.
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference leg import this package.  It shares no code with the CUDA library;
+the C source (``sscn_ref.c``) states the discretisation of every step.
+
+Arrays are numpy complex128, C-contiguous, shape (nz, ny, nx) (x fastest).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Params", "lib", "coord", "seed", "step", "nonlinear", "sweep",
+           "norm", "observables", "energy_parts", "sums", "thomas_tables",
+           "thomas_solve", "set_threads", "get_threads"]
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``ref_params`` in sscn_ref.c."""
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("hx", ctypes.c_double), ("hy", ctypes.c_double),
+                ("hz", ctypes.c_double), ("dt", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("nu", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("g", ctypes.c_double)]
+
+    @classmethod
+    def make(cls, shape, h, dt, gamma, nu, lam, g, mode):
+        """shape = (nx, ny, nz); h = (hx, hy, hz); mode 0 imaginary, 1 real."""
+        nx, ny, nz = shape
+        hx, hy, hz = h
+        return cls(nx, ny, nz, mode, hx, hy, hz, dt, gamma, nu, lam, g)
+
+    @property
+    def shape3(self):
+        return (self.nz, self.ny, self.nx)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER(Params)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "ref_set_threads": (None, [ctypes.c_int]),
+            "ref_get_threads": (ctypes.c_int, []),
+            "ref_coord": (dbl, [i32, dbl, i32]),
+            "ref_thomas_tables": (None, [i32, dbl, dbl, vp, vp]),
+            "ref_thomas_solve": (None, [i32, dbl, dbl, vp, vp, vp]),
+            "ref_nonlinear": (None, [P, vp]),
+            "ref_sweep": (None, [P, i32, vp]),
+            "ref_norm": (dbl, [P, vp]),
+            "ref_scale": (None, [P, vp, dbl]),
+            "ref_step": (None, [P, vp, i64]),
+            "ref_seed": (None, [P, vp]),
+            "ref_sums": (None, [P, vp, vp]),
+            "ref_energy_parts": (None, [P, vp, vp]),
+            "ref_observables": (None, [P, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(p, psi):
+    if psi.dtype != np.complex128 or not psi.flags.c_contiguous:
+        raise TypeError("psi must be C-contiguous complex128")
+    if psi.shape != p.shape3:
+        raise ValueError("psi shape %s != (nz, ny, nx) %s" % (psi.shape, p.shape3))
+
+
+def set_threads(n):
+    lib().ref_set_threads(int(n))
+
+
+def get_threads():
+    return lib().ref_get_threads()
+
+
+def coord(n, h, i):
+    return lib().ref_coord(n, h, i)
+
+
+def seed(p):
+    psi = np.zeros(p.shape3, np.complex128)
+    lib().ref_seed(ctypes.byref(p), _ptr(psi))
+    return psi
+
+
+def step(p, psi, n):
+    """n SSCN steps in place."""
+    _check(p, psi)
+    lib().ref_step(ctypes.byref(p), _ptr(psi), int(n))
+    return psi
+
+
+def nonlinear(p, psi):
+    _check(p, psi)
+    lib().ref_nonlinear(ctypes.byref(p), _ptr(psi))
+    return psi
+
+
+def sweep(p, axis, psi):
+    _check(p, psi)
+    lib().ref_sweep(ctypes.byref(p), int(axis), _ptr(psi))
+    return psi
+
+
+def norm(p, psi):
+    _check(p, psi)
+    return lib().ref_norm(ctypes.byref(p), _ptr(psi))
+
+
+def sums(p, psi):
+    _check(p, psi)
+    out = np.zeros(9)
+    lib().ref_sums(ctypes.byref(p), _ptr(psi), _ptr(out))
+    return out
+
+
+def energy_parts(p, psi):
+    """(E_kin, E_pot, E_int) per particle."""
+    _check(p, psi)
+    out = np.zeros(3)
+    lib().ref_energy_parts(ctypes.byref(p), _ptr(psi), _ptr(out))
+    return out
+
+
+OBS_NAMES = ("norm", "mu", "energy", "rms_x", "rms_y", "rms_z", "rms_r")
+
+
+def observables(p, psi):
+    """dict with norm, mu, energy, rms_x, rms_y, rms_z, rms_r."""
+    _check(p, psi)
+    out = np.zeros(7)
+    lib().ref_observables(ctypes.byref(p), _ptr(psi), _ptr(out))
+    return dict(zip(OBS_NAMES, out.tolist()))
+
+
+def thomas_tables(m, kappa):
+    cp = np.zeros(m, np.complex128)
+    mu = np.zeros(m, np.complex128)
+    lib().ref_thomas_tables(m, kappa.real, kappa.imag, _ptr(cp), _ptr(mu))
+    return cp, mu
+
+
+def thomas_solve(kappa, b):
+    """Solve (I - kappa L) u = b, L = tridiag(1, -2, 1), zero ends."""
+    b = np.ascontiguousarray(b, np.complex128)
+    m = b.shape[0]
+    u = np.zeros(m, np.complex128)
+    work = np.zeros(2 * m, np.complex128)
+    lib().ref_thomas_solve(m, kappa.real, kappa.imag, _ptr(b), _ptr(u), _ptr(work))
+    return u
