@@ -1,0 +1,161 @@
+/*
+ * gp.h -- C ABI of libgp, a GB300 (sm_103a) implementation of the split-step
+ * Crank-Nicolson (SSCN) propagation of the time-dependent Gross-Pitaevskii
+ * equation in a fully anisotropic harmonic trap,
+ *
+ *     i dpsi/dt = [ -lap/2 + (gamma^2 x^2 + nu^2 y^2 + lambda^2 z^2)/2 + g|psi|^2 ] psi,
+ *
+ * in real time and in imaginary time (t = -i tau), in 3D and in 2D (nz == 1).
+ *
+ * The paper (program summaries v, vi, xiv, xv and "Summary of revisions") names
+ * the per-step functions this library implements: calcnu (the pointwise
+ * potential and nonlinearity step), calclux / calcluy / calcluz (the
+ * Crank-Nicolson sweeps along x, y, z), calcnorm (normalisation), calcmuen and
+ * calcrms (chemical potential, energy, rms sizes).  Discretisation:
+ *
+ *   grid    axis k keeps n_k stored points x_i = -n_k h_k / 2 + i h_k,
+ *           i = 0 .. n_k - 1; point 0 is a zero Dirichlet node and a virtual
+ *           zero node sits at i = n_k (unknowns i = 1 .. n_k - 1).  In 2D
+ *           (nz == 1) z = 0 and there is no z sweep.
+ *   step    psi <- exp(-tau (V + g|psi|^2)) psi, then on every x, y, z line
+ *           (I - kappa L) u = (I + kappa L) psi with L = tridiag(1, -2, 1),
+ *           kappa = dt / (4 h_k^2) (imaginary time, tau = dt) or
+ *           i dt / (4 h_k^2) (real time, tau = i dt); imaginary time then
+ *           renormalises psi to N = 1.
+ *   obs     N = W sum |psi|^2 (W = h_x h_y h_z, h_x h_y in 2D);
+ *           E = W [ sum_k K_k / (2 h_k^2) + sum V|psi|^2 + g/2 sum |psi|^4 ] / N,
+ *           mu likewise with g sum |psi|^4, K_k the sum of squared forward
+ *           differences along axis k over i = 0 .. n_k - 1; rms_k =
+ *           sqrt(sum x_k^2 |psi|^2 / sum |psi|^2).
+ *
+ * Memory layout of psi: psi[(k * ny + j) * nx + i], x fastest, complex numbers
+ * stored as interleaved (re, im): complex128 (2 x double) for GP_C128,
+ * complex64 (2 x float) for GP_C64.  Reductions always accumulate in FP64.
+ *
+ * Conventions: every int-returning call returns GP_OK (0) or a negative GP_E*
+ * code and never throws; gp_last_error() gives a message for the last failure
+ * on that context.  A context owns its device memory (psi, coefficient tables,
+ * reduction partials and sweep scratch), allocated in gp_create and released
+ * in gp_destroy.  Host buffers passed in stay owned by the caller and are not
+ * retained after the call returns.  One context must not be used from two
+ * host threads at once; distinct contexts are independent.  Work is enqueued
+ * on the context's CUDA stream; errors raised by the device surface at the
+ * next synchronising call (gp_observables, gp_store, gp_sync).
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gp_ctx gp_ctx;
+
+/* Stored points per axis; nz == 1 selects 2D.  Each of nx, ny must be >= 3,
+ * nz == 1 or >= 3, and nx, ny, nz <= GP_MAX_EDGE. */
+typedef struct {
+    int32_t nx, ny, nz;
+} gp_grid;
+
+#define GP_MAX_EDGE 8192
+
+enum { GP_IMAG = 0, GP_REAL = 1 };           /* propagation mode            */
+enum { GP_C128 = 0, GP_C64 = 1 };            /* psi / sweep precision       */
+
+enum {
+    GP_OK = 0,
+    GP_EINVAL = -1,        /* bad argument: shape, spacing, dt, mode, count  */
+    GP_ENOMEM = -2,        /* device or pinned host allocation failed        */
+    GP_ECUDA = -3,         /* a CUDA runtime call failed                     */
+    GP_ENONFINITE = -4,    /* norm or an observable came out NaN / Inf       */
+    GP_ETIMEOUT = -5,      /* a bounded device wait gave up                  */
+    GP_EINTERNAL = -6      /* internal invariant violated                    */
+};
+
+/* Observables of the current state (calcnorm, calcmuen, calcrms). */
+typedef struct {
+    double norm, mu, energy, rms_x, rms_y, rms_z, rms_r;
+    int64_t step;          /* SSCN steps taken since the last gp_load        */
+    double t;              /* step * dt                                      */
+} gp_obs;
+
+/*
+ * Create a context for one grid.  dx[3] = (h_x, h_y, h_z), all > 0 (h_z is
+ * ignored in 2D); dt > 0; gamma, nu, lambda >= 0 are the trap frequencies; g
+ * is the nonlinearity (any sign); mode GP_IMAG or GP_REAL; precision GP_C128
+ * or GP_C64.  cuda_stream is a cudaStream_t to enqueue on, or NULL for a
+ * stream the context creates and owns.  psi starts as zero; call gp_load.
+ * On failure *out is set to NULL.
+ */
+int gp_create(const gp_grid *grid, const double dx[3], double dt,
+              double gamma, double nu, double lambda, double g, int mode,
+              int precision, void *cuda_stream, gp_ctx **out);
+
+/*
+ * Load psi.  psi points at count = nx*ny*nz interleaved complex values of the
+ * context's precision, on the device (on_device = 1) or the host (0, any host
+ * memory; pinned memory copies faster).  psi == NULL loads the normalised
+ * anisotropic Gaussian exp(-(gamma x^2 + nu y^2 + lambda z^2)/2) instead.
+ * The Dirichlet nodes (index 0 on every bounded axis) are set to zero after
+ * the copy.  Resets the step counter and t to 0.  Returns GP_EINVAL if count
+ * does not match the grid.
+ */
+int gp_load(gp_ctx *ctx, const void *psi, int64_t count, int on_device);
+
+/*
+ * Copy the current (normalised, in imaginary time) psi out to count
+ * interleaved complex values of the context's precision at psi_out, on the
+ * device or the host.  Synchronises the context's stream.
+ */
+int gp_store(gp_ctx *ctx, void *psi_out, int64_t count, int on_device);
+
+/*
+ * Change the nonlinearity and the propagation mode of the resident psi (a
+ * quench: for example an imaginary-time ground state at one g continued in
+ * real time at another).  Takes effect for the next gp_step.
+ */
+int gp_set_params(gp_ctx *ctx, double g, int mode);
+
+/*
+ * Enqueue n >= 0 SSCN steps on the context's stream and return without
+ * waiting.  Each step: calcnu fused with the x sweep, the y sweep, the z
+ * sweep (3D), and in imaginary time the norm reduction whose 1/sqrt(N) scale
+ * is applied at the start of the next step (or by the next read).
+ */
+int gp_step(gp_ctx *ctx, int64_t n);
+
+/*
+ * Compute N, mu, E and the rms sizes of the current state in FP64 and copy
+ * them to *out.  Synchronises the context's stream.  Returns GP_ENONFINITE
+ * (and still fills *out) if any value is NaN or infinite.
+ */
+int gp_observables(gp_ctx *ctx, gp_obs *out);
+
+/* Wait for all work enqueued on the context and report device errors. */
+int gp_sync(gp_ctx *ctx);
+
+/*
+ * Device address of the context's psi buffer (valid until gp_destroy).  The
+ * buffer holds psi up to a pending imaginary-time scale; call gp_store for
+ * normalised values.
+ */
+int gp_device_psi(gp_ctx *ctx, void **dev_ptr);
+
+/* Bytes of device memory gp_create allocates for this grid and precision. */
+int gp_footprint(const gp_grid *grid, int precision, size_t *bytes);
+
+/* Message for the last failure on ctx ("" if none); ctx may be NULL for the
+ * last failure of a gp_create in this thread. */
+const char *gp_last_error(const gp_ctx *ctx);
+
+/* Release the context and its device memory.  NULL is a no-op. */
+void gp_destroy(gp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GP_H */

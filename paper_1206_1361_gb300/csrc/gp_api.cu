@@ -1,0 +1,535 @@
+// gp_api.cu -- host side of libgp: the C ABI declared in include/gp.h, the
+// per-context device state, the Crank-Nicolson coefficient tables and the
+// CUDA-graph replay of the SSCN time loop.
+
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gp.h"
+#include "sscn_internal.h"
+
+using gp::AxisTables;
+using gp::Partials;
+using gp::SweepGeom;
+
+struct gp_ctx {
+    gp_grid grid{};
+    double h[3]{}, dt = 0, w[3]{}, g = 0;
+    int mode = 0, prec = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    void *psi = nullptr, *work = nullptr;
+    AxisTables ax[2][3];            // [mode][axis]
+    double *tv[3]{};                // dt * w_k^2 x^2 / 2 per axis (FP64)
+    float *tv32[3]{};
+    double *partials = nullptr;     // norm partials, >= max sweep blocks
+    int partial_cap = 0;
+    double *obs_partials = nullptr; // kReduceBlocks * kObsWidth
+    double *sums = nullptr;         // kObsWidth
+    double *scale = nullptr;        // pending imaginary-time scale
+    double *norm_dev = nullptr;     // last norm N
+    int *err_dev = nullptr;         // device error bits
+    double *host_sums = nullptr;    // pinned
+    int *host_err = nullptr;        // pinned
+
+    int64_t step = 0;
+    bool scale_pending = false;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    std::string last_error;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kGraphSteps = 10;
+
+int fail(gp_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->last_error = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(gp_ctx *c, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA, m);
+}
+
+#define GP_CK(ctx, call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+bool valid_grid(const gp_grid *g)
+{
+    if (!g) return false;
+    auto ok = [](int n) { return n >= 3 && n <= GP_MAX_EDGE; };
+    return ok(g->nx) && ok(g->ny) && (g->nz == 1 || ok(g->nz));
+}
+
+long long points(const gp_grid &g) { return (long long)g.nx * g.ny * g.nz; }
+
+size_t elem_bytes(int prec) { return prec == GP_C128 ? 16 : 8; }
+
+double coord(int n, double h, int i) { return n == 1 ? 0.0 : -0.5 * n * h + i * h; }
+
+int naxes(const gp_grid &g) { return g.nz > 1 ? 3 : 2; }
+
+int edge(const gp_grid &g, int k) { return k == 0 ? g.nx : (k == 1 ? g.ny : g.nz); }
+
+SweepGeom geom(const gp_grid &gr, int axis)
+{
+    const long long nx = gr.nx, ny = gr.ny;
+    SweepGeom g{};
+    if (axis == 0) { g.n = gr.nx; g.lines_a = gr.ny; g.lines_b = gr.nz; g.stride_a = nx; g.stride_b = nx * ny; g.pstride = 1; }
+    else if (axis == 1) { g.n = gr.ny; g.lines_a = gr.nx; g.lines_b = gr.nz; g.stride_a = 1; g.stride_b = nx * ny; g.pstride = nx; }
+    else { g.n = gr.nz; g.lines_a = gr.nx; g.lines_b = gr.ny; g.stride_a = 1; g.stride_b = nx; g.pstride = nx * ny; }
+    return g;
+}
+
+double cell_volume(const gp_ctx *c) { return c->h[0] * c->h[1] * (c->grid.nz > 1 ? c->h[2] : 1.0); }
+
+// Forward-elimination tables of (I - kappa L), m unknowns:
+// denom_i = 1 + 2 kappa + kappa c'_{i-1} (c'_0 = 0), mult_i = 1/denom_i,
+// c'_i = -kappa mult_i.
+void thomas_tables(int m, std::complex<double> kappa, std::vector<double2> &cp,
+                   std::vector<double2> &mult)
+{
+    cp.resize(m);
+    mult.resize(m);
+    std::complex<double> prev = 0.0;
+    for (int i = 0; i < m; ++i) {
+        const std::complex<double> f = 1.0 / ((1.0 + 2.0 * kappa) + kappa * prev);
+        const std::complex<double> c = -kappa * f;
+        mult[i] = make_double2(f.real(), f.imag());
+        cp[i] = make_double2(c.real(), c.imag());
+        prev = c;
+    }
+}
+
+int alloc(gp_ctx *c, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+    return GP_OK;
+}
+
+int upload_tables(gp_ctx *c)
+{
+    for (int mode = 0; mode < 2; ++mode) {
+        for (int k = 0; k < naxes(c->grid); ++k) {
+            AxisTables &a = c->ax[mode][k];
+            const int n = edge(c->grid, k), m = n - 1;
+            const double kap = c->dt / (4.0 * c->h[k] * c->h[k]);
+            a.n = n;
+            a.h = c->h[k];
+            a.kre = mode == 0 ? kap : 0.0;
+            a.kim = mode == 0 ? 0.0 : kap;
+            std::vector<double2> cp, mult;
+            thomas_tables(m, std::complex<double>(a.kre, a.kim), cp, mult);
+            std::vector<float2> cp32(m), mult32(m);
+            for (int i = 0; i < m; ++i) {
+                cp32[i] = make_float2((float)cp[i].x, (float)cp[i].y);
+                mult32[i] = make_float2((float)mult[i].x, (float)mult[i].y);
+            }
+            GP_CK(c, cudaMemcpy(a.cp64, cp.data(), m * sizeof(double2), cudaMemcpyHostToDevice));
+            GP_CK(c, cudaMemcpy(a.mult64, mult.data(), m * sizeof(double2), cudaMemcpyHostToDevice));
+            GP_CK(c, cudaMemcpy(a.cp32, cp32.data(), m * sizeof(float2), cudaMemcpyHostToDevice));
+            GP_CK(c, cudaMemcpy(a.mult32, mult32.data(), m * sizeof(float2), cudaMemcpyHostToDevice));
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        const int n = edge(c->grid, k);
+        std::vector<double> t(n);
+        std::vector<float> t32(n);
+        for (int i = 0; i < n; ++i) {
+            const double x = coord(n, c->h[k], i);
+            t[i] = c->dt * 0.5 * c->w[k] * c->w[k] * x * x;
+            t32[i] = (float)t[i];
+        }
+        GP_CK(c, cudaMemcpy(c->tv[k], t.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        GP_CK(c, cudaMemcpy(c->tv32[k], t32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return GP_OK;
+}
+
+size_t footprint_bytes(const gp_grid &g, int prec)
+{
+    const size_t psi = (size_t)points(g) * elem_bytes(prec);
+    size_t tables = 0;
+    for (int k = 0; k < 3; ++k) {
+        const size_t n = edge(g, k);
+        tables += 2 * 2 * n * (sizeof(double2) + sizeof(float2)) + n * (sizeof(double) + sizeof(float));
+    }
+    int blocks = 0;
+    for (int k = 0; k < naxes(g); ++k) blocks = std::max(blocks, gp::sweep_blocks(geom(g, k)));
+    blocks = std::max(blocks, gp::kReduceBlocks);
+    const size_t red = (size_t)blocks * sizeof(double) +
+                       (size_t)gp::kReduceBlocks * gp::kObsWidth * sizeof(double) +
+                       gp::kObsWidth * sizeof(double) + 2 * sizeof(double) + sizeof(int);
+    return 2 * psi + tables + red;
+}
+
+void release(gp_ctx *c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    auto fr = [](void *p) { if (p) cudaFree(p); };
+    fr(c->psi);
+    fr(c->work);
+    for (auto &row : c->ax)
+        for (auto &a : row) { fr(a.cp64); fr(a.mult64); fr(a.cp32); fr(a.mult32); }
+    for (int k = 0; k < 3; ++k) { fr(c->tv[k]); fr(c->tv32[k]); }
+    fr(c->partials);
+    fr(c->obs_partials);
+    fr(c->sums);
+    fr(c->scale);
+    fr(c->norm_dev);
+    fr(c->err_dev);
+    if (c->host_sums) cudaFreeHost(c->host_sums);
+    if (c->host_err) cudaFreeHost(c->host_err);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+// Enqueue one SSCN step.
+int enqueue_step(gp_ctx *c)
+{
+    const int mode = c->mode, prec = c->prec;
+    const bool three_d = c->grid.nz > 1;
+    Partials part{c->partials, 1};
+    const Partials *norm_x = nullptr;
+    gp::NonlinArgs nl;
+    nl.tvx = c->tv[0];
+    nl.tvy = c->tv[1];
+    nl.tvz = c->tv[2];
+    nl.tvx32 = c->tv32[0];
+    nl.tvy32 = c->tv32[1];
+    nl.tvz32 = c->tv32[2];
+    nl.dtg = c->dt * c->g;
+    nl.scale = c->scale;
+    const SweepGeom gx = geom(c->grid, 0), gy = geom(c->grid, 1), gz = geom(c->grid, 2);
+    GP_CK(c, gp::launch_sweep_x(prec, mode, c->psi, c->work, c->ax[mode][0], gx, nl,
+                                c->grid.ny, c->grid.nz, norm_x, c->stream));
+    const bool imag = mode == GP_IMAG;
+    GP_CK(c, gp::launch_sweep_yz(prec, mode, c->psi, c->work, c->ax[mode][1], gy,
+                                 (imag && !three_d) ? &part : nullptr, c->stream));
+    int last_blocks = gp::sweep_blocks(gy);
+    if (three_d) {
+        GP_CK(c, gp::launch_sweep_yz(prec, mode, c->psi, c->work, c->ax[mode][2], gz,
+                                     imag ? &part : nullptr, c->stream));
+        last_blocks = gp::sweep_blocks(gz);
+    }
+    if (imag)
+        GP_CK(c, gp::launch_norm_finish(c->partials, last_blocks, cell_volume(c), c->scale,
+                                        c->norm_dev, c->err_dev, c->stream));
+    return GP_OK;
+}
+
+void drop_graph(gp_ctx *c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_steps = 0;
+}
+
+// Capture kGraphSteps steps into a graph; on any capture failure fall back
+// to plain launches (graph stays null).
+void build_graph(gp_ctx *c)
+{
+    drop_graph(c);
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    int rc = GP_OK;
+    for (int s = 0; s < kGraphSteps && rc == GP_OK; ++s) rc = enqueue_step(c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc != GP_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return;
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+        c->graph = ex;
+        c->graph_steps = kGraphSteps;
+    } else {
+        cudaGetLastError();
+    }
+    cudaGraphDestroy(g);
+}
+
+int materialize_scale(gp_ctx *c)
+{
+    if (!c->scale_pending) return GP_OK;
+    GP_CK(c, gp::launch_apply_scale(c->prec, c->psi, points(c->grid), c->scale, c->stream));
+    c->scale_pending = false;
+    return GP_OK;
+}
+
+int read_errors(gp_ctx *c)
+{
+    GP_CK(c, cudaMemcpyAsync(c->host_err, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GP_CK(c, cudaStreamSynchronize(c->stream));
+    if (*c->host_err & 1) return fail(c, GP_ENONFINITE, "norm became non-finite or zero");
+    return GP_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+int gp_footprint(const gp_grid *grid, int precision, size_t *bytes)
+{
+    if (!valid_grid(grid) || (precision != GP_C128 && precision != GP_C64) || !bytes)
+        return fail(nullptr, GP_EINVAL, "gp_footprint: invalid grid or precision");
+    *bytes = footprint_bytes(*grid, precision);
+    return GP_OK;
+}
+
+int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, double nu,
+              double lambda, double g, int mode, int precision, void *cuda_stream,
+              gp_ctx **out)
+{
+    if (out) *out = nullptr;
+    if (!out || !valid_grid(grid) || !dx)
+        return fail(nullptr, GP_EINVAL, "gp_create: invalid grid (nx, ny >= 3; nz == 1 or >= 3; <= 8192)");
+    const int nd = grid->nz > 1 ? 3 : 2;
+    for (int k = 0; k < nd; ++k)
+        if (!(dx[k] > 0) || !std::isfinite(dx[k])) return fail(nullptr, GP_EINVAL, "gp_create: dx must be > 0");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(nullptr, GP_EINVAL, "gp_create: dt must be > 0");
+    if (!(gamma >= 0) || !(nu >= 0) || !(lambda >= 0) || !std::isfinite(gamma + nu + lambda) ||
+        !std::isfinite(g))
+        return fail(nullptr, GP_EINVAL, "gp_create: trap frequencies must be >= 0 and g finite");
+    if (mode != GP_IMAG && mode != GP_REAL) return fail(nullptr, GP_EINVAL, "gp_create: bad mode");
+    if (precision != GP_C128 && precision != GP_C64)
+        return fail(nullptr, GP_EINVAL, "gp_create: bad precision");
+
+    gp_ctx *c = new (std::nothrow) gp_ctx;
+    if (!c) return fail(nullptr, GP_ENOMEM, "gp_create: host allocation failed");
+    c->grid = *grid;
+    c->h[0] = dx[0];
+    c->h[1] = dx[1];
+    c->h[2] = nd == 3 ? dx[2] : 1.0;
+    c->dt = dt;
+    c->w[0] = gamma;
+    c->w[1] = nu;
+    c->w[2] = nd == 3 ? lambda : 0.0;
+    c->g = g;
+    c->mode = mode;
+    c->prec = precision;
+
+    auto bail = [&](int rc) {
+        g_create_error = c->last_error;
+        release(c);
+        delete c;
+        return rc;
+    };
+    int rc;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamCreate"));
+        c->own_stream = true;
+    }
+    const size_t psi_bytes = (size_t)points(c->grid) * elem_bytes(precision);
+    if ((rc = alloc(c, &c->psi, psi_bytes))) return bail(rc);
+    if ((rc = alloc(c, &c->work, psi_bytes))) return bail(rc);
+    for (int mode_i = 0; mode_i < 2; ++mode_i)
+        for (int k = 0; k < naxes(c->grid); ++k) {
+            AxisTables &a = c->ax[mode_i][k];
+            const size_t m = edge(c->grid, k) - 1;
+            if ((rc = alloc(c, (void **)&a.cp64, m * sizeof(double2)))) return bail(rc);
+            if ((rc = alloc(c, (void **)&a.mult64, m * sizeof(double2)))) return bail(rc);
+            if ((rc = alloc(c, (void **)&a.cp32, m * sizeof(float2)))) return bail(rc);
+            if ((rc = alloc(c, (void **)&a.mult32, m * sizeof(float2)))) return bail(rc);
+        }
+    for (int k = 0; k < 3; ++k) {
+        const size_t n = edge(c->grid, k);
+        if ((rc = alloc(c, (void **)&c->tv[k], n * sizeof(double)))) return bail(rc);
+        if ((rc = alloc(c, (void **)&c->tv32[k], n * sizeof(float)))) return bail(rc);
+    }
+    int blocks = gp::kReduceBlocks;
+    for (int k = 0; k < naxes(c->grid); ++k) blocks = std::max(blocks, gp::sweep_blocks(geom(c->grid, k)));
+    c->partial_cap = blocks;
+    if ((rc = alloc(c, (void **)&c->partials, blocks * sizeof(double)))) return bail(rc);
+    if ((rc = alloc(c, (void **)&c->obs_partials, gp::kReduceBlocks * gp::kObsWidth * sizeof(double)))) return bail(rc);
+    if ((rc = alloc(c, (void **)&c->sums, gp::kObsWidth * sizeof(double)))) return bail(rc);
+    if ((rc = alloc(c, (void **)&c->scale, sizeof(double)))) return bail(rc);
+    if ((rc = alloc(c, (void **)&c->norm_dev, sizeof(double)))) return bail(rc);
+    if ((rc = alloc(c, (void **)&c->err_dev, sizeof(int)))) return bail(rc);
+    {
+        cudaError_t e = cudaMallocHost((void **)&c->host_sums, gp::kObsWidth * sizeof(double));
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
+        e = cudaMallocHost((void **)&c->host_err, sizeof(int));
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
+    }
+    if ((rc = upload_tables(c))) return bail(rc);
+    {
+        cudaError_t e = cudaMemsetAsync(c->psi, 0, psi_bytes, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemsetAsync"));
+        const double one = 1.0;
+        e = cudaMemcpyAsync(c->scale, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "init"));
+    }
+    *out = c;
+    return GP_OK;
+}
+
+int gp_load(gp_ctx *c, const void *psi, int64_t count, int on_device)
+{
+    if (!c) return fail(nullptr, GP_EINVAL, "gp_load: null context");
+    const long long n = points(c->grid);
+    c->scale_pending = false;
+    c->step = 0;
+    if (psi == nullptr) {
+        GP_CK(c, gp::launch_seed(c->prec, c->psi, c->grid.nx, c->grid.ny, c->grid.nz, c->h,
+                                 c->w, c->stream));
+        Partials part{c->partials, 1};
+        GP_CK(c, gp::launch_norm_partials(c->prec, c->psi, n, part, gp::kReduceBlocks, c->stream));
+        GP_CK(c, gp::launch_norm_finish(c->partials, gp::kReduceBlocks, cell_volume(c), c->scale,
+                                        c->norm_dev, c->err_dev, c->stream));
+        c->scale_pending = true;
+        return materialize_scale(c);
+    }
+    if (count != n) return fail(c, GP_EINVAL, "gp_load: count != nx*ny*nz");
+    GP_CK(c, cudaMemcpyAsync(c->psi, psi, (size_t)n * elem_bytes(c->prec),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             c->stream));
+    GP_CK(c, gp::launch_zero_boundary(c->prec, c->psi, c->grid.nx, c->grid.ny, c->grid.nz, c->stream));
+    const double one = 1.0;
+    GP_CK(c, cudaMemcpyAsync(c->scale, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    GP_CK(c, cudaStreamSynchronize(c->stream));   // `one` and the caller's buffer
+    return GP_OK;
+}
+
+int gp_store(gp_ctx *c, void *out, int64_t count, int on_device)
+{
+    if (!c || !out) return fail(c, GP_EINVAL, "gp_store: null argument");
+    const long long n = points(c->grid);
+    if (count != n) return fail(c, GP_EINVAL, "gp_store: count != nx*ny*nz");
+    int rc = materialize_scale(c);
+    if (rc) return rc;
+    GP_CK(c, cudaMemcpyAsync(out, c->psi, (size_t)n * elem_bytes(c->prec),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             c->stream));
+    return read_errors(c);
+}
+
+int gp_set_params(gp_ctx *c, double g, int mode)
+{
+    if (!c) return fail(nullptr, GP_EINVAL, "gp_set_params: null context");
+    if (!std::isfinite(g) || (mode != GP_IMAG && mode != GP_REAL))
+        return fail(c, GP_EINVAL, "gp_set_params: bad g or mode");
+    if (mode != c->mode) {
+        int rc = materialize_scale(c);
+        if (rc) return rc;
+    }
+    c->g = g;
+    c->mode = mode;
+    drop_graph(c);
+    return GP_OK;
+}
+
+int gp_step(gp_ctx *c, int64_t n)
+{
+    if (!c) return fail(nullptr, GP_EINVAL, "gp_step: null context");
+    if (n < 0) return fail(c, GP_EINVAL, "gp_step: n < 0");
+    if (n == 0) return GP_OK;
+    if (n >= kGraphSteps && !c->graph) build_graph(c);
+    int64_t done = 0;
+    if (c->graph) {
+        for (; done + c->graph_steps <= n; done += c->graph_steps)
+            GP_CK(c, cudaGraphLaunch(c->graph, c->stream));
+    }
+    for (; done < n; ++done) {
+        int rc = enqueue_step(c);
+        if (rc) return rc;
+    }
+    c->step += n;
+    if (c->mode == GP_IMAG) c->scale_pending = true;
+    return GP_OK;
+}
+
+int gp_observables(gp_ctx *c, gp_obs *o)
+{
+    if (!c || !o) return fail(c, GP_EINVAL, "gp_observables: null argument");
+    gp::ObsArgs a{};
+    a.nx = c->grid.nx;
+    a.ny = c->grid.ny;
+    a.nz = c->grid.nz;
+    for (int k = 0; k < 3; ++k) {
+        a.h[k] = c->h[k];
+        a.w2[k] = c->w[k] * c->w[k];
+    }
+    a.scale = c->scale;
+    GP_CK(c, gp::launch_observables(c->prec, c->psi, a, c->obs_partials, gp::kReduceBlocks,
+                                    c->sums, c->stream));
+    GP_CK(c, cudaMemcpyAsync(c->host_sums, c->sums, gp::kObsWidth * sizeof(double),
+                             cudaMemcpyDeviceToHost, c->stream));
+    int rc = read_errors(c);
+    const double *s = c->host_sums;
+    const double w = cell_volume(c);
+    const double n = w * s[0];
+    double kin = 0.5 * (s[6] / (c->h[0] * c->h[0]) + s[7] / (c->h[1] * c->h[1]));
+    if (c->grid.nz > 1) kin += 0.5 * s[8] / (c->h[2] * c->h[2]);
+    o->norm = n;
+    o->mu = w * (kin + s[4] + c->g * s[5]) / n;
+    o->energy = w * (kin + s[4] + 0.5 * c->g * s[5]) / n;
+    o->rms_x = std::sqrt(s[1] / s[0]);
+    o->rms_y = std::sqrt(s[2] / s[0]);
+    o->rms_z = std::sqrt(s[3] / s[0]);
+    o->rms_r = std::sqrt((s[1] + s[2] + s[3]) / s[0]);
+    o->step = c->step;
+    o->t = c->step * c->dt;
+    if (rc) return rc;
+    const double v[7] = {o->norm, o->mu, o->energy, o->rms_x, o->rms_y, o->rms_z, o->rms_r};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(c, GP_ENONFINITE, "gp_observables: non-finite result");
+    return GP_OK;
+}
+
+int gp_sync(gp_ctx *c)
+{
+    if (!c) return fail(nullptr, GP_EINVAL, "gp_sync: null context");
+    return read_errors(c);
+}
+
+int gp_device_psi(gp_ctx *c, void **p)
+{
+    if (!c || !p) return fail(c, GP_EINVAL, "gp_device_psi: null argument");
+    *p = c->psi;
+    return GP_OK;
+}
+
+const char *gp_last_error(const gp_ctx *c)
+{
+    return c ? c->last_error.c_str() : g_create_error.c_str();
+}
+
+void gp_destroy(gp_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    release(c);
+    delete c;
+}
+
+}  // extern "C"

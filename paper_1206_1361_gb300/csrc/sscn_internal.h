@@ -1,0 +1,93 @@
+// sscn_internal.h -- shared declarations between the libgp host API and its
+// CUDA kernels.  Not part of the public ABI (that is include/gp.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gp {
+
+// Per-axis constants of one Crank-Nicolson sweep: the line has n stored points
+// (m = n - 1 unknowns at indices 1 .. n-1), kappa = kre + i kim, and the
+// forward-elimination tables c'_i and mult_i (i = 1 .. m, stored 0-based) in
+// FP64, plus their FP32 roundings for the complex64 path.
+struct AxisTables {
+    int n = 0;
+    double h = 0, kre = 0, kim = 0;
+    double2 *cp64 = nullptr, *mult64 = nullptr;   // device, m entries each
+    float2 *cp32 = nullptr, *mult32 = nullptr;    // device, m entries each
+};
+
+// One sweep launch: lines are indexed by (a, b), the line's first stored point
+// sits at a * stride_a + b * stride_b and its points are pstride apart.
+struct SweepGeom {
+    int n;               // stored points on each line
+    int lines_a;         // extent of a (thread index inside the grid's x)
+    int lines_b;         // extent of b (grid y)
+    long long stride_a, stride_b, pstride;
+};
+
+// Fused potential / nonlinearity data for the x sweep: theta = tv_x[i] +
+// tv_y[j] + tv_z[k] + dtg |psi|^2 with tv_k = dt * omega_k^2 x^2 / 2.
+struct NonlinArgs {
+    const double *tvx = nullptr, *tvy = nullptr, *tvz = nullptr;  // FP64 tables
+    const float *tvx32 = nullptr, *tvy32 = nullptr, *tvz32 = nullptr;
+    double dtg = 0;
+    const double *scale = nullptr;   // pending imaginary-time scale (device)
+};
+
+// Reduction partials of one sweep / observables pass.
+struct Partials {
+    double *buf = nullptr;   // device, >= blocks * width doubles
+    int width = 1;
+};
+
+enum Precision { kC128 = 0, kC64 = 1 };
+
+// ---- launchers (sscn_kernels.cu) -------------------------------------------
+// All launchers enqueue on `st` and return the launch error (cudaSuccess if
+// the launch was accepted).
+
+// x sweep with the pending scale and the potential/nonlinear step fused in.
+cudaError_t launch_sweep_x(int prec, int mode, void *psi, void *work,
+                           const AxisTables &ax, const SweepGeom &g,
+                           const NonlinArgs &nl, int ny, int nz,
+                           const Partials *norm_out, cudaStream_t st);
+// y or z sweep; norm_out != nullptr adds the FP64 sum |u|^2 per block.
+cudaError_t launch_sweep_yz(int prec, int mode, void *psi, void *work,
+                            const AxisTables &ax, const SweepGeom &g,
+                            const Partials *norm_out, cudaStream_t st);
+int sweep_blocks(const SweepGeom &g);
+
+// scale <- 1 / sqrt(w * sum(partials)); flags a non-finite or non-positive sum.
+cudaError_t launch_norm_finish(const double *partials, int count, double w,
+                               double *scale, double *norm_out, int *err,
+                               cudaStream_t st);
+// psi <- scale * psi over all points, then scale <- 1.
+cudaError_t launch_apply_scale(int prec, void *psi, long long count,
+                               double *scale, cudaStream_t st);
+// Gaussian seed exp(-(gamma x^2 + nu y^2 + lambda z^2)/2), zero Dirichlet nodes.
+cudaError_t launch_seed(int prec, void *psi, int nx, int ny, int nz,
+                        const double h[3], const double w[3], cudaStream_t st);
+// Zero the Dirichlet nodes (index 0 of each bounded axis).
+cudaError_t launch_zero_boundary(int prec, void *psi, int nx, int ny, int nz,
+                                 cudaStream_t st);
+// FP64 sums |psi|^2 over all points into per-block partials.
+cudaError_t launch_norm_partials(int prec, const void *psi, long long count,
+                                 const Partials &out, int blocks, cudaStream_t st);
+
+// Observables: 9 FP64 sums per block (S0, Sx, Sy, Sz, SV, S4, Kx, Ky, Kz) of
+// scale * psi, then a fixed-order finish into sums[9].
+struct ObsArgs {
+    int nx, ny, nz;
+    double h[3], w2[3];    // spacings, squared trap frequencies
+    const double *scale;   // pending scale (device)
+};
+cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
+                               double *partials, int blocks, double *sums,
+                               cudaStream_t st);
+
+constexpr int kObsWidth = 9;
+constexpr int kReduceBlocks = 608;      // 4 x 152 SMs for grid-stride reductions
+
+}  // namespace gp

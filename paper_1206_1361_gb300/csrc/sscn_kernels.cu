@@ -1,0 +1,502 @@
+// sscn_kernels.cu -- CUDA kernels of the split-step Crank-Nicolson step for
+// sm_103a: the fused calcnu + x sweep, the y / z sweeps (calclux, calcluy,
+// calcluz), the norm reduction (calcnorm) and the observables pass
+// (calcmuen, calcrms) of the paper's "Summary of revisions".
+//
+// Every sweep runs one grid line per thread.  For the y and z sweeps the
+// threads of a warp own neighbouring x, so each load and store of a point is a
+// contiguous warp-wide access; the x sweep walks contiguous lines per thread
+// and leans on L1.  The Thomas elimination is exact: forward elimination
+// writes d'_i to a scratch buffer laid out like psi, back substitution reads
+// it back in reverse while the line is still cache-resident.
+//
+// Reductions (norm partials, observables) accumulate in FP64 in a fixed order:
+// per thread sequentially, then a warp-shuffle tree, then per block, so a
+// given launch shape always produces the same bits.
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sscn_internal.h"
+
+namespace gp {
+namespace {
+
+// ------------------------------------------------------------- complex types
+
+template <typename T> struct CT;
+template <> struct CT<double> { using c = double2; };
+template <> struct CT<float> { using c = float2; };
+
+template <typename T> __device__ __forceinline__ typename CT<T>::c mk(T x, T y)
+{
+    typename CT<T>::c r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+
+template <typename T> __device__ __forceinline__ T abs2(typename CT<T>::c v)
+{
+    return v.x * v.x + v.y * v.y;
+}
+
+template <typename T> __device__ __forceinline__ double abs2d(typename CT<T>::c v)
+{
+    double x = (double)v.x, y = (double)v.y;
+    return x * x + y * y;
+}
+
+// ---------------------------------------------------------- block reduction
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum v over the block in a fixed order; the result is valid in thread 0.
+__device__ double block_sum(double v, double *red /* >= 32 doubles */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();                       // red may be reused by the caller
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = lane < nwarps ? red[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+// ------------------------------------------------------------------ sweeps
+
+// Crank-Nicolson coefficients specialised by mode: in imaginary time kappa
+// and the tables are real; in real time kappa = i kim and the tables complex.
+template <typename T, int MODE> struct Cn {
+    using C = typename CT<T>::c;
+    T k;                                   // kre (MODE 0) or kim (MODE 1)
+
+    // b = (1 - 2 kappa) mid + kappa (left + right)
+    __device__ __forceinline__ C rhs(C l, C m, C r) const
+    {
+        if (MODE == 0) {
+            const T a = (T)1 - (T)2 * k;
+            return mk<T>(fma(k, l.x + r.x, a * m.x), fma(k, l.y + r.y, a * m.y));
+        } else {
+            // (1 - 2 i k) m + i k (l + r) = m + i k (l + r - 2 m)
+            const T sx = l.x + r.x - (T)2 * m.x, sy = l.y + r.y - (T)2 * m.y;
+            return mk<T>(fma(-k, sy, m.x), fma(k, sx, m.y));
+        }
+    }
+    // b + kappa d
+    __device__ __forceinline__ C add_kd(C b, C d) const
+    {
+        if (MODE == 0) return mk<T>(fma(k, d.x, b.x), fma(k, d.y, b.y));
+        return mk<T>(fma(-k, d.y, b.x), fma(k, d.x, b.y));
+    }
+    // t * mult
+    __device__ __forceinline__ C mul(C t, C f) const
+    {
+        if (MODE == 0) return mk<T>(t.x * f.x, t.y * f.x);
+        return mk<T>(fma(t.x, f.x, -t.y * f.y), fma(t.x, f.y, t.y * f.x));
+    }
+    // d - c' u
+    __device__ __forceinline__ C back(C d, C c, C u) const
+    {
+        if (MODE == 0) return mk<T>(fma(-c.x, u.x, d.x), fma(-c.x, u.y, d.y));
+        return mk<T>(d.x - fma(c.x, u.x, -c.y * u.y), d.y - fma(c.x, u.y, c.y * u.x));
+    }
+};
+
+// The potential / nonlinearity factor at one point (calcnu):
+// imaginary time psi * s * exp(-theta), real time psi * exp(-i theta),
+// theta = tv_x[i] + tv_yz + dtg |s psi|^2.
+template <typename T, int MODE> struct Nonlin {
+    using C = typename CT<T>::c;
+    const T *tvx;
+    T tvyz, dtg, s;
+
+    __device__ __forceinline__ C apply(C v, int i) const
+    {
+        if (MODE == 0) {
+            v.x *= s;
+            v.y *= s;
+        }
+        const T theta = tvx[i] + tvyz + dtg * abs2<T>(v);
+        if (MODE == 0) {
+            const T f = exp(-theta);
+            return mk<T>(v.x * f, v.y * f);
+        } else {
+            T sn, cs;
+            if constexpr (sizeof(T) == 8) sincos(theta, &sn, &cs);
+            else sincosf(theta, &sn, &cs);
+            // (cs - i sn) (v.x + i v.y)
+            return mk<T>(fma(cs, v.x, sn * v.y), fma(cs, v.y, -sn * v.x));
+        }
+    }
+};
+
+template <typename T, int MODE, bool NL, bool NORM>
+__global__ void __launch_bounds__(128)
+k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ work,
+        const typename CT<T>::c *__restrict__ cp,
+        const typename CT<T>::c *__restrict__ mult, SweepGeom g, T kappa,
+        const T *__restrict__ tvx, const T *__restrict__ tvy,
+        const T *__restrict__ tvz, T dtg, const double *__restrict__ scale,
+        double *__restrict__ partials)
+{
+    using C = typename CT<T>::c;
+    __shared__ double red[32];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    double nacc = 0.0;
+    if (a < g.lines_a) {
+        const long long base = (long long)a * g.stride_a + (long long)b * g.stride_b;
+        C *line = psi + base;
+        C *wl = work + base;
+        const long long s = g.pstride;
+        const int m = g.n - 1;
+        const Cn<T, MODE> cn{kappa};
+        Nonlin<T, MODE> nl{};
+        if (NL) {
+            // x sweep: a is the y index, b the z index
+            nl.tvx = tvx;
+            nl.tvyz = tvy[a] + (tvz ? tvz[b] : (T)0);
+            nl.dtg = dtg;
+            nl.s = (MODE == 0) ? (T)(*scale) : (T)1;
+        }
+        const C zero = mk<T>((T)0, (T)0);
+        C left = zero;
+        C mid = line[s];
+        if (NL) mid = nl.apply(mid, 1);
+        C right = zero;
+        if (m >= 2) {
+            right = line[2 * s];
+            if (NL) right = nl.apply(right, 2);
+        }
+        C d = zero;
+        for (int i = 1; i <= m; ++i) {
+            const C rb = cn.rhs(left, mid, right);
+            d = cn.mul(cn.add_kd(rb, d), mult[i - 1]);
+            wl[i * s] = d;
+            left = mid;
+            mid = right;
+            if (i + 2 <= m) {
+                right = line[(long long)(i + 2) * s];
+                if (NL) right = nl.apply(right, i + 2);
+            } else {
+                right = zero;
+            }
+        }
+        C u = d;
+        line[(long long)m * s] = u;
+        if (NORM) nacc += abs2d<T>(u);
+        for (int i = m - 1; i >= 1; --i) {
+            u = cn.back(wl[(long long)i * s], cp[i - 1], u);
+            line[(long long)i * s] = u;
+            if (NORM) nacc += abs2d<T>(u);
+        }
+    }
+    if (NORM) {
+        const double r = block_sum(nacc, red);
+        if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = r;
+    }
+}
+
+constexpr int kSweepThreads = 128;
+
+template <typename T, int MODE, bool NL, bool NORM>
+cudaError_t sweep_launch(void *psi, void *work, const AxisTables &ax,
+                         const SweepGeom &g, const NonlinArgs *nl,
+                         const Partials *norm_out, cudaStream_t st)
+{
+    using C = typename CT<T>::c;
+    dim3 grid((g.lines_a + kSweepThreads - 1) / kSweepThreads, g.lines_b);
+    const C *cp, *mult;
+    const T *tvx = nullptr, *tvy = nullptr, *tvz = nullptr;
+    T kappa = (T)(MODE == 0 ? ax.kre : ax.kim);
+    if constexpr (sizeof(T) == 8) {
+        cp = reinterpret_cast<const C *>(ax.cp64);
+        mult = reinterpret_cast<const C *>(ax.mult64);
+        if (nl) { tvx = (const T *)nl->tvx; tvy = (const T *)nl->tvy; tvz = (const T *)nl->tvz; }
+    } else {
+        cp = reinterpret_cast<const C *>(ax.cp32);
+        mult = reinterpret_cast<const C *>(ax.mult32);
+        if (nl) { tvx = (const T *)nl->tvx32; tvy = (const T *)nl->tvy32; tvz = (const T *)nl->tvz32; }
+    }
+    k_sweep<T, MODE, NL, NORM><<<grid, kSweepThreads, 0, st>>>(
+        reinterpret_cast<C *>(psi), reinterpret_cast<C *>(work), cp, mult, g, kappa,
+        tvx, tvy, tvz, nl ? (T)nl->dtg : (T)0, nl ? nl->scale : nullptr,
+        norm_out ? norm_out->buf : nullptr);
+    return cudaGetLastError();
+}
+
+template <typename T, bool NL>
+cudaError_t sweep_dispatch(int mode, void *psi, void *work, const AxisTables &ax,
+                           const SweepGeom &g, const NonlinArgs *nl,
+                           const Partials *norm_out, cudaStream_t st)
+{
+    if (mode == 0) {
+        if (norm_out) return sweep_launch<T, 0, NL, true>(psi, work, ax, g, nl, norm_out, st);
+        return sweep_launch<T, 0, NL, false>(psi, work, ax, g, nl, norm_out, st);
+    }
+    if (norm_out) return sweep_launch<T, 1, NL, true>(psi, work, ax, g, nl, norm_out, st);
+    return sweep_launch<T, 1, NL, false>(psi, work, ax, g, nl, norm_out, st);
+}
+
+// ------------------------------------------------------- pointwise kernels
+
+__global__ void k_norm_finish(const double *__restrict__ partials, int count,
+                              double w, double *scale, double *norm_out, int *err)
+{
+    __shared__ double red[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) v += partials[i];
+    const double total = block_sum(v, red);
+    if (threadIdx.x == 0) {
+        const double n = w * total;
+        if (norm_out) *norm_out = n;
+        if (!(n > 0.0) || !isfinite(n)) {
+            atomicOr(err, 1);
+            *scale = 1.0;
+        } else {
+            *scale = 1.0 / sqrt(n);
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_apply_scale(typename CT<T>::c *__restrict__ psi, long long count,
+                              const double *__restrict__ scale)
+{
+    const T s = (T)(*scale);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
+         p += (long long)gridDim.x * blockDim.x) {
+        auto v = psi[p];
+        v.x *= s;
+        v.y *= s;
+        psi[p] = v;
+    }
+}
+
+__global__ void k_set_one(double *x) { *x = 1.0; }
+
+__device__ __forceinline__ double coord(int n, double h, int i)
+{
+    return n == 1 ? 0.0 : -0.5 * (double)n * h + (double)i * h;
+}
+
+template <typename T>
+__global__ void k_seed(typename CT<T>::c *__restrict__ psi, int nx, int ny, int nz,
+                       double hx, double hy, double hz, double gx, double gy, double gz)
+{
+    const long long count = (long long)nx * ny * nz;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p % nx);
+        const int j = (int)((p / nx) % ny);
+        const int k = (int)(p / ((long long)nx * ny));
+        const bool edge = i == 0 || j == 0 || (nz > 1 && k == 0);
+        double v = 0.0;
+        if (!edge) {
+            const double x = coord(nx, hx, i), y = coord(ny, hy, j), z = coord(nz, hz, k);
+            v = exp(-0.5 * (gx * x * x + gy * y * y + gz * z * z));
+        }
+        psi[p] = mk<T>((T)v, (T)0);
+    }
+}
+
+template <typename T>
+__global__ void k_zero_boundary(typename CT<T>::c *__restrict__ psi, int nx, int ny, int nz)
+{
+    const long long count = (long long)nx * ny * nz;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p % nx);
+        const int j = (int)((p / nx) % ny);
+        const int k = (int)(p / ((long long)nx * ny));
+        if (i == 0 || j == 0 || (nz > 1 && k == 0)) psi[p] = mk<T>((T)0, (T)0);
+    }
+}
+
+template <typename T>
+__global__ void k_norm_partials(const typename CT<T>::c *__restrict__ psi, long long count,
+                                double *__restrict__ partials)
+{
+    __shared__ double red[32];
+    double v = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
+         p += (long long)gridDim.x * blockDim.x)
+        v += abs2d<T>(psi[p]);
+    const double r = block_sum(v, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = r;
+}
+
+// ------------------------------------------------------------ observables
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_observables(const typename CT<T>::c *__restrict__ psi, ObsArgs a,
+              double *__restrict__ partials)
+{
+    using C = typename CT<T>::c;
+    __shared__ double red[32];
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long plane = (long long)nx * ny, count = plane * nz;
+    const double s = *a.scale, s2 = s * s;
+    double acc[kObsWidth];
+#pragma unroll
+    for (int q = 0; q < kObsWidth; ++q) acc[q] = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p % nx);
+        const int j = (int)((p / nx) % ny);
+        const int k = (int)(p / plane);
+        const C v = psi[p];
+        const double vr = v.x, vi = v.y;
+        const double am = s2 * (vr * vr + vi * vi);
+        const double x = coord(nx, a.h[0], i), y = coord(ny, a.h[1], j), z = coord(nz, a.h[2], k);
+        acc[0] += am;
+        acc[1] += x * x * am;
+        acc[2] += y * y * am;
+        acc[3] += z * z * am;
+        acc[4] += 0.5 * (a.w2[0] * x * x + a.w2[1] * y * y + a.w2[2] * z * z) * am;
+        acc[5] += am * am;
+        C nb;
+        nb = (i + 1 < nx) ? psi[p + 1] : mk<T>((T)0, (T)0);
+        acc[6] += s2 * (((double)nb.x - vr) * ((double)nb.x - vr) + ((double)nb.y - vi) * ((double)nb.y - vi));
+        nb = (j + 1 < ny) ? psi[p + nx] : mk<T>((T)0, (T)0);
+        acc[7] += s2 * (((double)nb.x - vr) * ((double)nb.x - vr) + ((double)nb.y - vi) * ((double)nb.y - vi));
+        if (nz > 1) {
+            nb = (k + 1 < nz) ? psi[p + plane] : mk<T>((T)0, (T)0);
+            acc[8] += s2 * (((double)nb.x - vr) * ((double)nb.x - vr) + ((double)nb.y - vi) * ((double)nb.y - vi));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kObsWidth; ++q) {
+        const double r = block_sum(acc[q], red);
+        if (threadIdx.x == 0) partials[(long long)blockIdx.x * kObsWidth + q] = r;
+    }
+}
+
+__global__ void k_obs_finish(const double *__restrict__ partials, int blocks,
+                             double *__restrict__ sums)
+{
+    __shared__ double red[32];
+    for (int q = 0; q < kObsWidth; ++q) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < blocks; b += blockDim.x) v += partials[(long long)b * kObsWidth + q];
+        const double r = block_sum(v, red);
+        if (threadIdx.x == 0) sums[q] = r;
+    }
+}
+
+constexpr int kPointThreads = 256;
+
+int point_blocks(long long count)
+{
+    long long b = (count + kPointThreads - 1) / kPointThreads;
+    if (b > kReduceBlocks) b = kReduceBlocks;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+// ================================================================ launchers
+
+int sweep_blocks(const SweepGeom &g)
+{
+    return ((g.lines_a + kSweepThreads - 1) / kSweepThreads) * g.lines_b;
+}
+
+cudaError_t launch_sweep_x(int prec, int mode, void *psi, void *work,
+                           const AxisTables &ax, const SweepGeom &g,
+                           const NonlinArgs &nl, int, int, const Partials *norm_out,
+                           cudaStream_t st)
+{
+    if (prec == kC128) return sweep_dispatch<double, true>(mode, psi, work, ax, g, &nl, norm_out, st);
+    return sweep_dispatch<float, true>(mode, psi, work, ax, g, &nl, norm_out, st);
+}
+
+cudaError_t launch_sweep_yz(int prec, int mode, void *psi, void *work,
+                            const AxisTables &ax, const SweepGeom &g,
+                            const Partials *norm_out, cudaStream_t st)
+{
+    if (prec == kC128) return sweep_dispatch<double, false>(mode, psi, work, ax, g, nullptr, norm_out, st);
+    return sweep_dispatch<float, false>(mode, psi, work, ax, g, nullptr, norm_out, st);
+}
+
+cudaError_t launch_norm_finish(const double *partials, int count, double w,
+                               double *scale, double *norm_out, int *err, cudaStream_t st)
+{
+    k_norm_finish<<<1, 256, 0, st>>>(partials, count, w, scale, norm_out, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_scale(int prec, void *psi, long long count, double *scale,
+                               cudaStream_t st)
+{
+    const int blocks = point_blocks(count);
+    if (prec == kC128)
+        k_apply_scale<double><<<blocks, kPointThreads, 0, st>>>((double2 *)psi, count, scale);
+    else
+        k_apply_scale<float><<<blocks, kPointThreads, 0, st>>>((float2 *)psi, count, scale);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_set_one<<<1, 1, 0, st>>>(scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed(int prec, void *psi, int nx, int ny, int nz, const double h[3],
+                        const double w[3], cudaStream_t st)
+{
+    const long long count = (long long)nx * ny * nz;
+    const int blocks = point_blocks(count);
+    if (prec == kC128)
+        k_seed<double><<<blocks, kPointThreads, 0, st>>>((double2 *)psi, nx, ny, nz, h[0], h[1], h[2], w[0], w[1], w[2]);
+    else
+        k_seed<float><<<blocks, kPointThreads, 0, st>>>((float2 *)psi, nx, ny, nz, h[0], h[1], h[2], w[0], w[1], w[2]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_boundary(int prec, void *psi, int nx, int ny, int nz, cudaStream_t st)
+{
+    const long long count = (long long)nx * ny * nz;
+    const int blocks = point_blocks(count);
+    if (prec == kC128)
+        k_zero_boundary<double><<<blocks, kPointThreads, 0, st>>>((double2 *)psi, nx, ny, nz);
+    else
+        k_zero_boundary<float><<<blocks, kPointThreads, 0, st>>>((float2 *)psi, nx, ny, nz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm_partials(int prec, const void *psi, long long count,
+                                 const Partials &out, int blocks, cudaStream_t st)
+{
+    if (prec == kC128)
+        k_norm_partials<double><<<blocks, kPointThreads, 0, st>>>((const double2 *)psi, count, out.buf);
+    else
+        k_norm_partials<float><<<blocks, kPointThreads, 0, st>>>((const float2 *)psi, count, out.buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
+                               double *partials, int blocks, double *sums, cudaStream_t st)
+{
+    if (prec == kC128)
+        k_observables<double><<<blocks, kPointThreads, 0, st>>>((const double2 *)psi, a, partials);
+    else
+        k_observables<float><<<blocks, kPointThreads, 0, st>>>((const float2 *)psi, a, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_obs_finish<<<1, 256, 0, st>>>(partials, blocks, sums);
+    return cudaGetLastError();
+}
+
+}  // namespace gp

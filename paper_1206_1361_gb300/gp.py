@@ -1,0 +1,258 @@
+"""Python binding of libgp's C ABI (include/gp.h): the same entry points,
+argument marshalling only.  Every step of the computation runs in the CUDA
+library; nothing here computes.
+
+psi arguments may be a numpy array (host), a torch tensor (host or CUDA), or a
+raw integer address with ``on_device`` given explicitly.  complex128 pairs
+with GP_C128 and complex64 with GP_C64.  Failures raise ``GPError`` carrying
+the library's code and message.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgp.so")
+
+GP_IMAG, GP_REAL = 0, 1
+GP_C128, GP_C64 = 0, 1
+GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ENONFINITE, GP_ETIMEOUT, GP_EINTERNAL = (
+    0, -1, -2, -3, -4, -5, -6)
+GP_MAX_EDGE = 8192
+
+ERROR_NAMES = {GP_EINVAL: "GP_EINVAL", GP_ENOMEM: "GP_ENOMEM", GP_ECUDA: "GP_ECUDA",
+               GP_ENONFINITE: "GP_ENONFINITE", GP_ETIMEOUT: "GP_ETIMEOUT",
+               GP_EINTERNAL: "GP_EINTERNAL"}
+
+
+class GPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERROR_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class gp_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class gp_obs(ctypes.Structure):
+    _fields_ = [("norm", ctypes.c_double), ("mu", ctypes.c_double),
+                ("energy", ctypes.c_double), ("rms_x", ctypes.c_double),
+                ("rms_y", ctypes.c_double), ("rms_z", ctypes.c_double),
+                ("rms_r", ctypes.c_double), ("step", ctypes.c_int64),
+                ("t", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# Every entry point include/gp.h declares: name -> (restype, argtypes).
+_vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_int = ctypes.c_int
+SIGNATURES = {
+    "gp_create": (_int, [ctypes.POINTER(gp_grid), ctypes.POINTER(ctypes.c_double), _dbl,
+                         _dbl, _dbl, _dbl, _dbl, _int, _int, _vp, ctypes.POINTER(_vp)]),
+    "gp_load": (_int, [_vp, _vp, _i64, _int]),
+    "gp_store": (_int, [_vp, _vp, _i64, _int]),
+    "gp_set_params": (_int, [_vp, _dbl, _int]),
+    "gp_step": (_int, [_vp, _i64]),
+    "gp_observables": (_int, [_vp, ctypes.POINTER(gp_obs)]),
+    "gp_sync": (_int, [_vp]),
+    "gp_device_psi": (_int, [_vp, ctypes.POINTER(_vp)]),
+    "gp_footprint": (_int, [ctypes.POINTER(gp_grid), _int, ctypes.POINTER(ctypes.c_size_t)]),
+    "gp_last_error": (ctypes.c_char_p, [_vp]),
+    "gp_destroy": (None, [_vp]),
+}
+
+_lib = None
+
+
+def load_library(path=None):
+    """Load libgp.so (built in-tree by ``__graft_entry__.build()``).  Raises
+    if it is missing: there is no fallback implementation."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libgp.so not built at %s: run __graft_entry__.build()" % p)
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _err(ctx, rc):
+    if rc != GP_OK:
+        msg = load_library().gp_last_error(ctx)
+        raise GPError(rc, msg.decode() if msg else "")
+
+
+def _buffer(psi):
+    """(address, element count, on_device, keepalive) for a psi argument."""
+    if psi is None:
+        return None, 0, 0, None
+    if isinstance(psi, np.ndarray):
+        if not psi.flags.c_contiguous:
+            raise ValueError("psi must be C-contiguous")
+        return psi.ctypes.data, psi.size, 0, psi
+    mod = type(psi).__module__
+    if mod.startswith("torch"):
+        if not psi.is_contiguous():
+            raise ValueError("psi must be contiguous")
+        return psi.data_ptr(), psi.numel(), 1 if psi.is_cuda else 0, psi
+    raise TypeError("psi must be a numpy array, a torch tensor or None")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream          # torch.cuda.Stream
+
+
+# ----------------------------------------------------------- entry points
+
+def gp_create(grid, dx, dt, gamma, nu, lam, g, mode=GP_IMAG, precision=GP_C128,
+              cuda_stream=None):
+    """grid = (nx, ny, nz); dx = (hx, hy, hz).  Returns the context handle."""
+    L = load_library()
+    gr = gp_grid(*[int(v) for v in grid])
+    h = (ctypes.c_double * 3)(*[float(v) for v in dx])
+    out = _vp()
+    rc = L.gp_create(ctypes.byref(gr), h, float(dt), float(gamma), float(nu), float(lam),
+                     float(g), int(mode), int(precision), _stream_handle(cuda_stream),
+                     ctypes.byref(out))
+    if rc != GP_OK:
+        msg = L.gp_last_error(None)
+        raise GPError(rc, msg.decode() if msg else "")
+    return out.value
+
+
+def gp_load(ctx, psi=None, count=None, on_device=None):
+    """psi None loads the normalised Gaussian seed."""
+    addr, n, dev, _keep = _buffer(psi) if not isinstance(psi, int) else (psi, count, on_device, None)
+    if count is not None:
+        n = count
+    if on_device is not None:
+        dev = on_device
+    _err(ctx, load_library().gp_load(ctx, addr, int(n or 0), int(dev or 0)))
+
+
+def gp_store(ctx, out, count=None, on_device=None):
+    addr, n, dev, _keep = _buffer(out) if not isinstance(out, int) else (out, count, on_device, None)
+    if count is not None:
+        n = count
+    if on_device is not None:
+        dev = on_device
+    _err(ctx, load_library().gp_store(ctx, addr, int(n), int(dev)))
+    return out
+
+
+def gp_set_params(ctx, g, mode):
+    _err(ctx, load_library().gp_set_params(ctx, float(g), int(mode)))
+
+
+def gp_step(ctx, n):
+    _err(ctx, load_library().gp_step(ctx, int(n)))
+
+
+def gp_observables(ctx):
+    o = gp_obs()
+    _err(ctx, load_library().gp_observables(ctx, ctypes.byref(o)))
+    return o.as_dict()
+
+
+def gp_sync(ctx):
+    _err(ctx, load_library().gp_sync(ctx))
+
+
+def gp_device_psi(ctx):
+    p = _vp()
+    _err(ctx, load_library().gp_device_psi(ctx, ctypes.byref(p)))
+    return p.value
+
+
+def gp_footprint(grid, precision=GP_C128):
+    gr = gp_grid(*[int(v) for v in grid])
+    b = ctypes.c_size_t()
+    rc = load_library().gp_footprint(ctypes.byref(gr), int(precision), ctypes.byref(b))
+    if rc != GP_OK:
+        raise GPError(rc, load_library().gp_last_error(None).decode())
+    return b.value
+
+
+def gp_last_error(ctx=None):
+    msg = load_library().gp_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def gp_destroy(ctx):
+    load_library().gp_destroy(ctx)
+
+
+# ------------------------------------------------------------ convenience
+
+class Solver:
+    """Owns one context.  ``shape`` is (nx, ny, nz); arrays are (nz, ny, nx)."""
+
+    def __init__(self, shape, dx, dt, gamma, nu, lam, g, mode=GP_IMAG,
+                 precision=GP_C128, stream=None):
+        self.shape = tuple(int(v) for v in shape)
+        self.precision = precision
+        self.ctx = gp_create(self.shape, dx, dt, gamma, nu, lam, g, mode, precision, stream)
+
+    @property
+    def array_shape(self):
+        nx, ny, nz = self.shape
+        return (nz, ny, nx)
+
+    @property
+    def dtype(self):
+        return np.complex128 if self.precision == GP_C128 else np.complex64
+
+    def load(self, psi=None):
+        gp_load(self.ctx, psi)
+        return self
+
+    def step(self, n):
+        gp_step(self.ctx, n)
+        return self
+
+    def set_params(self, g, mode):
+        gp_set_params(self.ctx, g, mode)
+        return self
+
+    def observables(self):
+        return gp_observables(self.ctx)
+
+    def psi(self):
+        out = np.empty(self.array_shape, self.dtype)
+        gp_store(self.ctx, out)
+        return out
+
+    def sync(self):
+        gp_sync(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            gp_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,171 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle,
+element by element on the same inputs.  Sizes span several 128-line tiles and
+ragged tails; tolerances are stated per test (FP64: relative L2 of psi <=
+1e-10 over 1000 steps; complex64: relative mu <= 1e-6)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1206_1361_gb300 import gp
+from tests.gpu_util import oracle_params, rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+W3 = (1.0, 1.5, 2.0)
+
+
+def rand_state(shape, seed, dtype=np.complex128):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    a = (rng.standard_normal((nz, ny, nx)) + 1j * rng.standard_normal((nz, ny, nx))) * 0.3
+    a[:, :, 0] = 0
+    a[:, 0, :] = 0
+    if nz > 1:
+        a[0] = 0
+    return a.astype(dtype)
+
+
+def run_gpu(shape, h, dt, w, g, mode, steps, psi0=None, precision=gp.GP_C128):
+    with gp.Solver(shape, h, dt, w[0], w[1], w[2], g, mode, precision) as s:
+        s.load(psi0)
+        s.step(steps)
+        return s.psi(), s.observables()
+
+
+SHAPES = [
+    ((3, 3, 3), (0.9, 0.8, 0.7)),
+    ((33, 130, 17), (0.3, 0.1, 0.5)),
+    ((129, 5, 3), (0.1, 1.0, 1.5)),
+    ((65, 131, 1), (0.2, 0.15, 1.0)),
+    ((200, 7, 140), (0.08, 1.2, 0.1)),
+]
+
+
+@pytest.mark.parametrize("shape,h", SHAPES)
+@pytest.mark.parametrize("mode", [gp.GP_IMAG, gp.GP_REAL])
+def test_random_state_steps_match_oracle(shape, h, mode):
+    require_gpu()
+    dt, g = 0.004, 7.0
+    psi0 = rand_state(shape, 17)
+    got, _ = run_gpu(shape, h, dt, W3, g, mode, 12, psi0)
+    p = oracle_params(shape, h, dt, W3, g, mode)
+    want = psi0.copy()
+    oracle.step(p, want, 12)
+    assert rel_l2(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("mode", [gp.GP_IMAG, gp.GP_REAL])
+def test_gaussian_seed_matches_oracle(mode):
+    require_gpu()
+    shape, h = (40, 36, 32), (0.25, 0.25, 0.25)
+    got, obs = run_gpu(shape, h, 0.01, W3, 5.0, mode, 0)
+    p = oracle_params(shape, h, 0.01, W3, 5.0, mode)
+    want = oracle.seed(p)
+    # the exponent reaches ~-50 at the box edge: a 1-ulp difference in a
+    # coordinate (FMA contraction on the GPU) moves exp by ~1e-14 relative
+    assert rel_l2(got, want) <= 1e-13
+    ref = oracle.observables(p, want)
+    for k, v in ref.items():
+        assert abs(obs[k] - v) <= 1e-12 * max(1.0, abs(v)), k
+
+
+def test_config_small_imaginary_time_1000_steps():
+    """64^3 on [-6.4, 6.4)^3, gamma, nu, lambda = 1, 1.5, 2, g = 10, dt = 0.002,
+    1000 imaginary-time steps from the Gaussian seed: relative L2 of psi and
+    every observable within 1e-10 of the oracle."""
+    require_gpu()
+    shape, h, dt, g = (64, 64, 64), (0.2, 0.2, 0.2), 0.002, 10.0
+    got, obs = run_gpu(shape, h, dt, W3, g, gp.GP_IMAG, 1000)
+    p = oracle_params(shape, h, dt, W3, g, 0)
+    want = oracle.seed(p)
+    oracle.step(p, want, 1000)
+    assert rel_l2(got, want) <= 1e-10
+    ref = oracle.observables(p, want)
+    for k, v in ref.items():
+        assert abs(obs[k] - v) <= 1e-10 * abs(v), (k, obs[k], v)
+    assert obs["step"] == 1000
+
+
+def test_quench_imag_to_real_matches_oracle():
+    require_gpu()
+    shape, h, dt = (48, 40, 36), (0.25, 0.25, 0.25), 0.002
+    with gp.Solver(shape, h, dt, *W3, 20.0, gp.GP_IMAG) as s:
+        s.load(None).step(150)
+        s.set_params(18.0, gp.GP_REAL).step(100)
+        got = s.psi()
+    pi = oracle_params(shape, h, dt, W3, 20.0, 0)
+    want = oracle.seed(pi)
+    oracle.step(pi, want, 150)
+    pr = oracle_params(shape, h, dt, W3, 18.0, 1)
+    oracle.step(pr, want, 100)
+    assert rel_l2(got, want) <= 1e-11
+
+
+def test_store_load_roundtrip_and_step_counter():
+    require_gpu()
+    shape, h = (20, 24, 28), (0.4, 0.4, 0.4)
+    psi0 = rand_state(shape, 3)
+    with gp.Solver(shape, h, 0.01, *W3, 1.0, gp.GP_REAL) as s:
+        s.load(psi0)
+        assert np.array_equal(s.psi(), psi0)
+        s.step(7)
+        assert s.observables()["step"] == 7
+        mid = s.psi()
+        s.load(mid)
+        assert s.observables()["step"] == 0
+        assert np.array_equal(s.psi(), mid)
+
+
+def test_load_zeroes_dirichlet_nodes():
+    require_gpu()
+    shape = (8, 9, 10)
+    a = np.ones((10, 9, 8), np.complex128)
+    with gp.Solver(shape, (0.5, 0.5, 0.5), 0.01, *W3, 0.0) as s:
+        s.load(a)
+        b = s.psi()
+    assert np.all(b[:, :, 0] == 0) and np.all(b[:, 0, :] == 0) and np.all(b[0] == 0)
+    assert np.all(b[1:, 1:, 1:] == 1)
+
+
+def test_complex64_mu_within_1e6_of_fp64():
+    require_gpu()
+    shape, h, dt, g = (64, 64, 64), (0.2, 0.2, 0.2), 0.002, 10.0
+    _, o64 = run_gpu(shape, h, dt, W3, g, gp.GP_IMAG, 1000)
+    got, o32 = run_gpu(shape, h, dt, W3, g, gp.GP_IMAG, 1000, precision=gp.GP_C64)
+    assert got.dtype == np.complex64
+    assert abs(o32["mu"] - o64["mu"]) <= 1e-6 * abs(o64["mu"])
+    assert abs(o32["norm"] - 1) <= 1e-6
+
+
+def test_torch_device_buffers_and_stream():
+    require_gpu()
+    import torch
+    shape, h = (32, 30, 28), (0.3, 0.3, 0.3)
+    psi0 = rand_state(shape, 9)
+    dev = torch.from_numpy(psi0).cuda()
+    stream = torch.cuda.Stream()
+    ctx = gp.gp_create(shape, h, 0.005, *W3, 3.0, gp.GP_REAL, gp.GP_C128, stream)
+    try:
+        gp.gp_load(ctx, dev)
+        gp.gp_step(ctx, 5)
+        out = torch.empty_like(dev)
+        gp.gp_store(ctx, out)
+        want = psi0.copy()
+        oracle.step(oracle_params(shape, h, 0.005, W3, 3.0, 1), want, 5)
+        assert rel_l2(out.cpu().numpy(), want) <= 1e-12
+        assert gp.gp_device_psi(ctx) != 0
+    finally:
+        gp.gp_destroy(ctx)
+
+
+def test_nonfinite_input_is_reported():
+    require_gpu()
+    shape = (8, 8, 8)
+    a = np.zeros((8, 8, 8), np.complex128)
+    a[3, 3, 3] = np.nan
+    with gp.Solver(shape, (0.5, 0.5, 0.5), 0.01, *W3, 1.0, gp.GP_IMAG) as s:
+        s.load(a)
+        s.step(2)
+        with pytest.raises(gp.GPError) as e:
+            s.observables()
+        assert e.value.code == gp.GP_ENONFINITE
