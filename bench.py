@@ -1,0 +1,431 @@
+#!/usr/bin/env python3
+"""Benchmark of the split-step Crank-Nicolson GP propagation on GB300.
+
+Workload (one GPU): 256^3 grid on [-12.8, 12.8)^3 (dx = 0.1), trap
+(1, sqrt 2, 2), dt = 0.0005, complex128 psi.  Untimed preparation: the
+imaginary-time ground state at g = 20 from the Gaussian seed, then a quench
+to g = 18 in real time.  One benchmark step = 10 real-time SSCN steps plus
+one observables report (the report interval), so every kernel of the path
+runs inside the timed region.  psi (268 MB) is larger than L2 (129 MB).
+
+Metric: grid-point-steps/s (points x SSCN steps / s), whole job over all
+ranks; with --gpus N > 1 each rank runs an independent replica (the path has
+no exchange step) and the time is the max over ranks.
+
+--impl reference times the FP64 CPU oracle on this host's cores on the same
+workload (Gaussian start, one SSCN step per benchmark step, observables every
+10th step) and prints the same JSON line with "impl": "reference".
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "3D SSCN grid-point-steps/s & HBM roofline frac; serve p50/p99 vs plain"
+UNIT = "grid-point-steps/s"
+STEPS_PER_BENCH_STEP = 10
+
+# FP64 flops per point of each kernel slot, counting +, -, x of the method's
+# formulas (a complex multiply is 6, complex add 2, real x complex 2; exp and
+# sincos count 1 each).  Real time: calcnu = |psi|^2 (3) + theta (3) + sincos
+# (1) + complex multiply (6) = 13; one Crank-Nicolson line update = RHS (10)
+# + forward elimination (10) + back substitution (8) = 28.  Imaginary time:
+# calcnu with the scale = 2 + 3 + 3 + 1 + 2 = 11; sweep = 8 + 6 + 4 = 18.
+FLOPS_PER_POINT = {
+    1: {"sweep_x": 13 + 28, "sweep_y": 28, "sweep_z": 28},
+    0: {"sweep_x": 11 + 18, "sweep_y": 18, "sweep_z": 18},
+}
+# Algorithmic HBM bytes per point of one sweep: read psi once, write it once.
+SWEEP_BYTES_PER_POINT = {0: 32, 1: 16}          # by precision: c128, c64
+
+SM_COUNT, SM_MAX_GHZ = 152, 2.07
+# GB300 FP64: 2 FMA per clock per SM (1.25 TFLOP/s nominal = 152 x 2 x 2 x
+# 2.07 GHz; a DFMA microbenchmark measured 1.19 TFLOP/s on this machine).
+FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_GHZ / 1e3
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__,
+                                 formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30, help="timed benchmark steps")
+    ap.add_argument("--warmup", type=int, default=3, help="untimed benchmark steps")
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--prep-max-steps", type=int, default=4000,
+                    help="cap on imaginary-time ground-state steps before the quench")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="budget of the oracle CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe", type=int, default=0, metavar="N",
+                    help="profiling aid: load the Gaussian seed, run N real-time SSCN "
+                         "steps of the workload, print nothing and exit")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1206_1361_gb300.workloads import REAL_256
+    return REAL_256
+
+
+def config_dict(case, extra=None):
+    d = {"workload": case.name, "grid": list(case.shape), "dx": list(case.h), "dt": case.dt,
+         "trap": [round(v, 6) for v in case.trap], "g": case.g, "mode": "real",
+         "psi": "complex128" if case.precision == 0 else "complex64",
+         "sscn_steps_per_bench_step": STEPS_PER_BENCH_STEP,
+         "report_every": case.extra.get("report_every", 10),
+         "l2": "inputs larger than L2 (psi 268 MB > 129 MB), no flush"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ------------------------------------------------------------------ clocks
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASON_NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    def __init__(self, device_id):
+        self.device_id = device_id
+        self.proc = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", "--query-gpu=" + CLOCK_FIELDS, "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.device_id:
+                cmd += ["-i", self.device_id]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(REASON_NAMES, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# -------------------------------------------------------------- helpers
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1206_1361_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload_name):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary under
+    profiles/, if it was taken on the current kernel sources; else None."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    sha = kernel_source_sha()
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith((".md", ".txt")):
+            continue
+        text = open(os.path.join(pdir, fn)).read()
+        m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+        if not m_sha or m_sha.group(1) != sha:
+            continue
+        m = re.search(r"traffic\[%s@%s\]:\s*([0-9.eE+]+)" % (re.escape(kernel),
+                                                           re.escape(workload_name)), text)
+        if m:
+            return float(m.group(1))
+    return None
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(value, world):
+    """Max of a float over ranks (the job time is the slowest rank's)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
+        else torch.device("cpu")
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# -------------------------------------------------------------- oracle leg
+
+def oracle_sample(case, psi0, seconds, max_steps=None):
+    """Time the FP64 CPU oracle stepping `case` from psi0 for about `seconds`
+    (at least 2 steps).  Returns (pt-steps/s, steps, threads)."""
+    import oracle
+    p = oracle.Params.make(case.shape, case.h, case.dt, *case.trap, case.g, case.mode)
+    psi = psi0.copy()
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.step(p, psi, 1)
+        steps += 1
+        if steps % 10 == 0:
+            oracle.observables(p, psi)
+        el = time.perf_counter() - t0
+        if (steps >= 2 and el >= seconds) or (max_steps and steps >= max_steps):
+            break
+    return case.points * steps / el, steps, oracle.get_threads()
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    case = workload()
+    p = oracle.Params.make(case.shape, case.h, case.dt, *case.trap, case.g, case.mode)
+    psi = oracle.seed(p)
+    for s in range(args.warmup):
+        oracle.step(p, psi, 1)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle.step(p, psi, 1)
+        if (s + 1) % 10 == 0:
+            oracle.observables(p, psi)
+    el = time.perf_counter() - t0
+    value = case.points * args.steps / el
+    cores = oracle.get_threads()
+    sample = ("FP64 CPU oracle (C, OpenMP over lines), %d^3 real time from the Gaussian "
+              "seed, one SSCN step per benchmark step, observables every 10th" % case.shape[0])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": config_dict(case, {"sscn_steps_per_bench_step": 1}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1206_1361_gb300 import gp
+    from paper_1206_1361_gb300.workloads import convergence_interval
+
+    case = workload()
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g0 = case.extra["g_ground"]
+    ctx = gp.gp_create(case.shape, case.h, case.dt, *case.trap, g0, gp.GP_IMAG,
+                       case.precision, stream)
+    try:
+        # ground state at g = 20 (untimed), |dmu| < 1e-6 between checks or the cap
+        gp.gp_load(ctx, None)
+        k = convergence_interval(case.dt)
+        mu_prev, dmu, prep = None, None, 0
+        while prep < args.prep_max_steps:
+            gp.gp_step(ctx, k)
+            prep += k
+            mu = gp.gp_observables(ctx)["mu"]
+            if mu_prev is not None:
+                dmu = abs(mu - mu_prev)
+                if dmu < 1e-6:
+                    break
+            mu_prev = mu
+        gp.gp_set_params(ctx, case.g, gp.GP_REAL)
+        obs0 = gp.gp_observables(ctx)
+
+        def bench_step():
+            gp.gp_step(ctx, STEPS_PER_BENCH_STEP)
+            return gp.gp_observables(ctx)
+
+        for _ in range(args.warmup):
+            bench_step()
+
+        dev_id = None
+        try:
+            dev_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+        except Exception:
+            pass
+        clocks = ClockSampler(dev_id)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        rms_t = []
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks.start()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            o = bench_step()
+            rms_t.append(o["rms_r"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        barrier(world)
+        ms = ev0.elapsed_time(ev1)
+        ms_max = reduce_max(ms, world)
+        obs_end = gp.gp_observables(ctx)
+        units = world * args.steps * STEPS_PER_BENCH_STEP * case.points
+        value = units / (ms_max / 1e3)
+        launches = args.steps * (STEPS_PER_BENCH_STEP * gp.gp_launches_per_step(ctx) + 2)
+
+        # per-kernel durations (events between launches on the context stream)
+        kt = gp.gp_time_kernels(ctx, 20)
+        sweeps = {k: v for k, v in kt.items() if k.startswith("sweep") and v > 0}
+        dom = max(sweeps, key=sweeps.get)
+        flops = FLOPS_PER_POINT[gp.GP_REAL][dom] * case.points
+        achieved_tf = flops / (sweeps[dom] * 1e-3) / 1e12
+        peaks = measured_peaks()
+        hbm_peak = peaks.get("hbm_gbs")
+        hbm_src = "measured" if hbm_peak else "fallback"
+        hbm_peak = hbm_peak or FALLBACK_HBM_GBS
+        sweep_bytes = SWEEP_BYTES_PER_POINT[case.precision] * case.points
+        hbm_achieved = sweep_bytes / (sweeps[dom] * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                    "traffic": profiled_traffic(dom, case.name), "kernel": dom,
+                    "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+                    "flops_per_point": FLOPS_PER_POINT[gp.GP_REAL][dom],
+                    "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": hbm_achieved / hbm_peak, "peak_source": hbm_src,
+                            "bytes_per_point": SWEEP_BYTES_PER_POINT[case.precision]},
+                    "kernel_ms": {k: round(v, 5) for k, v in kt.items()}}
+        roofline["step_hbm_frac"] = (3 * sweep_bytes / 1e9) / (
+            sum(sweeps.values()) * 1e-3) / hbm_peak
+
+        # end to end through the C ABI with host buffers: every step loads psi
+        # from pinned host memory and reads the observables back
+        host = torch.empty(case.points, dtype=torch.complex128, pin_memory=True)
+        gp.gp_store(ctx, host)
+        e2e_steps = max(3, min(args.steps, 10))
+        bench_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            gp.gp_load(ctx, host)
+            bench_step()
+        e2e_s = time.perf_counter() - t0
+        e2e_s = reduce_max(e2e_s, world)
+        e2e_value = world * e2e_steps * STEPS_PER_BENCH_STEP * case.points / e2e_s
+        e2e = {"value": e2e_value, "unit": UNIT,
+               "h2d_bytes_per_step": case.points * 16,
+               "d2h_bytes_per_step": 9 * 8}
+
+        cpu = None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            psi0 = host.numpy().reshape(case.shape[::-1]).copy()
+            v, n, cores = oracle_sample(case, psi0, args.cpu_seconds)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "FP64 CPU oracle, %d SSCN steps of the same 256^3 real-time "
+                             "state, observables every 10th" % n}
+
+        extra = {"prep_imag_steps": prep, "prep_dmu": dmu,
+                 "norm_drift": abs(obs_end["norm"] / obs0["norm"] - 1),
+                 "rms_r_range": [min(rms_t), max(rms_t)] if rms_t else None,
+                 "parallelism": "replicas" if world > 1 else "single",
+                 "kernel_source_sha": kernel_source_sha()}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": config_dict(case, extra),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+    finally:
+        gp.gp_destroy(ctx)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    return 0
+
+
+def run_probe(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1206_1361_gb300 import gp
+    case = workload()
+    with gp.Solver(case.shape, case.h, case.dt, *case.trap, case.g, gp.GP_REAL,
+                   case.precision) as s:
+        s.load(None).step(args.probe).sync()
+    torch.cuda.synchronize()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.probe:
+        return run_probe(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

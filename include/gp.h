@@ -134,6 +134,22 @@ int gp_step(gp_ctx *ctx, int64_t n);
  */
 int gp_observables(gp_ctx *ctx, gp_obs *out);
 
+/*
+ * Per-kernel timing: run `steps` >= 1 SSCN steps without graph replay, with a
+ * CUDA event on the context's stream before the first kernel of each step and
+ * after each kernel, then one observables pass bracketed the same way;
+ * synchronises.  ms_out[0 .. 4] receive mean milliseconds per launch of:
+ * 0 the x sweep (with calcnu fused), 1 the y sweep, 2 the z sweep (0 in 2D),
+ * 3 the norm finish (0 in real time), 4 the observables pass (calcmuen,
+ * calcrms: kernel, finish and the 72-byte copy out).  n_out >= 5; extra
+ * entries are zeroed.  The steps advance psi exactly like gp_step.
+ */
+int gp_time_kernels(gp_ctx *ctx, int64_t steps, double *ms_out, int n_out);
+
+/* Number of kernel launches one SSCN step enqueues (sweeps plus, in
+ * imaginary time, the norm finish); gp_observables adds 2. */
+int gp_launches_per_step(gp_ctx *ctx, int *kernels);
+
 /* Wait for all work enqueued on the context and report device errors. */
 int gp_sync(gp_ctx *ctx);
 

@@ -28,8 +28,8 @@ struct gp_ctx {
 
     void *psi = nullptr, *work = nullptr;
     AxisTables ax[2][3];            // [mode][axis]
-    double *tv[3]{};                // dt * w_k^2 x^2 / 2 per axis (FP64)
-    float *tv32[3]{};
+    double2 *ph[2][3]{};            // [mode][axis] exp(-tau w_k^2 x^2 / 2)
+    float2 *ph32[2][3]{};
     double *partials = nullptr;     // norm partials, >= max sweep blocks
     int partial_cap = 0;
     double *obs_partials = nullptr; // kReduceBlocks * kObsWidth
@@ -150,17 +150,21 @@ int upload_tables(gp_ctx *c)
             GP_CK(c, cudaMemcpy(a.mult32, mult32.data(), m * sizeof(float2), cudaMemcpyHostToDevice));
         }
     }
-    for (int k = 0; k < 3; ++k) {
-        const int n = edge(c->grid, k);
-        std::vector<double> t(n);
-        std::vector<float> t32(n);
-        for (int i = 0; i < n; ++i) {
-            const double x = coord(n, c->h[k], i);
-            t[i] = c->dt * 0.5 * c->w[k] * c->w[k] * x * x;
-            t32[i] = (float)t[i];
+    for (int mode = 0; mode < 2; ++mode) {
+        for (int k = 0; k < 3; ++k) {
+            const int n = edge(c->grid, k);
+            std::vector<double2> t(n);
+            std::vector<float2> t32(n);
+            for (int i = 0; i < n; ++i) {
+                const double x = coord(n, c->h[k], i);
+                const double th = c->dt * 0.5 * c->w[k] * c->w[k] * x * x;
+                t[i] = mode == 0 ? make_double2(std::exp(-th), 0.0)
+                                 : make_double2(std::cos(th), -std::sin(th));
+                t32[i] = make_float2((float)t[i].x, (float)t[i].y);
+            }
+            GP_CK(c, cudaMemcpy(c->ph[mode][k], t.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+            GP_CK(c, cudaMemcpy(c->ph32[mode][k], t32.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
         }
-        GP_CK(c, cudaMemcpy(c->tv[k], t.data(), n * sizeof(double), cudaMemcpyHostToDevice));
-        GP_CK(c, cudaMemcpy(c->tv32[k], t32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
     }
     return GP_OK;
 }
@@ -171,7 +175,7 @@ size_t footprint_bytes(const gp_grid &g, int prec)
     size_t tables = 0;
     for (int k = 0; k < 3; ++k) {
         const size_t n = edge(g, k);
-        tables += 2 * 2 * n * (sizeof(double2) + sizeof(float2)) + n * (sizeof(double) + sizeof(float));
+        tables += 2 * 2 * n * (sizeof(double2) + sizeof(float2)) + 2 * n * (sizeof(double2) + sizeof(float2));
     }
     int blocks = 0;
     for (int k = 0; k < naxes(g); ++k) blocks = std::max(blocks, gp::sweep_blocks(geom(g, k)));
@@ -190,7 +194,8 @@ void release(gp_ctx *c)
     fr(c->work);
     for (auto &row : c->ax)
         for (auto &a : row) { fr(a.cp64); fr(a.mult64); fr(a.cp32); fr(a.mult32); }
-    for (int k = 0; k < 3; ++k) { fr(c->tv[k]); fr(c->tv32[k]); }
+    for (int mode = 0; mode < 2; ++mode)
+        for (int k = 0; k < 3; ++k) { fr(c->ph[mode][k]); fr(c->ph32[mode][k]); }
     fr(c->partials);
     fr(c->obs_partials);
     fr(c->sums);
@@ -202,38 +207,52 @@ void release(gp_ctx *c)
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
-// Enqueue one SSCN step.
-int enqueue_step(gp_ctx *c)
+// Enqueue one SSCN step.  With ev != nullptr, record ev[0] before the first
+// kernel and ev[1 + k] after kernel slot k (x, y, z sweep, norm finish); slots
+// a step does not launch get their event recorded back to back.
+int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
 {
     const int mode = c->mode, prec = c->prec;
     const bool three_d = c->grid.nz > 1;
     Partials part{c->partials, 1};
     const Partials *norm_x = nullptr;
     gp::NonlinArgs nl;
-    nl.tvx = c->tv[0];
-    nl.tvy = c->tv[1];
-    nl.tvz = c->tv[2];
-    nl.tvx32 = c->tv32[0];
-    nl.tvy32 = c->tv32[1];
-    nl.tvz32 = c->tv32[2];
+    nl.px = c->ph[mode][0];
+    nl.py = c->ph[mode][1];
+    nl.pz = c->ph[mode][2];
+    nl.px32 = c->ph32[mode][0];
+    nl.py32 = c->ph32[mode][1];
+    nl.pz32 = c->ph32[mode][2];
     nl.dtg = c->dt * c->g;
     nl.scale = c->scale;
     const SweepGeom gx = geom(c->grid, 0), gy = geom(c->grid, 1), gz = geom(c->grid, 2);
+    auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], c->stream) : cudaSuccess; };
+    GP_CK(c, mark(0));
     GP_CK(c, gp::launch_sweep_x(prec, mode, c->psi, c->work, c->ax[mode][0], gx, nl,
                                 c->grid.ny, c->grid.nz, norm_x, c->stream));
+    GP_CK(c, mark(1));
     const bool imag = mode == GP_IMAG;
     GP_CK(c, gp::launch_sweep_yz(prec, mode, c->psi, c->work, c->ax[mode][1], gy,
                                  (imag && !three_d) ? &part : nullptr, c->stream));
+    GP_CK(c, mark(2));
     int last_blocks = gp::sweep_blocks(gy);
     if (three_d) {
         GP_CK(c, gp::launch_sweep_yz(prec, mode, c->psi, c->work, c->ax[mode][2], gz,
                                      imag ? &part : nullptr, c->stream));
         last_blocks = gp::sweep_blocks(gz);
     }
+    GP_CK(c, mark(3));
     if (imag)
         GP_CK(c, gp::launch_norm_finish(c->partials, last_blocks, cell_volume(c), c->scale,
                                         c->norm_dev, c->err_dev, c->stream));
+    GP_CK(c, mark(4));
     return GP_OK;
+}
+
+// Kernel launches per step (for launch accounting).
+int kernels_per_step(const gp_ctx *c)
+{
+    return (c->grid.nz > 1 ? 3 : 2) + (c->mode == GP_IMAG ? 1 : 0);
 }
 
 void drop_graph(gp_ctx *c)
@@ -276,6 +295,25 @@ int materialize_scale(gp_ctx *c)
     if (!c->scale_pending) return GP_OK;
     GP_CK(c, gp::launch_apply_scale(c->prec, c->psi, points(c->grid), c->scale, c->stream));
     c->scale_pending = false;
+    return GP_OK;
+}
+
+// Observables pass and finish, then the 9 sums to pinned host memory.
+int enqueue_observables(gp_ctx *c)
+{
+    gp::ObsArgs a{};
+    a.nx = c->grid.nx;
+    a.ny = c->grid.ny;
+    a.nz = c->grid.nz;
+    for (int k = 0; k < 3; ++k) {
+        a.h[k] = c->h[k];
+        a.w2[k] = c->w[k] * c->w[k];
+    }
+    a.scale = c->scale;
+    GP_CK(c, gp::launch_observables(c->prec, c->psi, a, c->obs_partials, gp::kReduceBlocks,
+                                    c->sums, c->stream));
+    GP_CK(c, cudaMemcpyAsync(c->host_sums, c->sums, gp::kObsWidth * sizeof(double),
+                             cudaMemcpyDeviceToHost, c->stream));
     return GP_OK;
 }
 
@@ -359,11 +397,12 @@ int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, 
             if ((rc = alloc(c, (void **)&a.cp32, m * sizeof(float2)))) return bail(rc);
             if ((rc = alloc(c, (void **)&a.mult32, m * sizeof(float2)))) return bail(rc);
         }
-    for (int k = 0; k < 3; ++k) {
-        const size_t n = edge(c->grid, k);
-        if ((rc = alloc(c, (void **)&c->tv[k], n * sizeof(double)))) return bail(rc);
-        if ((rc = alloc(c, (void **)&c->tv32[k], n * sizeof(float)))) return bail(rc);
-    }
+    for (int mode_i = 0; mode_i < 2; ++mode_i)
+        for (int k = 0; k < 3; ++k) {
+            const size_t n = edge(c->grid, k);
+            if ((rc = alloc(c, (void **)&c->ph[mode_i][k], n * sizeof(double2)))) return bail(rc);
+            if ((rc = alloc(c, (void **)&c->ph32[mode_i][k], n * sizeof(float2)))) return bail(rc);
+        }
     int blocks = gp::kReduceBlocks;
     for (int k = 0; k < naxes(c->grid); ++k) blocks = std::max(blocks, gp::sweep_blocks(geom(c->grid, k)));
     c->partial_cap = blocks;
@@ -471,19 +510,8 @@ int gp_step(gp_ctx *c, int64_t n)
 int gp_observables(gp_ctx *c, gp_obs *o)
 {
     if (!c || !o) return fail(c, GP_EINVAL, "gp_observables: null argument");
-    gp::ObsArgs a{};
-    a.nx = c->grid.nx;
-    a.ny = c->grid.ny;
-    a.nz = c->grid.nz;
-    for (int k = 0; k < 3; ++k) {
-        a.h[k] = c->h[k];
-        a.w2[k] = c->w[k] * c->w[k];
-    }
-    a.scale = c->scale;
-    GP_CK(c, gp::launch_observables(c->prec, c->psi, a, c->obs_partials, gp::kReduceBlocks,
-                                    c->sums, c->stream));
-    GP_CK(c, cudaMemcpyAsync(c->host_sums, c->sums, gp::kObsWidth * sizeof(double),
-                             cudaMemcpyDeviceToHost, c->stream));
+    int rc0 = enqueue_observables(c);
+    if (rc0) return rc0;
     int rc = read_errors(c);
     const double *s = c->host_sums;
     const double w = cell_volume(c);
@@ -503,6 +531,51 @@ int gp_observables(gp_ctx *c, gp_obs *o)
     const double v[7] = {o->norm, o->mu, o->energy, o->rms_x, o->rms_y, o->rms_z, o->rms_r};
     for (double x : v)
         if (!std::isfinite(x)) return fail(c, GP_ENONFINITE, "gp_observables: non-finite result");
+    return GP_OK;
+}
+
+int gp_time_kernels(gp_ctx *c, int64_t steps, double *ms_out, int n_out)
+{
+    if (!c || !ms_out || n_out < 5 || steps < 1)
+        return fail(c, GP_EINVAL, "gp_time_kernels: need steps >= 1 and n_out >= 5");
+    cudaEvent_t ev[5];
+    for (auto &e : ev) GP_CK(c, cudaEventCreate(&e));
+    double acc[4] = {0, 0, 0, 0};
+    int rc = GP_OK;
+    for (int64_t s = 0; s < steps && rc == GP_OK; ++s) {
+        rc = enqueue_step(c, ev);
+        if (rc) break;
+        cudaError_t e = cudaEventSynchronize(ev[4]);
+        if (e != cudaSuccess) { rc = cuda_fail(c, e, "cudaEventSynchronize"); break; }
+        for (int k = 0; k < 4; ++k) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            acc[k] += ms;
+        }
+    }
+    if (rc == GP_OK) {
+        c->step += steps;
+        if (c->mode == GP_IMAG) c->scale_pending = true;
+        // one observables pass: the kernel, then its fixed-order finish
+        cudaEvent_t e0 = ev[0], e1 = ev[1];
+        cudaEventRecord(e0, c->stream);
+        rc = enqueue_observables(c);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        for (int k = 0; k < 4; ++k) ms_out[k] = acc[k] / (double)steps;
+        ms_out[4] = ms;
+        for (int k = 5; k < n_out; ++k) ms_out[k] = 0.0;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    return rc;
+}
+
+int gp_launches_per_step(gp_ctx *c, int *kernels)
+{
+    if (!c || !kernels) return fail(c, GP_EINVAL, "gp_launches_per_step: null argument");
+    *kernels = kernels_per_step(c);
     return GP_OK;
 }
 

@@ -27,11 +27,14 @@ struct SweepGeom {
     long long stride_a, stride_b, pstride;
 };
 
-// Fused potential / nonlinearity data for the x sweep: theta = tv_x[i] +
-// tv_y[j] + tv_z[k] + dtg |psi|^2 with tv_k = dt * omega_k^2 x^2 / 2.
+// Fused potential / nonlinearity data for the x sweep.  V is separable, so
+// exp(-tau V) = P_x[i] P_y[j] P_z[k] with per-axis factor tables
+// P_k[i] = exp(-tau omega_k^2 x_i^2 / 2) (tau = dt: real factors stored as
+// (f, 0); tau = i dt: unit complex numbers), computed on the host in FP64.
+// Only the nonlinear phase dt g |psi|^2 is evaluated per point.
 struct NonlinArgs {
-    const double *tvx = nullptr, *tvy = nullptr, *tvz = nullptr;  // FP64 tables
-    const float *tvx32 = nullptr, *tvy32 = nullptr, *tvz32 = nullptr;
+    const double2 *px = nullptr, *py = nullptr, *pz = nullptr;   // FP64 tables
+    const float2 *px32 = nullptr, *py32 = nullptr, *pz32 = nullptr;
     double dtg = 0;
     const double *scale = nullptr;   // pending imaginary-time scale (device)
 };

@@ -8,7 +8,7 @@
 // contiguous warp-wide access; the x sweep walks contiguous lines per thread
 // and leans on L1.  The Thomas elimination is exact: forward elimination
 // writes d'_i to a scratch buffer laid out like psi, back substitution reads
-// it back in reverse while the line is still cache-resident.
+// it back in reverse.
 //
 // Reductions (norm partials, observables) accumulate in FP64 in a fixed order:
 // per thread sequentially, then a warp-shuffle tree, then per block, so a
@@ -74,6 +74,14 @@ __device__ double block_sum(double v, double *red /* >= 32 doubles */)
 }
 
 // ------------------------------------------------------------------ sweeps
+//
+// Each Crank-Nicolson line update (I - kappa L) u = (I + kappa L) psi is done
+// as u = 2 v - psi with (I - kappa L) v = psi, using I + kappa L =
+// 2 I - (I - kappa L): the same solution without forming the right-hand side
+// stencil, which saves a third of the FP64 instructions per point (the FP64
+// pipe bounds these kernels on GB300).  Forward elimination:
+// d'_i = (psi_i + kappa d'_{i-1}) mult_i into the scratch buffer; back
+// substitution: v_i = d'_i - c'_i v_{i+1}, u_i = 2 v_i - psi_i.
 
 // Crank-Nicolson coefficients specialised by mode: in imaginary time kappa
 // and the tables are real; in real time kappa = i kim and the tables complex.
@@ -81,74 +89,94 @@ template <typename T, int MODE> struct Cn {
     using C = typename CT<T>::c;
     T k;                                   // kre (MODE 0) or kim (MODE 1)
 
-    // b = (1 - 2 kappa) mid + kappa (left + right)
-    __device__ __forceinline__ C rhs(C l, C m, C r) const
+    // (p + kappa d) * f
+    __device__ __forceinline__ C fwd(C p, C d, C f) const
     {
-        if (MODE == 0) {
-            const T a = (T)1 - (T)2 * k;
-            return mk<T>(fma(k, l.x + r.x, a * m.x), fma(k, l.y + r.y, a * m.y));
-        } else {
-            // (1 - 2 i k) m + i k (l + r) = m + i k (l + r - 2 m)
-            const T sx = l.x + r.x - (T)2 * m.x, sy = l.y + r.y - (T)2 * m.y;
-            return mk<T>(fma(-k, sy, m.x), fma(k, sx, m.y));
-        }
+        if (MODE == 0) return mk<T>(fma(k, d.x, p.x) * f.x, fma(k, d.y, p.y) * f.x);
+        const T tx = fma(-k, d.y, p.x), ty = fma(k, d.x, p.y);
+        return mk<T>(fma(tx, f.x, -ty * f.y), fma(tx, f.y, ty * f.x));
     }
-    // b + kappa d
-    __device__ __forceinline__ C add_kd(C b, C d) const
+    // d - c v
+    __device__ __forceinline__ C back(C d, C c, C v) const
     {
-        if (MODE == 0) return mk<T>(fma(k, d.x, b.x), fma(k, d.y, b.y));
-        return mk<T>(fma(-k, d.y, b.x), fma(k, d.x, b.y));
+        if (MODE == 0) return mk<T>(fma(-c.x, v.x, d.x), fma(-c.x, v.y, d.y));
+        return mk<T>(fma(-c.x, v.x, fma(c.y, v.y, d.x)), fma(-c.x, v.y, fma(-c.y, v.x, d.y)));
     }
-    // t * mult
-    __device__ __forceinline__ C mul(C t, C f) const
+    // 2 v - p
+    static __device__ __forceinline__ C out(C v, C p)
     {
-        if (MODE == 0) return mk<T>(t.x * f.x, t.y * f.x);
-        return mk<T>(fma(t.x, f.x, -t.y * f.y), fma(t.x, f.y, t.y * f.x));
-    }
-    // d - c' u
-    __device__ __forceinline__ C back(C d, C c, C u) const
-    {
-        if (MODE == 0) return mk<T>(fma(-c.x, u.x, d.x), fma(-c.x, u.y, d.y));
-        return mk<T>(d.x - fma(c.x, u.x, -c.y * u.y), d.y - fma(c.x, u.y, c.y * u.x));
+        return mk<T>(fma((T)2, v.x, -p.x), fma((T)2, v.y, -p.y));
     }
 };
 
-// The potential / nonlinearity factor at one point (calcnu):
-// imaginary time psi * s * exp(-theta), real time psi * exp(-i theta),
-// theta = tv_x[i] + tv_yz + dtg |s psi|^2.
+// exp(-i a) and exp(-a) for the nonlinear phase a = dt g |psi|^2: Taylor
+// polynomials for |a| <= 1/16 (truncation below 3e-19 relative, under half an
+// FP64 ulp), the library functions beyond.
+__device__ __forceinline__ void expmi_small(double a, double &c, double &s)
+{
+    if (fabs(a) <= 0.0625) {
+        const double t = a * a;
+        c = fma(t, fma(t, fma(t, fma(t, 1.0 / 40320, -1.0 / 720), 1.0 / 24), -0.5), 1.0);
+        s = a * fma(t, fma(t, fma(t, fma(t, 1.0 / 362880, -1.0 / 5040), 1.0 / 120), -1.0 / 6), 1.0);
+    } else {
+        sincos(a, &s, &c);
+    }
+}
+
+__device__ __forceinline__ double expm_small(double a)
+{
+    if (fabs(a) <= 0.0625) {
+        double r = -1.0 / 362880;
+        r = fma(r, a, 1.0 / 40320);
+        r = fma(r, a, -1.0 / 5040);
+        r = fma(r, a, 1.0 / 720);
+        r = fma(r, a, -1.0 / 120);
+        r = fma(r, a, 1.0 / 24);
+        r = fma(r, a, -1.0 / 6);
+        r = fma(r, a, 0.5);
+        r = fma(r, a, -1.0);
+        return fma(r, a, 1.0);
+    }
+    return exp(-a);
+}
+
+__device__ __forceinline__ void expmi_small(float a, float &c, float &s) { sincosf(a, &s, &c); }
+__device__ __forceinline__ float expm_small(float a) { return expf(-a); }
+
+// calcnu at one point: imaginary time s P exp(-dt g |s psi|^2) psi (P real),
+// real time P exp(-i dt g |psi|^2) psi (P unit complex), with P = P_x[i] P_yz.
 template <typename T, int MODE> struct Nonlin {
     using C = typename CT<T>::c;
-    const T *tvx;
-    T tvyz, dtg, s;
+    const C *px;
+    C pyz;          // P_y[j] P_z[k] (times s in imaginary time)
+    T a_coef;       // dt g (times s^2 in imaginary time)
 
     __device__ __forceinline__ C apply(C v, int i) const
     {
+        const C q = px[i];
+        const T a = a_coef * abs2<T>(v);
         if (MODE == 0) {
-            v.x *= s;
-            v.y *= s;
-        }
-        const T theta = tvx[i] + tvyz + dtg * abs2<T>(v);
-        if (MODE == 0) {
-            const T f = exp(-theta);
+            const T f = q.x * pyz.x * expm_small(a);
             return mk<T>(v.x * f, v.y * f);
         } else {
-            T sn, cs;
-            if constexpr (sizeof(T) == 8) sincos(theta, &sn, &cs);
-            else sincosf(theta, &sn, &cs);
-            // (cs - i sn) (v.x + i v.y)
-            return mk<T>(fma(cs, v.x, sn * v.y), fma(cs, v.y, -sn * v.x));
+            T cs, sn;
+            expmi_small(a, cs, sn);
+            // P = q * pyz; w = (cs - i sn) v; result P w
+            const T prx = fma(q.x, pyz.x, -q.y * pyz.y), pry = fma(q.x, pyz.y, q.y * pyz.x);
+            const T wx = fma(cs, v.x, sn * v.y), wy = fma(cs, v.y, -sn * v.x);
+            return mk<T>(fma(prx, wx, -pry * wy), fma(prx, wy, pry * wx));
         }
     }
 };
 
 template <typename T, int MODE, bool NL, bool NORM>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(64)
 k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ work,
         const typename CT<T>::c *__restrict__ cp,
         const typename CT<T>::c *__restrict__ mult, SweepGeom g, T kappa,
-        const T *__restrict__ tvx, const T *__restrict__ tvy,
-        const T *__restrict__ tvz, T dtg, const double *__restrict__ scale,
-        double *__restrict__ partials)
+        const typename CT<T>::c *__restrict__ px, const typename CT<T>::c *__restrict__ py,
+        const typename CT<T>::c *__restrict__ pz, double dtg,
+        const double *__restrict__ scale, double *__restrict__ partials)
 {
     using C = typename CT<T>::c;
     __shared__ double red[32];
@@ -165,39 +193,39 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
         Nonlin<T, MODE> nl{};
         if (NL) {
             // x sweep: a is the y index, b the z index
-            nl.tvx = tvx;
-            nl.tvyz = tvy[a] + (tvz ? tvz[b] : (T)0);
-            nl.dtg = dtg;
-            nl.s = (MODE == 0) ? (T)(*scale) : (T)1;
-        }
-        const C zero = mk<T>((T)0, (T)0);
-        C left = zero;
-        C mid = line[s];
-        if (NL) mid = nl.apply(mid, 1);
-        C right = zero;
-        if (m >= 2) {
-            right = line[2 * s];
-            if (NL) right = nl.apply(right, 2);
-        }
-        C d = zero;
-        for (int i = 1; i <= m; ++i) {
-            const C rb = cn.rhs(left, mid, right);
-            d = cn.mul(cn.add_kd(rb, d), mult[i - 1]);
-            wl[i * s] = d;
-            left = mid;
-            mid = right;
-            if (i + 2 <= m) {
-                right = line[(long long)(i + 2) * s];
-                if (NL) right = nl.apply(right, i + 2);
+            const C qy = py[a], qz = pz[b];
+            nl.px = px;
+            if (MODE == 0) {
+                const double sc = *scale;
+                nl.pyz = mk<T>((T)(sc * (double)qy.x * (double)qz.x), (T)0);
+                nl.a_coef = (T)(dtg * sc * sc);
             } else {
-                right = zero;
+                nl.pyz = mk<T>(qy.x * qz.x - qy.y * qz.y, qy.x * qz.y + qy.y * qz.x);
+                nl.a_coef = (T)dtg;
             }
         }
-        C u = d;
+        C d = mk<T>((T)0, (T)0);
+        C p = d;
+        C nxt = line[s];
+#pragma unroll 2
+        for (int i = 1; i <= m; ++i) {
+            p = nxt;
+            if (i < m) nxt = line[(long long)(i + 1) * s];
+            if (NL) {
+                p = nl.apply(p, i);
+                line[(long long)i * s] = p;
+            }
+            d = cn.fwd(p, d, mult[i - 1]);
+            wl[(long long)i * s] = d;
+        }
+        C v = d;
+        C u = Cn<T, MODE>::out(v, p);
         line[(long long)m * s] = u;
         if (NORM) nacc += abs2d<T>(u);
+#pragma unroll 2
         for (int i = m - 1; i >= 1; --i) {
-            u = cn.back(wl[(long long)i * s], cp[i - 1], u);
+            v = cn.back(wl[(long long)i * s], cp[i - 1], v);
+            u = Cn<T, MODE>::out(v, line[(long long)i * s]);
             line[(long long)i * s] = u;
             if (NORM) nacc += abs2d<T>(u);
         }
@@ -208,7 +236,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
     }
 }
 
-constexpr int kSweepThreads = 128;
+constexpr int kSweepThreads = 64;
 
 template <typename T, int MODE, bool NL, bool NORM>
 cudaError_t sweep_launch(void *psi, void *work, const AxisTables &ax,
@@ -217,21 +245,20 @@ cudaError_t sweep_launch(void *psi, void *work, const AxisTables &ax,
 {
     using C = typename CT<T>::c;
     dim3 grid((g.lines_a + kSweepThreads - 1) / kSweepThreads, g.lines_b);
-    const C *cp, *mult;
-    const T *tvx = nullptr, *tvy = nullptr, *tvz = nullptr;
+    const C *cp, *mult, *px = nullptr, *py = nullptr, *pz = nullptr;
     T kappa = (T)(MODE == 0 ? ax.kre : ax.kim);
     if constexpr (sizeof(T) == 8) {
         cp = reinterpret_cast<const C *>(ax.cp64);
         mult = reinterpret_cast<const C *>(ax.mult64);
-        if (nl) { tvx = (const T *)nl->tvx; tvy = (const T *)nl->tvy; tvz = (const T *)nl->tvz; }
+        if (nl) { px = (const C *)nl->px; py = (const C *)nl->py; pz = (const C *)nl->pz; }
     } else {
         cp = reinterpret_cast<const C *>(ax.cp32);
         mult = reinterpret_cast<const C *>(ax.mult32);
-        if (nl) { tvx = (const T *)nl->tvx32; tvy = (const T *)nl->tvy32; tvz = (const T *)nl->tvz32; }
+        if (nl) { px = (const C *)nl->px32; py = (const C *)nl->py32; pz = (const C *)nl->pz32; }
     }
     k_sweep<T, MODE, NL, NORM><<<grid, kSweepThreads, 0, st>>>(
         reinterpret_cast<C *>(psi), reinterpret_cast<C *>(work), cp, mult, g, kappa,
-        tvx, tvy, tvz, nl ? (T)nl->dtg : (T)0, nl ? nl->scale : nullptr,
+        px, py, pz, nl ? nl->dtg : 0.0, nl ? nl->scale : nullptr,
         norm_out ? norm_out->buf : nullptr);
     return cudaGetLastError();
 }

@@ -59,6 +59,8 @@ SIGNATURES = {
     "gp_step": (_int, [_vp, _i64]),
     "gp_observables": (_int, [_vp, ctypes.POINTER(gp_obs)]),
     "gp_sync": (_int, [_vp]),
+    "gp_time_kernels": (_int, [_vp, _i64, ctypes.POINTER(ctypes.c_double), _int]),
+    "gp_launches_per_step": (_int, [_vp, ctypes.POINTER(_int)]),
     "gp_device_psi": (_int, [_vp, ctypes.POINTER(_vp)]),
     "gp_footprint": (_int, [ctypes.POINTER(gp_grid), _int, ctypes.POINTER(ctypes.c_size_t)]),
     "gp_last_error": (ctypes.c_char_p, [_vp]),
@@ -167,6 +169,22 @@ def gp_observables(ctx):
     o = gp_obs()
     _err(ctx, load_library().gp_observables(ctx, ctypes.byref(o)))
     return o.as_dict()
+
+
+KERNEL_SLOTS = ("sweep_x", "sweep_y", "sweep_z", "norm_finish", "observables")
+
+
+def gp_time_kernels(ctx, steps):
+    """Mean ms per launch of each kernel slot (dict keyed by KERNEL_SLOTS)."""
+    out = (ctypes.c_double * 8)()
+    _err(ctx, load_library().gp_time_kernels(ctx, int(steps), out, 8))
+    return dict(zip(KERNEL_SLOTS, list(out)[:5]))
+
+
+def gp_launches_per_step(ctx):
+    k = ctypes.c_int()
+    _err(ctx, load_library().gp_launches_per_step(ctx, ctypes.byref(k)))
+    return k.value
 
 
 def gp_sync(ctx):
