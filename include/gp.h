@@ -160,6 +160,31 @@ int gp_sync(gp_ctx *ctx);
  */
 int gp_device_psi(gp_ctx *ctx, void **dev_ptr);
 
+/*
+ * One Crank-Nicolson sweep along `axis` (0 x, 1 y, 2 z; 3D only for z),
+ * (I - kappa L) u = (I + kappa L) psi on every line with kappa = dt / (4 h^2)
+ * (GP_IMAG) or i dt / (4 h^2) (GP_REAL), in place on psi_device: a
+ * caller-owned device buffer of nx*ny*nz interleaved complex values of the
+ * given precision, laid out like a context's psi.  Enqueued on cuda_stream
+ * (NULL: the legacy default stream); returns without waiting.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- code inside another framework's operator
+ * that may only use the buffers it was given, or loops that cannot afford the
+ * device-wide synchronisation of cudaMalloc / cudaFree.  It calls no device
+ * allocator: the sweep's scratch and tables live in a static device array of
+ * 16 MiB (+384 KiB of tables) that every GPU loading libgp holds until exit,
+ * so grids above 1048576 complex128 or 2097152 complex64 points are rejected
+ * with GP_EINVAL.  The first call on each device looks up the array's device
+ * address (make that first call before any stream capture).  All calls share
+ * the one array, which keeps the last call's contents: calls whose work
+ * overlaps on the GPU race with each other.  Errors: GP_EINVAL for bad
+ * arguments, GP_ECUDA if a CUDA call fails; the message is in
+ * gp_last_error(NULL).
+ */
+int gp_sweep_noalloc(void *psi_device, const gp_grid *grid, int axis, double h,
+                     double dt, int mode, int precision, void *cuda_stream);
+
 /* Bytes of device memory gp_create allocates for this grid and precision. */
 int gp_footprint(const gp_grid *grid, int precision, size_t *bytes);
 

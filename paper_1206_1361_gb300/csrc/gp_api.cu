@@ -327,6 +327,8 @@ int read_errors(gp_ctx *c)
 
 }  // namespace
 
+void gp::set_thread_error(const char *msg) { g_create_error = msg ? msg : ""; }
+
 // =================================================================== C ABI
 
 extern "C" {

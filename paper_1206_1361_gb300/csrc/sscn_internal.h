@@ -90,6 +90,9 @@ cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
                                double *partials, int blocks, double *sums,
                                cudaStream_t st);
 
+// Record msg as the message gp_last_error(NULL) returns in this thread.
+void set_thread_error(const char *msg);
+
 constexpr int kObsWidth = 9;
 constexpr int kReduceBlocks = 608;      // 4 x 152 SMs for grid-stride reductions
 

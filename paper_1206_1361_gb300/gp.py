@@ -63,6 +63,8 @@ SIGNATURES = {
     "gp_launches_per_step": (_int, [_vp, ctypes.POINTER(_int)]),
     "gp_device_psi": (_int, [_vp, ctypes.POINTER(_vp)]),
     "gp_footprint": (_int, [ctypes.POINTER(gp_grid), _int, ctypes.POINTER(ctypes.c_size_t)]),
+    "gp_sweep_noalloc": (_int, [_vp, ctypes.POINTER(gp_grid), _int, _dbl, _dbl, _int, _int,
+                                _vp]),
     "gp_last_error": (ctypes.c_char_p, [_vp]),
     "gp_destroy": (None, [_vp]),
 }
@@ -204,6 +206,22 @@ def gp_footprint(grid, precision=GP_C128):
     if rc != GP_OK:
         raise GPError(rc, load_library().gp_last_error(None).decode())
     return b.value
+
+
+def gp_sweep_noalloc(psi_device, grid, axis, h, dt, mode, precision, cuda_stream=None):
+    """One Crank-Nicolson sweep in place on a caller-owned device buffer (a
+    CUDA torch tensor or a device address), with no device allocation."""
+    if isinstance(psi_device, int):
+        addr = psi_device
+    else:
+        addr, _n, dev, _keep = _buffer(psi_device)
+        if not dev:
+            raise ValueError("gp_sweep_noalloc needs a device buffer")
+    gr = gp_grid(*[int(v) for v in grid])
+    rc = load_library().gp_sweep_noalloc(addr, ctypes.byref(gr), int(axis), float(h), float(dt),
+                                         int(mode), int(precision), _stream_handle(cuda_stream))
+    if rc != GP_OK:
+        raise GPError(rc, gp_last_error(None))
 
 
 def gp_last_error(ctx=None):
