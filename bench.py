@@ -151,13 +151,17 @@ def measured_peaks():
         return {}
 
 
+KERNEL_SOURCES = ("sscn_kernels.cu", "sscn_internal.h")
+
+
 def kernel_source_sha():
+    """Hash of the sources that define the sweep and observables kernels; a
+    committed ncu traffic figure is used only while it matches."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1206_1361_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(f.read())
+    for fn in KERNEL_SOURCES:
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -332,7 +336,8 @@ def run_ours(args):
         obs_end = gp.gp_observables(ctx)
         units = world * args.steps * STEPS_PER_BENCH_STEP * case.points
         value = units / (ms_max / 1e3)
-        launches = args.steps * (STEPS_PER_BENCH_STEP * gp.gp_launches_per_step(ctx) + 2)
+        per_step, per_obs = gp.gp_launches_per_step(ctx)
+        launches = args.steps * (STEPS_PER_BENCH_STEP * per_step + per_obs)
 
         # per-kernel durations (events between launches on the context stream)
         kt = gp.gp_time_kernels(ctx, 20)
@@ -414,6 +419,7 @@ def run_probe(args):
     with gp.Solver(case.shape, case.h, case.dt, *case.trap, case.g, gp.GP_REAL,
                    case.precision) as s:
         s.load(None).step(args.probe).sync()
+        s.observables()
     torch.cuda.synchronize()
     return 0
 

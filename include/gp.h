@@ -146,9 +146,10 @@ int gp_observables(gp_ctx *ctx, gp_obs *out);
  */
 int gp_time_kernels(gp_ctx *ctx, int64_t steps, double *ms_out, int n_out);
 
-/* Number of kernel launches one SSCN step enqueues (sweeps plus, in
- * imaginary time, the norm finish); gp_observables adds 2. */
-int gp_launches_per_step(gp_ctx *ctx, int *kernels);
+/* Kernel launches one SSCN step enqueues (the sweeps plus, in imaginary time,
+ * the norm finish) into *per_step, and those one gp_observables enqueues into
+ * *per_observables (either pointer may be NULL). */
+int gp_launches_per_step(gp_ctx *ctx, int *per_step, int *per_observables);
 
 /* Wait for all work enqueued on the context and report device errors. */
 int gp_sync(gp_ctx *ctx);

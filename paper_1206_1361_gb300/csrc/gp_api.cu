@@ -32,7 +32,8 @@ struct gp_ctx {
     float2 *ph32[2][3]{};
     double *partials = nullptr;     // norm partials, >= max sweep blocks
     int partial_cap = 0;
-    double *obs_partials = nullptr; // kReduceBlocks * kObsWidth
+    double *obs_partials = nullptr; // observables scratch (rows + finish stage)
+    double *obs_tab = nullptr;      // x^2 and w^2 x^2 / 2 per axis
     double *sums = nullptr;         // kObsWidth
     double *scale = nullptr;        // pending imaginary-time scale
     double *norm_dev = nullptr;     // last norm N
@@ -144,11 +145,23 @@ int upload_tables(gp_ctx *c)
                 cp32[i] = make_float2((float)cp[i].x, (float)cp[i].y);
                 mult32[i] = make_float2((float)mult[i].x, (float)mult[i].y);
             }
+            gp::set_mid(a, m, cp.data());
             GP_CK(c, cudaMemcpy(a.cp64, cp.data(), m * sizeof(double2), cudaMemcpyHostToDevice));
             GP_CK(c, cudaMemcpy(a.mult64, mult.data(), m * sizeof(double2), cudaMemcpyHostToDevice));
             GP_CK(c, cudaMemcpy(a.cp32, cp32.data(), m * sizeof(float2), cudaMemcpyHostToDevice));
             GP_CK(c, cudaMemcpy(a.mult32, mult32.data(), m * sizeof(float2), cudaMemcpyHostToDevice));
         }
+    }
+    {
+        std::vector<double> x2, v;
+        for (int k = 0; k < 3; ++k)
+            for (int i = 0; i < edge(c->grid, k); ++i) {
+                const double x = coord(edge(c->grid, k), c->h[k], i);
+                x2.push_back(x * x);
+                v.push_back(0.5 * c->w[k] * c->w[k] * x * x);
+            }
+        x2.insert(x2.end(), v.begin(), v.end());
+        GP_CK(c, cudaMemcpy(c->obs_tab, x2.data(), x2.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
     for (int mode = 0; mode < 2; ++mode) {
         for (int k = 0; k < 3; ++k) {
@@ -180,8 +193,13 @@ size_t footprint_bytes(const gp_grid &g, int prec)
     int blocks = 0;
     for (int k = 0; k < naxes(g); ++k) blocks = std::max(blocks, gp::sweep_blocks(geom(g, k)));
     blocks = std::max(blocks, gp::kReduceBlocks);
+    gp::ObsArgs oa{};
+    oa.nx = g.nx;
+    oa.ny = g.ny;
+    oa.nz = g.nz;
     const size_t red = (size_t)blocks * sizeof(double) +
-                       (size_t)gp::kReduceBlocks * gp::kObsWidth * sizeof(double) +
+                       (size_t)gp::obs_scratch_doubles(oa) * sizeof(double) +
+                       2 * (size_t)(g.nx + g.ny + g.nz) * sizeof(double) +
                        gp::kObsWidth * sizeof(double) + 2 * sizeof(double) + sizeof(int);
     return 2 * psi + tables + red;
 }
@@ -198,6 +216,7 @@ void release(gp_ctx *c)
         for (int k = 0; k < 3; ++k) { fr(c->ph[mode][k]); fr(c->ph32[mode][k]); }
     fr(c->partials);
     fr(c->obs_partials);
+    fr(c->obs_tab);
     fr(c->sums);
     fr(c->scale);
     fr(c->norm_dev);
@@ -298,20 +317,27 @@ int materialize_scale(gp_ctx *c)
     return GP_OK;
 }
 
-// Observables pass and finish, then the 9 sums to pinned host memory.
-int enqueue_observables(gp_ctx *c)
+gp::ObsArgs obs_args(const gp_ctx *c)
 {
     gp::ObsArgs a{};
     a.nx = c->grid.nx;
     a.ny = c->grid.ny;
     a.nz = c->grid.nz;
-    for (int k = 0; k < 3; ++k) {
-        a.h[k] = c->h[k];
-        a.w2[k] = c->w[k] * c->w[k];
-    }
+    a.x2 = c->obs_tab;
+    a.y2 = a.x2 + c->grid.nx;
+    a.z2 = a.y2 + c->grid.ny;
+    a.vx = a.z2 + c->grid.nz;
+    a.vy = a.vx + c->grid.nx;
+    a.vz = a.vy + c->grid.ny;
     a.scale = c->scale;
-    GP_CK(c, gp::launch_observables(c->prec, c->psi, a, c->obs_partials, gp::kReduceBlocks,
-                                    c->sums, c->stream));
+    return a;
+}
+
+// Observables pass and finish, then the 9 sums to pinned host memory.
+int enqueue_observables(gp_ctx *c)
+{
+    GP_CK(c, gp::launch_observables(c->prec, c->psi, obs_args(c), c->obs_partials, c->sums,
+                                    c->stream));
     GP_CK(c, cudaMemcpyAsync(c->host_sums, c->sums, gp::kObsWidth * sizeof(double),
                              cudaMemcpyDeviceToHost, c->stream));
     return GP_OK;
@@ -328,6 +354,18 @@ int read_errors(gp_ctx *c)
 }  // namespace
 
 void gp::set_thread_error(const char *msg) { g_create_error = msg ? msg : ""; }
+
+void gp::set_mid(AxisTables &a, int m, const double2 *cp)
+{
+    const std::complex<double> kappa(a.kre, a.kim);
+    const int k = (m + 1) / 2;
+    auto c = [&](int j) {   // c'_j, 1-based, c'_0 = 0
+        return j <= 0 ? std::complex<double>(0.0) : std::complex<double>(cp[j - 1].x, cp[j - 1].y);
+    };
+    const std::complex<double> f = 1.0 / (1.0 + 2.0 * kappa + kappa * (c(k - 1) + c(m - k)));
+    a.mid64 = make_double2(f.real(), f.imag());
+    a.mid32 = make_float2((float)f.real(), (float)f.imag());
+}
 
 // =================================================================== C ABI
 
@@ -409,7 +447,15 @@ int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, 
     for (int k = 0; k < naxes(c->grid); ++k) blocks = std::max(blocks, gp::sweep_blocks(geom(c->grid, k)));
     c->partial_cap = blocks;
     if ((rc = alloc(c, (void **)&c->partials, blocks * sizeof(double)))) return bail(rc);
-    if ((rc = alloc(c, (void **)&c->obs_partials, gp::kReduceBlocks * gp::kObsWidth * sizeof(double)))) return bail(rc);
+    {
+        gp::ObsArgs oa{};
+        oa.nx = grid->nx;
+        oa.ny = grid->ny;
+        oa.nz = grid->nz;
+        if ((rc = alloc(c, (void **)&c->obs_partials, gp::obs_scratch_doubles(oa) * sizeof(double)))) return bail(rc);
+        const int nt = grid->nx + grid->ny + grid->nz;
+        if ((rc = alloc(c, (void **)&c->obs_tab, 2 * nt * sizeof(double)))) return bail(rc);
+    }
     if ((rc = alloc(c, (void **)&c->sums, gp::kObsWidth * sizeof(double)))) return bail(rc);
     if ((rc = alloc(c, (void **)&c->scale, sizeof(double)))) return bail(rc);
     if ((rc = alloc(c, (void **)&c->norm_dev, sizeof(double)))) return bail(rc);
@@ -574,10 +620,11 @@ int gp_time_kernels(gp_ctx *c, int64_t steps, double *ms_out, int n_out)
     return rc;
 }
 
-int gp_launches_per_step(gp_ctx *c, int *kernels)
+int gp_launches_per_step(gp_ctx *c, int *per_step, int *per_observables)
 {
-    if (!c || !kernels) return fail(c, GP_EINVAL, "gp_launches_per_step: null argument");
-    *kernels = kernels_per_step(c);
+    if (!c) return fail(c, GP_EINVAL, "gp_launches_per_step: null context");
+    if (per_step) *per_step = kernels_per_step(c);
+    if (per_observables) *per_observables = 3;   // line pass + two finish passes
     return GP_OK;
 }
 

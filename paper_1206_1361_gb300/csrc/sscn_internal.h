@@ -11,12 +11,19 @@ namespace gp {
 // (m = n - 1 unknowns at indices 1 .. n-1), kappa = kre + i kim, and the
 // forward-elimination tables c'_i and mult_i (i = 1 .. m, stored 0-based) in
 // FP64, plus their FP32 roundings for the complex64 path.
+// mid is the middle-row multiplier of the two-ended elimination,
+// 1 / (1 + 2 kappa + kappa (c'_{k-1} + c'_{m-k})) with k = ceil(m / 2), c'_0 = 0.
 struct AxisTables {
     int n = 0;
     double h = 0, kre = 0, kim = 0;
     double2 *cp64 = nullptr, *mult64 = nullptr;   // device, m entries each
     float2 *cp32 = nullptr, *mult32 = nullptr;    // device, m entries each
+    double2 mid64{0, 0};
+    float2 mid32{0, 0};
 };
+
+// Fill a.mid64 / a.mid32 from the host copy of the c' table (m entries).
+void set_mid(AxisTables &a, int m, const double2 *cp_host);
 
 // One sweep launch: lines are indexed by (a, b), the line's first stored point
 // sits at a * stride_a + b * stride_b and its points are pstride apart.
@@ -79,16 +86,19 @@ cudaError_t launch_zero_boundary(int prec, void *psi, int nx, int ny, int nz,
 cudaError_t launch_norm_partials(int prec, const void *psi, long long count,
                                  const Partials &out, int blocks, cudaStream_t st);
 
-// Observables: 9 FP64 sums per block (S0, Sx, Sy, Sz, SV, S4, Kx, Ky, Kz) of
-// scale * psi, then a fixed-order finish into sums[9].
+// Observables: the 9 FP64 sums (S0, Sx, Sy, Sz, SV, S4, Kx, Ky, Kz) of
+// scale * psi, one partials row per x-line, then a fixed-order finish into
+// sums[9].  x2/y2/z2 hold x_i^2 per axis, vx/vy/vz the potential terms
+// omega_k^2 x_i^2 / 2 (device, FP64).
 struct ObsArgs {
     int nx, ny, nz;
-    double h[3], w2[3];    // spacings, squared trap frequencies
+    const double *x2, *y2, *z2, *vx, *vy, *vz;
     const double *scale;   // pending scale (device)
 };
+// Doubles of scratch launch_observables needs for this grid.
+long long obs_scratch_doubles(const ObsArgs &a);
 cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
-                               double *partials, int blocks, double *sums,
-                               cudaStream_t st);
+                               double *scratch, double *sums, cudaStream_t st);
 
 // Record msg as the message gp_last_error(NULL) returns in this thread.
 void set_thread_error(const char *msg);

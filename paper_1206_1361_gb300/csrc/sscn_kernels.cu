@@ -12,7 +12,8 @@
 //
 // Reductions (norm partials, observables) accumulate in FP64 in a fixed order:
 // per thread sequentially, then a warp-shuffle tree, then per block, so a
-// given launch shape always produces the same bits.
+// given launch shape always produces the same bits (the observables do not
+// depend on the launch shape at all: one partials row per grid line).
 
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -169,65 +170,106 @@ template <typename T, int MODE> struct Nonlin {
     }
 };
 
+// Two-ended elimination ("burn at both ends", a twisted factorisation): the
+// lane pair (l, l ^ 16) of a warp owns one line; the low lane eliminates from
+// the top (i = 1 .. k-1), the high lane from the bottom (i = m .. k+1) with the
+// mirrored tables (the matrix is symmetric Toeplitz, so the reversed system
+// has the same coefficients), they meet at the middle unknown k =
+// ceil(m / 2), and back-substitute outward.  Same FP64 work as one-sided
+// Thomas, twice the independent chains: 16 lines per warp.
+//   top:    d'_i = (psi_i + kappa d'_{i-1}) mult_i,      v_i = d'_i - c'_i v_{i+1}
+//   bottom: e_i  = (psi_i + kappa e_{i+1}) mult_{m+1-i}, v_i = e_i - c'_{m+1-i} v_{i-1}
+//   middle: v_k  = (psi_k + kappa (d'_{k-1} + e_{k+1})) mid,
+//           mid  = 1 / (1 + 2 kappa + kappa (c'_{k-1} + c'_{m-k})), c'_0 = 0.
+constexpr int kSweepThreads = 64;
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ typename CT<T>::c shfl_xor16(typename CT<T>::c v)
+{
+    v.x = __shfl_xor_sync(kFull, v.x, 16);
+    v.y = __shfl_xor_sync(kFull, v.y, 16);
+    return v;
+}
+
 template <typename T, int MODE, bool NL, bool NORM>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(kSweepThreads)
 k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ work,
         const typename CT<T>::c *__restrict__ cp,
-        const typename CT<T>::c *__restrict__ mult, SweepGeom g, T kappa,
-        const typename CT<T>::c *__restrict__ px, const typename CT<T>::c *__restrict__ py,
-        const typename CT<T>::c *__restrict__ pz, double dtg,
-        const double *__restrict__ scale, double *__restrict__ partials)
+        const typename CT<T>::c *__restrict__ mult, typename CT<T>::c mid, SweepGeom g,
+        T kappa, const typename CT<T>::c *__restrict__ px,
+        const typename CT<T>::c *__restrict__ py, const typename CT<T>::c *__restrict__ pz,
+        double dtg, const double *__restrict__ scale, double *__restrict__ partials)
 {
     using C = typename CT<T>::c;
     __shared__ double red[32];
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool top = lane < 16;
+    const int a = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 16 + (lane & 15);
     const int b = blockIdx.y;
+    const bool active = a < g.lines_a;
+    const int m = g.n - 1;
+    const int k = (m + 1) >> 1;              // middle unknown
+    const int len = top ? k - 1 : m - k;     // points this lane eliminates
+    const int span = m - k;                  // >= k - 1
+    const long long s = g.pstride;
+    const long long base = active ? (long long)a * g.stride_a + (long long)b * g.stride_b : 0;
+    C *line = psi + base;
+    C *wl = work + base;
+    const Cn<T, MODE> cn{kappa};
+    Nonlin<T, MODE> nl{};
+    if (NL && active) {
+        // x sweep: a is the y index, b the z index
+        const C qy = py[a], qz = pz[b];
+        nl.px = px;
+        if (MODE == 0) {
+            const double sc = *scale;
+            nl.pyz = mk<T>((T)(sc * (double)qy.x * (double)qz.x), (T)0);
+            nl.a_coef = (T)(dtg * sc * sc);
+        } else {
+            nl.pyz = mk<T>(qy.x * qz.x - qy.y * qz.y, qy.x * qz.y + qy.y * qz.x);
+            nl.a_coef = (T)dtg;
+        }
+    }
     double nacc = 0.0;
-    if (a < g.lines_a) {
-        const long long base = (long long)a * g.stride_a + (long long)b * g.stride_b;
-        C *line = psi + base;
-        C *wl = work + base;
-        const long long s = g.pstride;
-        const int m = g.n - 1;
-        const Cn<T, MODE> cn{kappa};
-        Nonlin<T, MODE> nl{};
-        if (NL) {
-            // x sweep: a is the y index, b the z index
-            const C qy = py[a], qz = pz[b];
-            nl.px = px;
-            if (MODE == 0) {
-                const double sc = *scale;
-                nl.pyz = mk<T>((T)(sc * (double)qy.x * (double)qz.x), (T)0);
-                nl.a_coef = (T)(dtg * sc * sc);
-            } else {
-                nl.pyz = mk<T>(qy.x * qz.x - qy.y * qz.y, qy.x * qz.y + qy.y * qz.x);
-                nl.a_coef = (T)dtg;
-            }
-        }
-        C d = mk<T>((T)0, (T)0);
-        C p = d;
-        C nxt = line[s];
+    C d = mk<T>((T)0, (T)0);
+    if (active) {
 #pragma unroll 2
-        for (int i = 1; i <= m; ++i) {
-            p = nxt;
-            if (i < m) nxt = line[(long long)(i + 1) * s];
-            if (NL) {
-                p = nl.apply(p, i);
-                line[(long long)i * s] = p;
+        for (int t = 0; t < span; ++t) {
+            if (t < len) {
+                const long long at = (long long)(top ? 1 + t : m - t) * s;
+                C p = line[at];
+                if (NL) {
+                    p = nl.apply(p, top ? 1 + t : m - t);
+                    line[at] = p;
+                }
+                d = cn.fwd(p, d, mult[t]);
+                wl[at] = d;
             }
-            d = cn.fwd(p, d, mult[i - 1]);
-            wl[(long long)i * s] = d;
         }
-        C v = d;
-        C u = Cn<T, MODE>::out(v, p);
-        line[(long long)m * s] = u;
+    }
+    const C other = shfl_xor16<T>(d);
+    C vk = mk<T>((T)0, (T)0);
+    if (active && top) {
+        C pk = line[(long long)k * s];
+        if (NL) pk = nl.apply(pk, k);
+        vk = cn.fwd(pk, mk<T>(d.x + other.x, d.y + other.y), mid);
+        const C u = Cn<T, MODE>::out(vk, pk);
+        line[(long long)k * s] = u;
         if (NORM) nacc += abs2d<T>(u);
+    }
+    const C vpair = shfl_xor16<T>(vk);
+    C v = top ? vk : vpair;
+    if (active) {
 #pragma unroll 2
-        for (int i = m - 1; i >= 1; --i) {
-            v = cn.back(wl[(long long)i * s], cp[i - 1], v);
-            u = Cn<T, MODE>::out(v, line[(long long)i * s]);
-            line[(long long)i * s] = u;
-            if (NORM) nacc += abs2d<T>(u);
+        for (int t = span - 1; t >= 0; --t) {
+            if (t < len) {
+                const long long at = (long long)(top ? 1 + t : m - t) * s;
+                v = cn.back(wl[at], cp[t], v);
+                const C u = Cn<T, MODE>::out(v, line[at]);
+                line[at] = u;
+                if (NORM) nacc += abs2d<T>(u);
+            }
         }
     }
     if (NORM) {
@@ -236,7 +278,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
     }
 }
 
-constexpr int kSweepThreads = 64;
+constexpr int kLinesPerBlock = kSweepThreads / 2;
 
 template <typename T, int MODE, bool NL, bool NORM>
 cudaError_t sweep_launch(void *psi, void *work, const AxisTables &ax,
@@ -244,20 +286,23 @@ cudaError_t sweep_launch(void *psi, void *work, const AxisTables &ax,
                          const Partials *norm_out, cudaStream_t st)
 {
     using C = typename CT<T>::c;
-    dim3 grid((g.lines_a + kSweepThreads - 1) / kSweepThreads, g.lines_b);
+    dim3 grid((g.lines_a + kLinesPerBlock - 1) / kLinesPerBlock, g.lines_b);
     const C *cp, *mult, *px = nullptr, *py = nullptr, *pz = nullptr;
+    C mid;
     T kappa = (T)(MODE == 0 ? ax.kre : ax.kim);
     if constexpr (sizeof(T) == 8) {
         cp = reinterpret_cast<const C *>(ax.cp64);
         mult = reinterpret_cast<const C *>(ax.mult64);
+        mid = ax.mid64;
         if (nl) { px = (const C *)nl->px; py = (const C *)nl->py; pz = (const C *)nl->pz; }
     } else {
         cp = reinterpret_cast<const C *>(ax.cp32);
         mult = reinterpret_cast<const C *>(ax.mult32);
+        mid = ax.mid32;
         if (nl) { px = (const C *)nl->px32; py = (const C *)nl->py32; pz = (const C *)nl->pz32; }
     }
     k_sweep<T, MODE, NL, NORM><<<grid, kSweepThreads, 0, st>>>(
-        reinterpret_cast<C *>(psi), reinterpret_cast<C *>(work), cp, mult, g, kappa,
+        reinterpret_cast<C *>(psi), reinterpret_cast<C *>(work), cp, mult, mid, g, kappa,
         px, py, pz, nl ? nl->dtg : 0.0, nl ? nl->scale : nullptr,
         norm_out ? norm_out->buf : nullptr);
     return cudaGetLastError();
@@ -365,61 +410,93 @@ __global__ void k_norm_partials(const typename CT<T>::c *__restrict__ psi, long 
 }
 
 // ------------------------------------------------------------ observables
+//
+// One warp per x-line (j, k).  Per point: a = |psi|^2 and the forward
+// differences to the next point along x, y and z (zero beyond the last
+// stored point); the y and z coordinate factors are constant on the line, so
+// sum y^2 |psi|^2 = y_j^2 sum |psi|^2 etc. are formed once per line.  Each line
+// writes its 9 sums (times the pending scale s^2, s^4 for |psi|^4) to its own
+// partials row; two fixed-order passes add the rows, so the result does not
+// depend on the launch shape.
+
+constexpr int kObsThreads = 256;
+constexpr int kObsChunk = 1024;          // lines per first-stage finish block
 
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kObsThreads)
 k_observables(const typename CT<T>::c *__restrict__ psi, ObsArgs a,
               double *__restrict__ partials)
 {
     using C = typename CT<T>::c;
-    __shared__ double red[32];
+    const int lane = threadIdx.x & 31;
+    const long long line = (long long)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long long plane = (long long)nx * ny, count = plane * nz;
-    const double s = *a.scale, s2 = s * s;
-    double acc[kObsWidth];
-#pragma unroll
-    for (int q = 0; q < kObsWidth; ++q) acc[q] = 0.0;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(p % nx);
-        const int j = (int)((p / nx) % ny);
-        const int k = (int)(p / plane);
-        const C v = psi[p];
+    if (line >= (long long)ny * nz) return;       // whole warp
+    const int j = (int)(line % ny), k = (int)(line / ny);
+    const long long plane = (long long)nx * ny;
+    const C *row = psi + line * nx;
+    const bool has_y = j + 1 < ny, has_z = k + 1 < nz;
+    double s0 = 0, sx = 0, svx = 0, s4 = 0, kx = 0, ky = 0, kz = 0;
+    for (int i = lane; i < nx; i += 32) {
+        const C v = row[i];
         const double vr = v.x, vi = v.y;
-        const double am = s2 * (vr * vr + vi * vi);
-        const double x = coord(nx, a.h[0], i), y = coord(ny, a.h[1], j), z = coord(nz, a.h[2], k);
-        acc[0] += am;
-        acc[1] += x * x * am;
-        acc[2] += y * y * am;
-        acc[3] += z * z * am;
-        acc[4] += 0.5 * (a.w2[0] * x * x + a.w2[1] * y * y + a.w2[2] * z * z) * am;
-        acc[5] += am * am;
-        C nb;
-        nb = (i + 1 < nx) ? psi[p + 1] : mk<T>((T)0, (T)0);
-        acc[6] += s2 * (((double)nb.x - vr) * ((double)nb.x - vr) + ((double)nb.y - vi) * ((double)nb.y - vi));
-        nb = (j + 1 < ny) ? psi[p + nx] : mk<T>((T)0, (T)0);
-        acc[7] += s2 * (((double)nb.x - vr) * ((double)nb.x - vr) + ((double)nb.y - vi) * ((double)nb.y - vi));
+        const double am = fma(vr, vr, vi * vi);
+        s0 += am;
+        sx = fma(a.x2[i], am, sx);
+        svx = fma(a.vx[i], am, svx);
+        s4 = fma(am, am, s4);
+        double dr, di;
+        const C nb = (i + 1 < nx) ? row[i + 1] : mk<T>((T)0, (T)0);
+        dr = (double)nb.x - vr;
+        di = (double)nb.y - vi;
+        kx = fma(dr, dr, fma(di, di, kx));
+        const C ny_ = has_y ? row[i + nx] : mk<T>((T)0, (T)0);
+        dr = (double)ny_.x - vr;
+        di = (double)ny_.y - vi;
+        ky = fma(dr, dr, fma(di, di, ky));
         if (nz > 1) {
-            nb = (k + 1 < nz) ? psi[p + plane] : mk<T>((T)0, (T)0);
-            acc[8] += s2 * (((double)nb.x - vr) * ((double)nb.x - vr) + ((double)nb.y - vi) * ((double)nb.y - vi));
+            const C nz_ = has_z ? row[i + plane] : mk<T>((T)0, (T)0);
+            dr = (double)nz_.x - vr;
+            di = (double)nz_.y - vi;
+            kz = fma(dr, dr, fma(di, di, kz));
         }
     }
-#pragma unroll
-    for (int q = 0; q < kObsWidth; ++q) {
-        const double r = block_sum(acc[q], red);
-        if (threadIdx.x == 0) partials[(long long)blockIdx.x * kObsWidth + q] = r;
+    s0 = warp_sum(s0);
+    sx = warp_sum(sx);
+    svx = warp_sum(svx);
+    s4 = warp_sum(s4);
+    kx = warp_sum(kx);
+    ky = warp_sum(ky);
+    kz = warp_sum(kz);
+    if (lane == 0) {
+        const double sc = *a.scale, s2 = sc * sc;
+        double *out = partials + line * kObsWidth;
+        out[0] = s2 * s0;
+        out[1] = s2 * sx;
+        out[2] = s2 * a.y2[j] * s0;
+        out[3] = s2 * a.z2[k] * s0;
+        out[4] = s2 * (svx + (a.vy[j] + a.vz[k]) * s0);
+        out[5] = s2 * s2 * s4;
+        out[6] = s2 * kx;
+        out[7] = s2 * ky;
+        out[8] = s2 * kz;
     }
 }
 
-__global__ void k_obs_finish(const double *__restrict__ partials, int blocks,
-                             double *__restrict__ sums)
+// Sum rows [b * chunk, (b + 1) * chunk) of a [rows][9] array into out[b][9].
+__global__ void __launch_bounds__(256)
+k_rows_sum(const double *__restrict__ rows, long long count, int chunk,
+           double *__restrict__ out)
 {
     __shared__ double red[32];
+    const long long r0 = (long long)blockIdx.x * chunk;
+    long long r1 = r0 + chunk;
+    if (r1 > count) r1 = count;
     for (int q = 0; q < kObsWidth; ++q) {
         double v = 0.0;
-        for (int b = threadIdx.x; b < blocks; b += blockDim.x) v += partials[(long long)b * kObsWidth + q];
-        const double r = block_sum(v, red);
-        if (threadIdx.x == 0) sums[q] = r;
+        for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) v += rows[r * kObsWidth + q];
+        const double t = block_sum(v, red);
+        if (threadIdx.x == 0) out[(long long)blockIdx.x * kObsWidth + q] = t;
     }
 }
 
@@ -439,7 +516,7 @@ int point_blocks(long long count)
 
 int sweep_blocks(const SweepGeom &g)
 {
-    return ((g.lines_a + kSweepThreads - 1) / kSweepThreads) * g.lines_b;
+    return ((g.lines_a + kLinesPerBlock - 1) / kLinesPerBlock) * g.lines_b;
 }
 
 cudaError_t launch_sweep_x(int prec, int mode, void *psi, void *work,
@@ -513,16 +590,29 @@ cudaError_t launch_norm_partials(int prec, const void *psi, long long count,
     return cudaGetLastError();
 }
 
-cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
-                               double *partials, int blocks, double *sums, cudaStream_t st)
+long long obs_scratch_doubles(const ObsArgs &a)
 {
+    const long long lines = (long long)a.ny * a.nz;
+    const long long chunks = (lines + kObsChunk - 1) / kObsChunk;
+    return (lines + chunks) * kObsWidth;
+}
+
+cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
+                               double *scratch, double *sums, cudaStream_t st)
+{
+    const long long lines = (long long)a.ny * a.nz;
+    const long long chunks = (lines + kObsChunk - 1) / kObsChunk;
+    double *rows = scratch, *stage = scratch + lines * kObsWidth;
+    const long long blocks = (lines * 32 + kObsThreads - 1) / kObsThreads;
     if (prec == kC128)
-        k_observables<double><<<blocks, kPointThreads, 0, st>>>((const double2 *)psi, a, partials);
+        k_observables<double><<<(unsigned)blocks, kObsThreads, 0, st>>>((const double2 *)psi, a, rows);
     else
-        k_observables<float><<<blocks, kPointThreads, 0, st>>>((const float2 *)psi, a, partials);
+        k_observables<float><<<(unsigned)blocks, kObsThreads, 0, st>>>((const float2 *)psi, a, rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_obs_finish<<<1, 256, 0, st>>>(partials, blocks, sums);
+    k_rows_sum<<<(unsigned)chunks, 256, 0, st>>>(rows, lines, kObsChunk, stage);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_rows_sum<<<1, 256, 0, st>>>(stage, chunks, (int)chunks, sums);
     return cudaGetLastError();
 }
 

@@ -60,7 +60,7 @@ SIGNATURES = {
     "gp_observables": (_int, [_vp, ctypes.POINTER(gp_obs)]),
     "gp_sync": (_int, [_vp]),
     "gp_time_kernels": (_int, [_vp, _i64, ctypes.POINTER(ctypes.c_double), _int]),
-    "gp_launches_per_step": (_int, [_vp, ctypes.POINTER(_int)]),
+    "gp_launches_per_step": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "gp_device_psi": (_int, [_vp, ctypes.POINTER(_vp)]),
     "gp_footprint": (_int, [ctypes.POINTER(gp_grid), _int, ctypes.POINTER(ctypes.c_size_t)]),
     "gp_sweep_noalloc": (_int, [_vp, ctypes.POINTER(gp_grid), _int, _dbl, _dbl, _int, _int,
@@ -184,9 +184,10 @@ def gp_time_kernels(ctx, steps):
 
 
 def gp_launches_per_step(ctx):
-    k = ctypes.c_int()
-    _err(ctx, load_library().gp_launches_per_step(ctx, ctypes.byref(k)))
-    return k.value
+    """(kernel launches per SSCN step, kernel launches per gp_observables)."""
+    k, o = ctypes.c_int(), ctypes.c_int()
+    _err(ctx, load_library().gp_launches_per_step(ctx, ctypes.byref(k), ctypes.byref(o)))
+    return k.value, o.value
 
 
 def gp_sync(ctx):
