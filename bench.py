@@ -70,6 +70,9 @@ def parse_args():
     ap.add_argument("--probe", type=int, default=0, metavar="N",
                     help="profiling aid: load the Gaussian seed, run N real-time SSCN "
                          "steps of the workload, print nothing and exit")
+    ap.add_argument("--probe-case", default=None,
+                    help="workload name for --probe (default: the benchmark workload)")
+    ap.add_argument("--probe-shape", type=int, default=None, help="TMA tile shape for --probe")
     return ap.parse_args()
 
 
@@ -415,9 +418,12 @@ def run_probe(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_1206_1361_gb300 import gp
-    case = workload()
+    from paper_1206_1361_gb300.workloads import CASES
+    case = CASES[args.probe_case] if args.probe_case else workload()
     with gp.Solver(case.shape, case.h, case.dt, *case.trap, case.g, gp.GP_REAL,
                    case.precision) as s:
+        if args.probe_shape is not None:
+            gp.gp_set_option(s.ctx, gp.GP_OPT_TILE_SHAPE, args.probe_shape)
         s.load(None).step(args.probe).sync()
         s.observables()
     torch.cuda.synchronize()

@@ -186,6 +186,36 @@ int gp_device_psi(gp_ctx *ctx, void **dev_ptr);
 int gp_sweep_noalloc(void *psi_device, const gp_grid *grid, int axis, double h,
                      double dt, int mode, int precision, void *cuda_stream);
 
+/* Options of a context (gp_set_option / gp_get_option). */
+enum {
+    /* Sweep kernel: GP_PATH_AUTO picks per axis and mode; GP_PATH_EXACT is one
+     * line per thread with the elimination scratch in device memory;
+     * GP_PATH_TMA streams chunks of a tile of lines through shared memory with
+     * TMA and back-substitutes over a window, which is only selected (and
+     * only accepted) when the window's truncation bound |c'|^(C+1) is below
+     * the precision's rounding (2^-26 complex64, 2^-55 complex128). */
+    GP_OPT_SWEEP_PATH = 1,
+    /* Tile shape of the TMA sweep path: an index (0 .. GP_TILE_SHAPES - 1,
+     * per precision) into the library's table of (lines per CTA, points per
+     * chunk, pipeline stages); gp_get_option reads it back. */
+    GP_OPT_TILE_SHAPE = 2
+};
+enum { GP_PATH_AUTO = 0, GP_PATH_EXACT = 1, GP_PATH_TMA = 2 };
+
+/* Set an option; GP_EINVAL if the option or value is unknown or, for
+ * GP_PATH_TMA, if some axis cannot take it.  Takes effect at the next step. */
+int gp_set_option(gp_ctx *ctx, int option, int value);
+
+/* Read an option's current value into *value. */
+int gp_get_option(gp_ctx *ctx, int option, int *value);
+
+/* Number of tile shapes GP_OPT_TILE_SHAPE accepts for a precision. */
+int gp_tile_shapes(int precision, int *count);
+
+/* The sweep path each axis uses now in the current mode (GP_PATH_EXACT or
+ * GP_PATH_TMA) into path[0..2] (path[2] = 0 in 2D). */
+int gp_sweep_paths(gp_ctx *ctx, int path[3]);
+
 /* Bytes of device memory gp_create allocates for this grid and precision. */
 int gp_footprint(const gp_grid *grid, int precision, size_t *bytes);
 

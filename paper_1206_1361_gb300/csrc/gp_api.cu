@@ -2,6 +2,7 @@
 // per-context device state, the Crank-Nicolson coefficient tables and the
 // CUDA-graph replay of the SSCN time loop.
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -40,6 +41,12 @@ struct gp_ctx {
     int *err_dev = nullptr;         // device error bits
     double *host_sums = nullptr;    // pinned
     int *host_err = nullptr;        // pinned
+
+    CUtensorMap maps[3];            // 64-byte aligned type
+    bool map_ok[3]{};
+    bool tma_ok[2][3]{};            // [mode][axis] TMA path eligible
+    int path_opt = GP_PATH_AUTO;
+    int tile_shape = 0;
 
     int64_t step = 0;
     bool scale_pending = false;
@@ -146,6 +153,7 @@ int upload_tables(gp_ctx *c)
                 mult32[i] = make_float2((float)mult[i].x, (float)mult[i].y);
             }
             gp::set_mid(a, m, cp.data());
+            gp::set_converged(a, m, cp.data(), mult.data());
             GP_CK(c, cudaMemcpy(a.cp64, cp.data(), m * sizeof(double2), cudaMemcpyHostToDevice));
             GP_CK(c, cudaMemcpy(a.mult64, mult.data(), m * sizeof(double2), cudaMemcpyHostToDevice));
             GP_CK(c, cudaMemcpy(a.cp32, cp32.data(), m * sizeof(float2), cudaMemcpyHostToDevice));
@@ -182,6 +190,23 @@ int upload_tables(gp_ctx *c)
     return GP_OK;
 }
 
+// TMA path eligibility per (mode, axis): the tensor map encodes, and the
+// window truncation bound max|c'|^(C+1) is below the precision's rounding.
+void setup_tma(gp_ctx *c)
+{
+    const int C = gp::tma_chunk(c->prec, c->tile_shape);
+    for (int k = 0; k < naxes(c->grid); ++k) {
+        c->map_ok[k] = gp::make_sweep_map(c->prec, c->tile_shape, c->psi, c->grid.nx, c->grid.ny,
+                                          c->grid.nz, k, &c->maps[k]) == cudaSuccess;
+        cudaGetLastError();
+        for (int mode = 0; mode < 2; ++mode) {
+            const gp::AxisTables &a = c->ax[mode][k];
+            const int w = c->prec == GP_C64 ? a.win32 : a.win64;
+            c->tma_ok[mode][k] = c->map_ok[k] && w >= 1 && w <= C;
+        }
+    }
+}
+
 size_t footprint_bytes(const gp_grid &g, int prec)
 {
     const size_t psi = (size_t)points(g) * elem_bytes(prec);
@@ -191,7 +216,9 @@ size_t footprint_bytes(const gp_grid &g, int prec)
         tables += 2 * 2 * n * (sizeof(double2) + sizeof(float2)) + 2 * n * (sizeof(double2) + sizeof(float2));
     }
     int blocks = 0;
-    for (int k = 0; k < naxes(g); ++k) blocks = std::max(blocks, gp::sweep_blocks(geom(g, k)));
+    for (int k = 0; k < naxes(g); ++k)
+        for (int sh = 0; sh < gp::tma_shapes(prec); ++sh)
+            blocks = std::max({blocks, gp::sweep_blocks(geom(g, k)), gp::tma_blocks(prec, sh, geom(g, k))});
     blocks = std::max(blocks, gp::kReduceBlocks);
     gp::ObsArgs oa{};
     oa.nx = g.nx;
@@ -226,12 +253,39 @@ void release(gp_ctx *c)
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
+// Path of the sweep along `axis` in the current mode.
+int sweep_path(const gp_ctx *c, int axis)
+{
+    if (!c->tma_ok[c->mode][axis]) return GP_PATH_EXACT;
+    if (c->path_opt == GP_PATH_EXACT) return GP_PATH_EXACT;
+    if (c->path_opt == GP_PATH_TMA) return GP_PATH_TMA;
+    // auto: the FP64 path is bound by the FP64 pipe, where the window's extra
+    // back-substitution work costs more than the traffic it saves
+    return c->prec == GP_C64 ? GP_PATH_TMA : GP_PATH_EXACT;
+}
+
+cudaError_t launch_sweep(gp_ctx *c, int axis, const gp::NonlinArgs *nl, const Partials *norm,
+                         int *blocks)
+{
+    const SweepGeom g = geom(c->grid, axis);
+    const gp::AxisTables &ax = c->ax[c->mode][axis];
+    if (sweep_path(c, axis) == GP_PATH_TMA) {
+        if (blocks) *blocks = gp::tma_blocks(c->prec, c->tile_shape, g);
+        return gp::launch_sweep_tma(c->prec, c->tile_shape, c->mode, axis, c->maps[axis], ax, g,
+                                    nl, norm, c->err_dev, c->stream);
+    }
+    if (blocks) *blocks = gp::sweep_blocks(g);
+    if (nl) return gp::launch_sweep_x(c->prec, c->mode, c->psi, c->work, ax, g, *nl, c->grid.ny,
+                                      c->grid.nz, norm, c->stream);
+    return gp::launch_sweep_yz(c->prec, c->mode, c->psi, c->work, ax, g, norm, c->stream);
+}
+
 // Enqueue one SSCN step.  With ev != nullptr, record ev[0] before the first
 // kernel and ev[1 + k] after kernel slot k (x, y, z sweep, norm finish); slots
 // a step does not launch get their event recorded back to back.
 int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
 {
-    const int mode = c->mode, prec = c->prec;
+    const int mode = c->mode;
     const bool three_d = c->grid.nz > 1;
     Partials part{c->partials, 1};
     const Partials *norm_x = nullptr;
@@ -244,22 +298,15 @@ int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
     nl.pz32 = c->ph32[mode][2];
     nl.dtg = c->dt * c->g;
     nl.scale = c->scale;
-    const SweepGeom gx = geom(c->grid, 0), gy = geom(c->grid, 1), gz = geom(c->grid, 2);
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], c->stream) : cudaSuccess; };
     GP_CK(c, mark(0));
-    GP_CK(c, gp::launch_sweep_x(prec, mode, c->psi, c->work, c->ax[mode][0], gx, nl,
-                                c->grid.ny, c->grid.nz, norm_x, c->stream));
+    GP_CK(c, launch_sweep(c, 0, &nl, norm_x, nullptr));
     GP_CK(c, mark(1));
     const bool imag = mode == GP_IMAG;
-    GP_CK(c, gp::launch_sweep_yz(prec, mode, c->psi, c->work, c->ax[mode][1], gy,
-                                 (imag && !three_d) ? &part : nullptr, c->stream));
+    int last_blocks = 0;
+    GP_CK(c, launch_sweep(c, 1, nullptr, (imag && !three_d) ? &part : nullptr, &last_blocks));
     GP_CK(c, mark(2));
-    int last_blocks = gp::sweep_blocks(gy);
-    if (three_d) {
-        GP_CK(c, gp::launch_sweep_yz(prec, mode, c->psi, c->work, c->ax[mode][2], gz,
-                                     imag ? &part : nullptr, c->stream));
-        last_blocks = gp::sweep_blocks(gz);
-    }
+    if (three_d) GP_CK(c, launch_sweep(c, 2, nullptr, imag ? &part : nullptr, &last_blocks));
     GP_CK(c, mark(3));
     if (imag)
         GP_CK(c, gp::launch_norm_finish(c->partials, last_blocks, cell_volume(c), c->scale,
@@ -347,6 +394,7 @@ int read_errors(gp_ctx *c)
 {
     GP_CK(c, cudaMemcpyAsync(c->host_err, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     GP_CK(c, cudaStreamSynchronize(c->stream));
+    if (*c->host_err & 2) return fail(c, GP_ETIMEOUT, "a sweep's bounded wait for a TMA chunk gave up");
     if (*c->host_err & 1) return fail(c, GP_ENONFINITE, "norm became non-finite or zero");
     return GP_OK;
 }
@@ -354,6 +402,36 @@ int read_errors(gp_ctx *c)
 }  // namespace
 
 void gp::set_thread_error(const char *msg) { g_create_error = msg ? msg : ""; }
+
+void gp::set_converged(AxisTables &a, int m, const double2 *cp, const double2 *mult)
+{
+    int c64 = m - 1, c32 = m - 1;
+    auto f = [](double v) { return (double)(float)v; };
+    while (c64 > 0 && cp[c64 - 1].x == cp[m - 1].x && cp[c64 - 1].y == cp[m - 1].y &&
+           mult[c64 - 1].x == mult[m - 1].x && mult[c64 - 1].y == mult[m - 1].y)
+        --c64;
+    while (c32 > 0 && f(cp[c32 - 1].x) == f(cp[m - 1].x) && f(cp[c32 - 1].y) == f(cp[m - 1].y) &&
+           f(mult[c32 - 1].x) == f(mult[m - 1].x) && f(mult[c32 - 1].y) == f(mult[m - 1].y))
+        --c32;
+    a.conv64 = c64;
+    a.conv32 = c32;
+    a.cinf64 = cp[m - 1];
+    a.minf64 = mult[m - 1];
+    a.cinf32 = make_float2((float)cp[m - 1].x, (float)cp[m - 1].y);
+    a.minf32 = make_float2((float)mult[m - 1].x, (float)mult[m - 1].y);
+    double cmax = 0.0;
+    for (int i = 0; i < m; ++i) cmax = std::max(cmax, std::hypot(cp[i].x, cp[i].y));
+    auto window = [&](double tol) {
+        double p = cmax;
+        for (int w = 1; w <= 64; ++w) {
+            p *= cmax;                         // cmax^(w+1)
+            if (p < tol) return w;
+        }
+        return 0;
+    };
+    a.win64 = window(std::ldexp(1.0, -55));
+    a.win32 = window(std::ldexp(1.0, -26));
+}
 
 void gp::set_mid(AxisTables &a, int m, const double2 *cp)
 {
@@ -444,7 +522,10 @@ int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, 
             if ((rc = alloc(c, (void **)&c->ph32[mode_i][k], n * sizeof(float2)))) return bail(rc);
         }
     int blocks = gp::kReduceBlocks;
-    for (int k = 0; k < naxes(c->grid); ++k) blocks = std::max(blocks, gp::sweep_blocks(geom(c->grid, k)));
+    for (int k = 0; k < naxes(c->grid); ++k)
+        for (int sh = 0; sh < gp::tma_shapes(precision); ++sh)
+            blocks = std::max({blocks, gp::sweep_blocks(geom(c->grid, k)),
+                               gp::tma_blocks(precision, sh, geom(c->grid, k))});
     c->partial_cap = blocks;
     if ((rc = alloc(c, (void **)&c->partials, blocks * sizeof(double)))) return bail(rc);
     {
@@ -467,6 +548,7 @@ int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, 
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
     }
     if ((rc = upload_tables(c))) return bail(rc);
+    setup_tma(c);
     {
         cudaError_t e = cudaMemsetAsync(c->psi, 0, psi_bytes, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
@@ -618,6 +700,57 @@ int gp_time_kernels(gp_ctx *c, int64_t steps, double *ms_out, int n_out)
     }
     for (auto &e : ev) cudaEventDestroy(e);
     return rc;
+}
+
+int gp_set_option(gp_ctx *c, int option, int value)
+{
+    if (!c) return fail(nullptr, GP_EINVAL, "gp_set_option: null context");
+    if (option == GP_OPT_TILE_SHAPE) {
+        if (value < 0 || value >= gp::tma_shapes(c->prec))
+            return fail(c, GP_EINVAL, "gp_set_option: tile shape out of range");
+        c->tile_shape = value;
+        setup_tma(c);
+        if (c->path_opt == GP_PATH_TMA)
+            for (int k = 0; k < naxes(c->grid); ++k)
+                if (!c->tma_ok[c->mode][k]) c->path_opt = GP_PATH_AUTO;
+        drop_graph(c);
+        return GP_OK;
+    }
+    if (option != GP_OPT_SWEEP_PATH) return fail(c, GP_EINVAL, "gp_set_option: unknown option");
+    if (value != GP_PATH_AUTO && value != GP_PATH_EXACT && value != GP_PATH_TMA)
+        return fail(c, GP_EINVAL, "gp_set_option: unknown sweep path");
+    if (value == GP_PATH_TMA)
+        for (int k = 0; k < naxes(c->grid); ++k)
+            if (!c->tma_ok[c->mode][k])
+                return fail(c, GP_EINVAL, "gp_set_option: the TMA sweep path does not apply to "
+                                          "this grid, dt and mode");
+    c->path_opt = value;
+    drop_graph(c);
+    return GP_OK;
+}
+
+int gp_get_option(gp_ctx *c, int option, int *value)
+{
+    if (!c || !value) return fail(c, GP_EINVAL, "gp_get_option: null argument");
+    if (option == GP_OPT_SWEEP_PATH) *value = c->path_opt;
+    else if (option == GP_OPT_TILE_SHAPE) *value = c->tile_shape;
+    else return fail(c, GP_EINVAL, "gp_get_option: unknown option");
+    return GP_OK;
+}
+
+int gp_tile_shapes(int precision, int *count)
+{
+    if ((precision != GP_C128 && precision != GP_C64) || !count)
+        return fail(nullptr, GP_EINVAL, "gp_tile_shapes: bad precision");
+    *count = gp::tma_shapes(precision);
+    return GP_OK;
+}
+
+int gp_sweep_paths(gp_ctx *c, int path[3])
+{
+    if (!c || !path) return fail(c, GP_EINVAL, "gp_sweep_paths: null argument");
+    for (int k = 0; k < 3; ++k) path[k] = k < naxes(c->grid) ? sweep_path(c, k) : 0;
+    return GP_OK;
 }
 
 int gp_launches_per_step(gp_ctx *c, int *per_step, int *per_observables)

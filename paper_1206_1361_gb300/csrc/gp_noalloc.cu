@@ -103,6 +103,7 @@ extern "C" int gp_sweep_noalloc(void *psi_device, const gp_grid *grid, int axis,
     ax.kre = mode == GP_IMAG ? kap : 0.0;
     ax.kim = mode == GP_IMAG ? 0.0 : kap;
     gp::set_mid(ax, m, g_cp64);
+    gp::set_converged(ax, m, g_cp64, g_mult64);
     unsigned char *tab = base + kScratchBytes;
     ax.cp64 = reinterpret_cast<double2 *>(tab);
     ax.mult64 = ax.cp64 + kTableEntries;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace gp {
@@ -20,7 +21,20 @@ struct AxisTables {
     float2 *cp32 = nullptr, *mult32 = nullptr;    // device, m entries each
     double2 mid64{0, 0};
     float2 mid32{0, 0};
+    // From index conv64 (conv32) on, every FP64 (FP32) table entry equals the
+    // last one: the elimination coefficients converge geometrically along a
+    // constant-coefficient line, so kernels may hold c'_inf and mult_inf in
+    // registers there (0-based table indices).
+    int conv64 = 0, conv32 = 0;
+    double2 cinf64{0, 0}, minf64{0, 0};
+    float2 cinf32{0, 0}, minf32{0, 0};
+    // Look-back window of the TMA path: smallest W with max|c'|^(W+1) below
+    // the precision's rounding (2^-55 / 2^-26); 0 if none up to the chunk.
+    int win64 = 0, win32 = 0;
 };
+
+// Fill the convergence fields of `a` from the host tables (m entries).
+void set_converged(AxisTables &a, int m, const double2 *cp, const double2 *mult);
 
 // Fill a.mid64 / a.mid32 from the host copy of the c' table (m entries).
 void set_mid(AxisTables &a, int m, const double2 *cp_host);
@@ -99,6 +113,23 @@ struct ObsArgs {
 long long obs_scratch_doubles(const ObsArgs &a);
 cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
                                double *scratch, double *sums, cudaStream_t st);
+
+// ---- TMA-pipelined sweeps (sscn_tma.cu) -------------------------------------
+// `shape` indexes a small table of tile shapes (lines per CTA, points per
+// chunk, pipeline stages); tma_shapes(prec) is its size.
+int tma_shapes(int prec);
+int tma_chunk(int prec, int shape);          // points per chunk C
+int tma_lines(int prec, int shape);          // lines per CTA L
+int tma_blocks(int prec, int shape, const SweepGeom &g);
+// Tensor map of psi for the sweep along `axis`; fails (no map) when the
+// layout breaks a TMA rule (complex64 rows must be a multiple of 16 bytes).
+cudaError_t make_sweep_map(int prec, int shape, void *psi, int nx, int ny, int nz, int axis,
+                           CUtensorMap *out);
+// Windowed, TMA-staged sweep; nl != nullptr fuses calcnu (x sweep);
+// norm_out adds FP64 sum |u|^2 per block; err receives bit 2 on a wait timeout.
+cudaError_t launch_sweep_tma(int prec, int shape, int mode, int axis, const CUtensorMap &map,
+                             const AxisTables &ax, const SweepGeom &g, const NonlinArgs *nl,
+                             const Partials *norm_out, int *err, cudaStream_t st);
 
 // Record msg as the message gp_last_error(NULL) returns in this thread.
 void set_thread_error(const char *msg);

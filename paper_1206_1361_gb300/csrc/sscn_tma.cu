@@ -1,0 +1,597 @@
+// sscn_tma.cu -- TMA-pipelined Crank-Nicolson sweeps (calclux / calcluy /
+// calcluz, with calcnu fused into the x sweep) for the bandwidth-bound
+// complex64 form, sm_103a.
+//
+// One CTA owns a tile of L = 32 K lines (one consumer thread per line) and
+// walks them chunk by chunk: a chunk is the C consecutive points of all L
+// lines, one TMA box.  A producer warp keeps up to S - 1 chunks in flight
+// ahead of the compute through an S-stage shared-memory ring
+// (cp.async.bulk.tensor loads completing on one mbarrier per stage); ragged
+// tiles and the points past the end of a line arrive as zeros (TMA
+// out-of-bounds fill) and are clipped on the way back.
+//
+// Each consumer thread runs the forward elimination of its line through the
+// tile, keeping d'_i for the last two chunks in a shared-memory ring, and
+// writes the finished values back into the tile in place; the producer then
+// stores the tile with a TMA store and reuses the stage.  Back substitution is windowed: the values of chunk q-1
+// are produced after the forward pass of chunk q, starting from v ~ d' at the
+// end of chunk q.  The dropped term is c'_e v_{e+1}, damped by |c'| at every
+// step back; the seed sits W points into chunk q, so every output carries an
+// error below |c'|^(W+1) max|v|.  The host picks the smallest W <= C for which
+// that bound is under 2^-26 (complex64) / 2^-55 (complex128) and otherwise
+// uses the exact one-line-per-thread kernel.
+// The last two chunks are back-substituted exactly from v_m = d'_m.
+//
+// Layout of a stage: x sweep -> [L rows][C points] with the 128-byte TMA
+// swizzle (16-byte chunk j of row r sits at j ^ (r % 8)), so a warp reading
+// point c of 32 different rows hits distinct banks; y / z sweeps ->
+// [C rows][L points], consecutive threads on consecutive addresses.
+
+#include <cstdint>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include "sscn_internal.h"
+
+namespace gp {
+namespace {
+
+template <typename T> struct CT2;
+template <> struct CT2<double> { using c = double2; };
+template <> struct CT2<float> { using c = float2; };
+
+template <typename T> __device__ __forceinline__ typename CT2<T>::c mk2(T x, T y)
+{
+    typename CT2<T>::c r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+
+// ------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of the barrier, for at most `limit_ns`.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int c0,
+                                             int c1, int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+template <int N> __device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// ------------------------------------------------------------- arithmetic
+
+template <typename T, int MODE> struct CnT {
+    using C = typename CT2<T>::c;
+    T k;
+    __device__ __forceinline__ C fwd(C p, C d, C f) const
+    {
+        if (MODE == 0) return mk2<T>(fma(k, d.x, p.x) * f.x, fma(k, d.y, p.y) * f.x);
+        const T tx = fma(-k, d.y, p.x), ty = fma(k, d.x, p.y);
+        return mk2<T>(fma(tx, f.x, -ty * f.y), fma(tx, f.y, ty * f.x));
+    }
+    __device__ __forceinline__ C back(C d, C c, C v) const
+    {
+        if (MODE == 0) return mk2<T>(fma(-c.x, v.x, d.x), fma(-c.x, v.y, d.y));
+        return mk2<T>(fma(-c.x, v.x, fma(c.y, v.y, d.x)), fma(-c.x, v.y, fma(-c.y, v.x, d.y)));
+    }
+    static __device__ __forceinline__ C out(C v, C p)
+    {
+        return mk2<T>(fma((T)2, v.x, -p.x), fma((T)2, v.y, -p.y));
+    }
+};
+
+__device__ __forceinline__ void expmi(float a, float &c, float &s) { sincosf(a, &s, &c); }
+__device__ __forceinline__ float expm(float a) { return expf(-a); }
+__device__ __forceinline__ void expmi(double a, double &c, double &s) { sincos(a, &s, &c); }
+__device__ __forceinline__ double expm(double a) { return exp(-a); }
+
+// calcnu: P_x[i] P_yz exp(-tau dt g |psi|^2) psi (P_yz carries the pending
+// imaginary-time scale, a_coef = dt g s^2).
+template <typename T, int MODE> struct NonlinT {
+    using C = typename CT2<T>::c;
+    const C *px;
+    C pyz;
+    T a_coef;
+    __device__ __forceinline__ C apply(C v, int i) const
+    {
+        const C q = px[i];
+        const T a = a_coef * (v.x * v.x + v.y * v.y);
+        if (MODE == 0) {
+            const T f = q.x * pyz.x * expm(a);
+            return mk2<T>(v.x * f, v.y * f);
+        } else {
+            T cs, sn;
+            expmi(a, cs, sn);
+            const T prx = fma(q.x, pyz.x, -q.y * pyz.y), pry = fma(q.x, pyz.y, q.y * pyz.x);
+            const T wx = fma(cs, v.x, sn * v.y), wy = fma(cs, v.y, -sn * v.x);
+            return mk2<T>(fma(prx, wx, -pry * wy), fma(prx, wy, pry * wx));
+        }
+    }
+};
+
+// ------------------------------------------------------------------ kernel
+
+struct TmaArgs {
+    int n;              // stored points per line (m = n - 1 unknowns)
+    int lines_a;        // extent of the in-tile line index (y for x, x for y / z)
+    int win;            // look-back window W (1 .. C)
+    int conv;           // table index from which c' and mult are constant
+    double2 cinf, minf; // those constants (FP64; rounded to T in the kernel)
+    const void *cp, *mult;      // complex T tables, m entries
+    const void *px, *py, *pz;   // calcnu factor tables (x sweep)
+    double kappa;       // kre (imaginary time) or kim (real time)
+    double dtg;
+    const double *scale;
+    double *partials;   // norm partials (NORM)
+    int *err;           // device error bits
+};
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per chunk wait
+constexpr int kErrTimeout = 2;
+
+template <typename T, int L, int C, int S, int AXIS>
+struct TileGeom {
+    static constexpr int E = (int)sizeof(typename CT2<T>::c);   // bytes per complex value
+    static constexpr int U = E / 8;                              // 8-byte TMA units per value
+    static constexpr int kStageBytes = L * C * E;
+    // byte offset of (line l, point c) inside a stage
+    static __device__ __forceinline__ int off(int l, int c)
+    {
+        if (AXIS == 0) {
+            const int byte = c * E;                 // within the 128-byte row of line l
+            return l * (C * E) + ((((byte >> 4) ^ (l & 7))) << 4) + (byte & 15);
+        }
+        return (c * L + l) * E;
+    }
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp-specialised CTA: K consumer warps own L = 32 K lines (one per
+// thread); warp K is the producer, whose lane 0 issues every TMA load and
+// store.  Per stage s: full[s] completes when a chunk's bytes have landed,
+// ready[s] when all K consumer warps have written the chunk's final values
+// (one arrival per warp).  The producer stores a chunk once it is ready and
+// reuses its stage only after that store has read shared memory, so the
+// consumers never wait on a store.
+template <typename T, int MODE, int AXIS, bool NL, bool NORM, int K, int C, int S>
+__global__ void __launch_bounds__(32 * (K + 1))
+k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
+{
+    using Cx = typename CT2<T>::c;
+    constexpr int L = 32 * K;
+    using G = TileGeom<T, L, C, S, AXIS>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment of the stage ring (the 128-byte swizzle needs it)
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *stages = smem;
+    Cx *ring = reinterpret_cast<Cx *>(stages + S * G::kStageBytes);     // [2][C][L]
+    uint64_t *full = reinterpret_cast<uint64_t *>(ring + 2 * C * L);
+    uint64_t *ready = full + S;
+    double *red = reinterpret_cast<double *>(ready + S);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool producer = warp == K;
+    const int l = producer ? 0 : threadIdx.x;        // line inside the tile
+    const int tile0 = blockIdx.x * L;
+    const int a = tile0 + l;
+    const bool active = !producer && a < args.lines_a;
+    const int m = args.n - 1;
+    const int Q = (args.n + C - 1) / C;             // chunks covering stored points 0 .. m
+    const Cx *cp_tab = static_cast<const Cx *>(args.cp);
+    const Cx *mult_tab = static_cast<const Cx *>(args.mult);
+    const CnT<T, MODE> cn{(T)args.kappa};
+    const int conv = args.conv, win = args.win;
+    const Cx cinf = mk2<T>((T)args.cinf.x, (T)args.cinf.y);
+    const Cx minf = mk2<T>((T)args.minf.x, (T)args.minf.y);
+    // table entry t (0-based): past `conv` every entry equals the last one
+    auto cp = [&](int t) { return t < conv ? cp_tab[t] : cinf; };
+    auto mult = [&](int t) { return t < conv ? mult_tab[t] : minf; };
+
+    // TMA coordinates (innermost first, in 8-byte units) of chunk q
+    auto coords = [&](int q, int &c0, int &c1, int &c2) {
+        if (AXIS == 0) { c0 = q * C * G::U; c1 = tile0; c2 = blockIdx.y; }
+        else if (AXIS == 1) { c0 = tile0 * G::U; c1 = q * C; c2 = blockIdx.y; }
+        else { c0 = tile0 * G::U; c1 = blockIdx.y; c2 = q * C; }
+    };
+    auto stage_ptr = [&](int q) { return stages + (q % S) * G::kStageBytes; };
+    auto at = [&](int q, int c) -> Cx * { return reinterpret_cast<Cx *>(stage_ptr(q) + G::off(l, c)); };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&ready[s], K);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    bool failed = false;
+    double nacc = 0.0;
+    if (producer) {
+        if (lane == 0) {
+            auto store = [&](int q) {
+                int c0, c1, c2;
+                coords(q, c0, c1, c2);
+                tma_store_3d(&map, stage_ptr(q), c0, c1, c2);
+                bulk_commit();
+            };
+            for (int q = 0; q < Q && !failed; ++q) {
+                if (q >= S) {
+                    // the stage last held chunk q - S: store it once final,
+                    // then let the store finish reading before reloading
+                    const int o = q - S;
+                    if (!mbar_wait_bounded(&ready[o % S], (uint32_t)((o / S) & 1), kWaitLimitNs)) {
+                        failed = true;
+                        break;
+                    }
+                    store(o);
+                    bulk_wait_read<0>();
+                }
+                int c0, c1, c2;
+                coords(q, c0, c1, c2);
+                mbar_arrive_expect_tx(&full[q % S], G::kStageBytes);
+                tma_load_3d(stage_ptr(q), &map, &full[q % S], c0, c1, c2);
+            }
+            for (int o = Q > S ? Q - S : 0; o < Q && !failed; ++o) {
+                if (!mbar_wait_bounded(&ready[o % S], (uint32_t)((o / S) & 1), kWaitLimitNs)) {
+                    failed = true;
+                    break;
+                }
+                store(o);
+            }
+            bulk_wait_all();
+        }
+    } else {
+        NonlinT<T, MODE> nl{};
+        if (NL && active) {
+            const Cx *py = static_cast<const Cx *>(args.py), *pz = static_cast<const Cx *>(args.pz);
+            const Cx qy = py[a], qz = pz[blockIdx.y];
+            nl.px = static_cast<const Cx *>(args.px);
+            if (MODE == 0) {
+                const double sc = *args.scale;
+                nl.pyz = mk2<T>((T)(sc * (double)qy.x * (double)qz.x), (T)0);
+                nl.a_coef = (T)(args.dtg * sc * sc);
+            } else {
+                nl.pyz = mk2<T>(qy.x * qz.x - qy.y * qz.y, qy.x * qz.y + qy.y * qz.x);
+                nl.a_coef = (T)args.dtg;
+            }
+        }
+        Cx d = mk2<T>((T)0, (T)0);
+        for (int q = 0; q < Q; ++q) {
+            if (!mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs)) {
+                failed = true;
+                break;
+            }
+            // forward elimination through chunk q
+            Cx *rq = ring + (q & 1) * C * L;
+            if (active) {
+#pragma unroll 4
+                for (int c = 0; c < C; ++c) {
+                    const int i = q * C + c;
+                    if (i >= 1 && i <= m) {
+                        Cx p = *at(q, c);
+                        if (NL) {
+                            p = nl.apply(p, i);
+                            *at(q, c) = p;
+                        }
+                        d = cn.fwd(p, d, mult(i - 1));
+                        rq[c * L + l] = d;
+                    }
+                }
+            }
+            const bool last = q == Q - 1;
+            if (active) {
+                if (!last && q >= 1) {
+                    // windowed: seed W points into chunk q, output chunk q - 1
+                    Cx v = rq[(win - 1) * L + l];
+                    for (int c = win - 2; c >= 0; --c)
+                        v = cn.back(rq[c * L + l], cp(q * C + c - 1), v);
+                    Cx *rp = ring + ((q - 1) & 1) * C * L;
+#pragma unroll 4
+                    for (int c = C - 1; c >= 0; --c) {
+                        const int i = (q - 1) * C + c;
+                        if (i < 1) break;
+                        v = cn.back(rp[c * L + l], cp(i - 1), v);
+                        Cx *slot = at(q - 1, c);
+                        const Cx u = CnT<T, MODE>::out(v, *slot);
+                        *slot = u;
+                        if (NORM) nacc += (double)u.x * u.x + (double)u.y * u.y;
+                    }
+                } else if (last) {
+                    // exact: v_m = d'_m, down through chunks q and q - 1
+                    Cx v = d;
+                    const int lo = q >= 1 ? (q - 1) * C : 0;
+                    for (int i = m; i >= lo && i >= 1; --i) {
+                        const int qq = i / C, c = i - qq * C;
+                        const Cx *rr = ring + (qq & 1) * C * L;
+                        if (i < m) v = cn.back(rr[c * L + l], cp(i - 1), v);
+                        Cx *slot = at(qq, c);
+                        const Cx u = CnT<T, MODE>::out(v, *slot);
+                        *slot = u;
+                        if (NORM) nacc += (double)u.x * u.x + (double)u.y * u.y;
+                    }
+                }
+            }
+            if (q >= 1 || last) {
+                fence_proxy_async();             // tile writes -> async proxy
+                __syncwarp();
+                if (lane == 0) {
+                    if (q >= 1) mbar_arrive(&ready[(q - 1) % S]);
+                    if (last) mbar_arrive(&ready[q % S]);
+                }
+            }
+        }
+    }
+    if (failed) atomicOr(args.err, kErrTimeout);
+    if (NORM) {
+        // block sum of the per-line norm contributions, fixed order
+        double v = nacc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double r = lane < K ? red[lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+            if (lane == 0) args.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = r;
+        }
+    }
+}
+
+template <typename T, int K, int C, int S>
+constexpr size_t tma_smem_bytes()
+{
+    constexpr size_t L = 32 * K;
+    return 1024 + (size_t)S * L * C * sizeof(typename CT2<T>::c) +
+           2 * (size_t)C * L * sizeof(typename CT2<T>::c) + 2 * S * sizeof(uint64_t) +
+           32 * sizeof(double);
+}
+
+template <typename T, int MODE, int AXIS, bool NL, bool NORM, int K, int C, int S>
+cudaError_t launch_tma_inst(const CUtensorMap &map, const TmaArgs &args, int tiles, int lines_b,
+                            cudaStream_t st)
+{
+    auto kern = k_sweep_tma<T, MODE, AXIS, NL, NORM, K, C, S>;
+    constexpr size_t smem = tma_smem_bytes<T, K, C, S>();
+    constexpr int threads = 32 * (K + 1);
+    static bool configured[64] = {};          // per device ordinal
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!configured[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    kern<<<dim3(tiles, lines_b), threads, smem, st>>>(map, args);
+    return cudaGetLastError();
+}
+
+template <typename T, int AXIS, int K, int C, int S>
+cudaError_t launch_tma_axis(int mode, bool nl, bool norm, const CUtensorMap &map,
+                            const TmaArgs &args, int tiles, int lines_b, cudaStream_t st)
+{
+    // calcnu is fused into the x sweep only
+#define GP_TMA(MODE, NLV, NORMV)                                                             \
+    return launch_tma_inst<T, MODE, AXIS, (NLV && AXIS == 0), NORMV, K, C, S>(map, args, tiles, \
+                                                                           lines_b, st)
+    if (mode == 0) {
+        if (nl) { if (norm) GP_TMA(0, true, true); GP_TMA(0, true, false); }
+        if (norm) GP_TMA(0, false, true);
+        GP_TMA(0, false, false);
+    }
+    if (nl) { if (norm) GP_TMA(1, true, true); GP_TMA(1, true, false); }
+    if (norm) GP_TMA(1, false, true);
+    GP_TMA(1, false, false);
+#undef GP_TMA
+}
+
+// Tile shapes (consumer warps K, points per chunk C, stages S); a CTA owns
+// 32 K lines.  C is fixed by the 128-byte swizzled x rows (16 complex64 / 8
+// complex128 points); K and S trade CTAs per SM against chunks in flight.
+struct Shape { int K, C, S; };
+// Index 0 is the default: the fastest measured at 512 x 512 x 256 complex64
+// (2 consumer warps, 3 stages: 5 CTAs per SM) and 256^3 complex128.
+constexpr Shape kShapes32[] = {{2, 16, 3}, {1, 16, 4}, {2, 16, 4}, {4, 16, 3}, {1, 16, 3}};
+constexpr Shape kShapes64[] = {{1, 8, 4}, {2, 8, 4}, {4, 8, 3}};
+constexpr int kNumShapes32 = 5, kNumShapes64 = 3;
+
+template <typename T, int K, int C, int S>
+cudaError_t launch_shape(int mode, int axis, bool nl, bool norm, const CUtensorMap &map,
+                         const TmaArgs &args, int tiles, int lines_b, cudaStream_t st)
+{
+    if (axis == 0) return launch_tma_axis<T, 0, K, C, S>(mode, nl, norm, map, args, tiles, lines_b, st);
+    if (axis == 1) return launch_tma_axis<T, 1, K, C, S>(mode, nl, norm, map, args, tiles, lines_b, st);
+    return launch_tma_axis<T, 2, K, C, S>(mode, nl, norm, map, args, tiles, lines_b, st);
+}
+
+Shape shape_of(int prec, int shape)
+{
+    if (prec == kC128) return kShapes64[shape < 0 || shape >= kNumShapes64 ? 0 : shape];
+    return kShapes32[shape < 0 || shape >= kNumShapes32 ? 0 : shape];
+}
+
+}  // namespace
+
+int tma_shapes(int prec) { return prec == kC128 ? kNumShapes64 : kNumShapes32; }
+int tma_chunk(int prec, int shape) { return shape_of(prec, shape).C; }
+int tma_lines(int prec, int shape) { return 32 * shape_of(prec, shape).K; }
+
+int tma_blocks(int prec, int shape, const SweepGeom &g)
+{
+    const int L = tma_lines(prec, shape);
+    return ((g.lines_a + L - 1) / L) * g.lines_b;
+}
+
+// Encode the tensor map of psi for one sweep axis.  psi is viewed as a 3D
+// array of 8-byte units {U * nx, ny, nz}; the box is one chunk of one tile.
+cudaError_t make_sweep_map(int prec, int shape, void *psi, int nx, int ny, int nz, int axis,
+                           CUtensorMap *out)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const int U = prec == kC128 ? 2 : 1;
+    const Shape sh = shape_of(prec, shape);
+    const cuuint64_t dims[3] = {(cuuint64_t)U * nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)U * nx * 8, (cuuint64_t)U * nx * ny * 8};
+    cuuint32_t box[3];
+    CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_NONE;
+    const int L = 32 * sh.K;
+    if (axis == 0) { box[0] = U * sh.C; box[1] = L; box[2] = 1; sw = CU_TENSOR_MAP_SWIZZLE_128B; }
+    else if (axis == 1) { box[0] = U * L; box[1] = sh.C; box[2] = 1; }
+    else { box[0] = U * L; box[1] = 1; box[2] = sh.C; }
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, psi, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sweep_tma(int prec, int shape, int mode, int axis, const CUtensorMap &map,
+                             const AxisTables &ax, const SweepGeom &g, const NonlinArgs *nl,
+                             const Partials *norm_out, int *err, cudaStream_t st)
+{
+    TmaArgs args{};
+    args.n = g.n;
+    args.lines_a = g.lines_a;
+    args.kappa = mode == 0 ? ax.kre : ax.kim;
+    args.partials = norm_out ? norm_out->buf : nullptr;
+    args.err = err;
+    if (prec == kC128) {
+        args.cp = ax.cp64;
+        args.mult = ax.mult64;
+        args.conv = ax.conv64;
+        args.win = ax.win64;
+        args.cinf = ax.cinf64;
+        args.minf = ax.minf64;
+    } else {
+        args.cp = ax.cp32;
+        args.mult = ax.mult32;
+        args.conv = ax.conv32;
+        args.win = ax.win32;
+        args.cinf = make_double2(ax.cinf32.x, ax.cinf32.y);
+        args.minf = make_double2(ax.minf32.x, ax.minf32.y);
+    }
+    if (nl) {
+        args.px = prec == kC128 ? (const void *)nl->px : (const void *)nl->px32;
+        args.py = prec == kC128 ? (const void *)nl->py : (const void *)nl->py32;
+        args.pz = prec == kC128 ? (const void *)nl->pz : (const void *)nl->pz32;
+        args.dtg = nl->dtg;
+        args.scale = nl->scale;
+    }
+    const int tiles = (g.lines_a + tma_lines(prec, shape) - 1) / tma_lines(prec, shape);
+    const bool norm = norm_out != nullptr, has_nl = nl != nullptr;
+    const int lb = g.lines_b;
+#define GP_SHAPE(T, SH, I)                                                                   \
+    if (shape == I)                                                                          \
+        return launch_shape<T, SH[I].K, SH[I].C, SH[I].S>(mode, axis, has_nl, norm, map, args, \
+                                                          tiles, lb, st)
+    if (prec == kC128) {
+        GP_SHAPE(double, kShapes64, 1);
+        GP_SHAPE(double, kShapes64, 2);
+        GP_SHAPE(double, kShapes64, 0);
+        return cudaErrorInvalidValue;
+    }
+    GP_SHAPE(float, kShapes32, 1);
+    GP_SHAPE(float, kShapes32, 2);
+    GP_SHAPE(float, kShapes32, 3);
+    GP_SHAPE(float, kShapes32, 4);
+    GP_SHAPE(float, kShapes32, 0);
+#undef GP_SHAPE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace gp

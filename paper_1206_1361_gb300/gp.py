@@ -20,6 +20,8 @@ GP_C128, GP_C64 = 0, 1
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ENONFINITE, GP_ETIMEOUT, GP_EINTERNAL = (
     0, -1, -2, -3, -4, -5, -6)
 GP_MAX_EDGE = 8192
+GP_OPT_SWEEP_PATH, GP_OPT_TILE_SHAPE = 1, 2
+GP_PATH_AUTO, GP_PATH_EXACT, GP_PATH_TMA = 0, 1, 2
 
 ERROR_NAMES = {GP_EINVAL: "GP_EINVAL", GP_ENOMEM: "GP_ENOMEM", GP_ECUDA: "GP_ECUDA",
                GP_ENONFINITE: "GP_ENONFINITE", GP_ETIMEOUT: "GP_ETIMEOUT",
@@ -59,6 +61,10 @@ SIGNATURES = {
     "gp_step": (_int, [_vp, _i64]),
     "gp_observables": (_int, [_vp, ctypes.POINTER(gp_obs)]),
     "gp_sync": (_int, [_vp]),
+    "gp_set_option": (_int, [_vp, _int, _int]),
+    "gp_sweep_paths": (_int, [_vp, ctypes.POINTER(_int)]),
+    "gp_get_option": (_int, [_vp, _int, ctypes.POINTER(_int)]),
+    "gp_tile_shapes": (_int, [_int, ctypes.POINTER(_int)]),
     "gp_time_kernels": (_int, [_vp, _i64, ctypes.POINTER(ctypes.c_double), _int]),
     "gp_launches_per_step": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "gp_device_psi": (_int, [_vp, ctypes.POINTER(_vp)]),
@@ -190,6 +196,31 @@ def gp_launches_per_step(ctx):
     return k.value, o.value
 
 
+def gp_set_option(ctx, option, value):
+    _err(ctx, load_library().gp_set_option(ctx, int(option), int(value)))
+
+
+def gp_get_option(ctx, option):
+    v = ctypes.c_int()
+    _err(ctx, load_library().gp_get_option(ctx, int(option), ctypes.byref(v)))
+    return v.value
+
+
+def gp_tile_shapes(precision):
+    n = ctypes.c_int()
+    rc = load_library().gp_tile_shapes(int(precision), ctypes.byref(n))
+    if rc != GP_OK:
+        raise GPError(rc, gp_last_error(None))
+    return n.value
+
+
+def gp_sweep_paths(ctx):
+    """Sweep path per axis now in use: GP_PATH_EXACT or GP_PATH_TMA (0 if none)."""
+    p = (ctypes.c_int * 3)()
+    _err(ctx, load_library().gp_sweep_paths(ctx, p))
+    return tuple(p)
+
+
 def gp_sync(ctx):
     _err(ctx, load_library().gp_sync(ctx))
 
@@ -276,6 +307,13 @@ class Solver:
 
     def sync(self):
         gp_sync(self.ctx)
+
+    def set_path(self, path):
+        gp_set_option(self.ctx, GP_OPT_SWEEP_PATH, path)
+        return self
+
+    def paths(self):
+        return gp_sweep_paths(self.ctx)
 
     def close(self):
         if self.ctx:
