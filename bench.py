@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="budget of the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the complex64 precision-form measurement")
     ap.add_argument("--probe", type=int, default=0, metavar="N",
                     help="profiling aid: load the Gaussian seed, run N real-time SSCN "
                          "steps of the workload, print nothing and exit")
@@ -392,6 +394,10 @@ def run_ours(args):
                    "sample": "FP64 CPU oracle, %d SSCN steps of the same 256^3 real-time "
                              "state, observables every 10th" % n}
 
+        forms = None
+        if world == 1 and not args.no_forms:
+            forms = {"precision": precision_form(gp, torch, stream, args)}
+
         extra = {"prep_imag_steps": prep, "prep_dmu": dmu,
                  "norm_drift": abs(obs_end["norm"] / obs0["norm"] - 1),
                  "rms_r_range": [min(rms_t), max(rms_t)] if rms_t else None,
@@ -402,7 +408,7 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic", "config": config_dict(case, extra),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": launches}
+                "gpu_launches": launches, "forms": forms}
         if rank == 0:
             print(json.dumps(line), flush=True)
     finally:
@@ -411,6 +417,69 @@ def run_ours(args):
             import torch.distributed as dist
             dist.destroy_process_group()
     return 0
+
+
+def precision_form(gp, torch, stream, args):
+    """The complex64 form on 512 x 512 x 256 (real time from the Gaussian
+    seed, g = 50): throughput, the HBM roofline of its dominant sweep, and the
+    error of every observable after 1000 steps against an FP64 GPU run of the
+    same case (FP64 reductions and tables on both)."""
+    from paper_1206_1361_gb300.workloads import PRECISION_512 as case
+    steps = case.steps
+    out = {}
+    obs, psi = {}, {}
+    for prec in (gp.GP_C64, gp.GP_C128):
+        ctx = gp.gp_create(case.shape, case.h, case.dt, *case.trap, case.g, gp.GP_REAL, prec,
+                           stream)
+        try:
+            gp.gp_load(ctx, None)
+            gp.gp_step(ctx, 10)
+            gp.gp_observables(ctx)
+            gp.gp_load(ctx, None)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(steps // STEPS_PER_BENCH_STEP):
+                gp.gp_step(ctx, STEPS_PER_BENCH_STEP)
+                o = gp.gp_observables(ctx)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            obs[prec] = o
+            dt = torch.complex64 if prec == gp.GP_C64 else torch.complex128
+            buf = torch.empty(case.points, dtype=dt, device="cuda")
+            gp.gp_store(ctx, buf)
+            psi[prec] = buf
+            rate = steps * case.points / (ms / 1e3)
+            entry = {"value": rate, "unit": UNIT, "ms_per_sscn_step": ms / steps,
+                     "paths": list(gp.gp_sweep_paths(ctx))}
+            if prec == gp.GP_C64:
+                kt = gp.gp_time_kernels(ctx, 10)
+                sweeps = {k: v for k, v in kt.items() if k.startswith("sweep") and v > 0}
+                dom = max(sweeps, key=sweeps.get)
+                peaks = measured_peaks()
+                peak = peaks.get("hbm_gbs") or FALLBACK_HBM_GBS
+                ach = SWEEP_BYTES_PER_POINT[1] * case.points / (sweeps[dom] * 1e-3) / 1e9
+                entry["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                     "frac": ach / peak, "kernel": dom,
+                                     "traffic": profiled_traffic(dom, case.name),
+                                     "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
+                                     "kernel_ms": {k: round(v, 5) for k, v in kt.items()},
+                                     "step_hbm_frac": (3 * SWEEP_BYTES_PER_POINT[1] * case.points / 1e9)
+                                     / (sum(sweeps.values()) * 1e-3) / peak}
+            out["complex64" if prec == gp.GP_C64 else "complex128"] = entry
+        finally:
+            gp.gp_destroy(ctx)
+    a, b = psi[gp.GP_C64].to(torch.complex128), psi[gp.GP_C128]
+    err = {k: abs(obs[gp.GP_C64][k] - obs[gp.GP_C128][k]) / abs(obs[gp.GP_C128][k])
+           for k in ("norm", "mu", "energy", "rms_x", "rms_y", "rms_z", "rms_r")}
+    err["psi_rel_l2"] = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    del psi
+    return {"workload": case.name, "steps": steps, "grid": list(case.shape),
+            "complex64": out["complex64"], "complex128": out["complex128"],
+            "speedup_c64_over_fp64": out["complex64"]["value"] / out["complex128"]["value"],
+            "rel_error_vs_fp64": err}
 
 
 def run_probe(args):

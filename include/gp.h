@@ -72,7 +72,8 @@ enum {
     GP_ECUDA = -3,         /* a CUDA runtime call failed                     */
     GP_ENONFINITE = -4,    /* norm or an observable came out NaN / Inf       */
     GP_ETIMEOUT = -5,      /* a bounded device wait gave up                  */
-    GP_EINTERNAL = -6      /* internal invariant violated                    */
+    GP_EINTERNAL = -6,     /* internal invariant violated                    */
+    GP_EFULL = -7          /* a batch's memory cap cannot take the instance  */
 };
 
 /* Observables of the current state (calcnorm, calcmuen, calcrms). */
@@ -225,6 +226,49 @@ const char *gp_last_error(const gp_ctx *ctx);
 
 /* Release the context and its device memory.  NULL is a no-op. */
 void gp_destroy(gp_ctx *ctx);
+
+/* ------------------------------------------------------------------ batches
+ *
+ * A batch advances many independent problems -- each with its own grid
+ * (edges 3 .. 512 for complex64, 3 .. 384 for complex128), spacings, trap
+ * frequencies, g, dt and mode -- together: gp_batch_step runs n SSCN steps of
+ * every instance in one persistent kernel launch (per 2^30 work items), whose
+ * work items are (step, sweep or norm, instance, tile of 32 lines).  Each
+ * instance follows the same discretisation as a context (calcnu, calclux,
+ * calcluy, calcluz, calcnorm; observables calcmuen, calcrms), with the
+ * elimination done exactly in shared memory, so its result does not depend
+ * on which other instances share the batch.  One precision per batch;
+ * reductions in FP64.  Instance memory comes from the stream-ordered
+ * allocator and is charged against cap_bytes (gp_batch_footprint gives the
+ * charge); gp_batch_add returns GP_EFULL when the cap cannot take it.  Slots
+ * are small integers, reused after gp_batch_remove.  Errors from the device
+ * surface at the next synchronising call.
+ */
+typedef struct gp_batch gp_batch;
+
+int gp_batch_create(int precision, size_t cap_bytes, void *cuda_stream, gp_batch **out);
+int gp_batch_footprint(const gp_grid *grid, int precision, size_t *bytes);
+/* Add an instance (psi zero until gp_batch_load); *slot receives its id. */
+int gp_batch_add(gp_batch *b, const gp_grid *grid, const double dx[3], double dt,
+                 double gamma, double nu, double lambda, double g, int mode, int *slot);
+/* As gp_load for one slot (psi NULL: the normalised Gaussian seed). */
+int gp_batch_load(gp_batch *b, int slot, const void *psi, int64_t count, int on_device);
+/* As gp_store for one slot; synchronises. */
+int gp_batch_store(gp_batch *b, int slot, void *psi_out, int64_t count, int on_device);
+/* Quench one slot: new g and mode from its next step on. */
+int gp_batch_set_params(gp_batch *b, int slot, double g, int mode);
+/* Advance every instance in the batch by n steps (asynchronous). */
+int gp_batch_step(gp_batch *b, int64_t n);
+/* Observables of every instance, out[slot] for slot < capacity (unused slots
+ * get step = -1); synchronises. */
+int gp_batch_observables(gp_batch *b, gp_obs *out, int capacity);
+/* Release one slot's memory (stream-ordered). */
+int gp_batch_remove(gp_batch *b, int slot);
+/* Active instances, slot table size and bytes charged against the cap. */
+int gp_batch_info(gp_batch *b, int *active, int *slots, size_t *used_bytes);
+int gp_batch_sync(gp_batch *b);
+const char *gp_batch_last_error(const gp_batch *b);
+void gp_batch_destroy(gp_batch *b);
 
 #ifdef __cplusplus
 }

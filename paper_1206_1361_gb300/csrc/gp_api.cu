@@ -35,6 +35,7 @@ struct gp_ctx {
     int partial_cap = 0;
     double *obs_partials = nullptr; // observables scratch (rows + finish stage)
     double *obs_tab = nullptr;      // x^2 and w^2 x^2 / 2 per axis
+    float *obs_tab32 = nullptr;     // their FP32 roundings
     double *sums = nullptr;         // kObsWidth
     double *scale = nullptr;        // pending imaginary-time scale
     double *norm_dev = nullptr;     // last norm N
@@ -117,14 +118,7 @@ void thomas_tables(int m, std::complex<double> kappa, std::vector<double2> &cp,
 {
     cp.resize(m);
     mult.resize(m);
-    std::complex<double> prev = 0.0;
-    for (int i = 0; i < m; ++i) {
-        const std::complex<double> f = 1.0 / ((1.0 + 2.0 * kappa) + kappa * prev);
-        const std::complex<double> c = -kappa * f;
-        mult[i] = make_double2(f.real(), f.imag());
-        cp[i] = make_double2(c.real(), c.imag());
-        prev = c;
-    }
+    gp::host_thomas_tables(m, kappa.real(), kappa.imag(), cp.data(), mult.data());
 }
 
 int alloc(gp_ctx *c, void **p, size_t bytes)
@@ -170,6 +164,8 @@ int upload_tables(gp_ctx *c)
             }
         x2.insert(x2.end(), v.begin(), v.end());
         GP_CK(c, cudaMemcpy(c->obs_tab, x2.data(), x2.size() * sizeof(double), cudaMemcpyHostToDevice));
+        std::vector<float> x2f(x2.begin(), x2.end());
+        GP_CK(c, cudaMemcpy(c->obs_tab32, x2f.data(), x2f.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
     for (int mode = 0; mode < 2; ++mode) {
         for (int k = 0; k < 3; ++k) {
@@ -244,6 +240,7 @@ void release(gp_ctx *c)
     fr(c->partials);
     fr(c->obs_partials);
     fr(c->obs_tab);
+    fr(c->obs_tab32);
     fr(c->sums);
     fr(c->scale);
     fr(c->norm_dev);
@@ -376,6 +373,8 @@ gp::ObsArgs obs_args(const gp_ctx *c)
     a.vx = a.z2 + c->grid.nz;
     a.vy = a.vx + c->grid.nx;
     a.vz = a.vy + c->grid.ny;
+    a.x2f = c->obs_tab32;
+    a.vxf = c->obs_tab32 + (c->grid.nx + c->grid.ny + c->grid.nz);
     a.scale = c->scale;
     return a;
 }
@@ -402,6 +401,19 @@ int read_errors(gp_ctx *c)
 }  // namespace
 
 void gp::set_thread_error(const char *msg) { g_create_error = msg ? msg : ""; }
+
+void gp::host_thomas_tables(int m, double kre, double kim, double2 *cp, double2 *mult)
+{
+    const std::complex<double> kappa(kre, kim);
+    std::complex<double> prev = 0.0;
+    for (int i = 0; i < m; ++i) {
+        const std::complex<double> f = 1.0 / ((1.0 + 2.0 * kappa) + kappa * prev);
+        const std::complex<double> c = -kappa * f;
+        mult[i] = make_double2(f.real(), f.imag());
+        cp[i] = make_double2(c.real(), c.imag());
+        prev = c;
+    }
+}
 
 void gp::set_converged(AxisTables &a, int m, const double2 *cp, const double2 *mult)
 {
@@ -536,6 +548,7 @@ int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, 
         if ((rc = alloc(c, (void **)&c->obs_partials, gp::obs_scratch_doubles(oa) * sizeof(double)))) return bail(rc);
         const int nt = grid->nx + grid->ny + grid->nz;
         if ((rc = alloc(c, (void **)&c->obs_tab, 2 * nt * sizeof(double)))) return bail(rc);
+        if ((rc = alloc(c, (void **)&c->obs_tab32, 2 * nt * sizeof(float)))) return bail(rc);
     }
     if ((rc = alloc(c, (void **)&c->sums, gp::kObsWidth * sizeof(double)))) return bail(rc);
     if ((rc = alloc(c, (void **)&c->scale, sizeof(double)))) return bail(rc);

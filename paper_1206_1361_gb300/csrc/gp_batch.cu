@@ -1,0 +1,1104 @@
+// gp_batch.cu -- many independent SSCN problems (different grids, traps, g,
+// dt and modes) advanced together by one persistent kernel.
+//
+// Work is a queue of items (step s, phase p, instance i, tile t) in that
+// order: phases are the x, y and z Crank-Nicolson sweeps (calclux, calcluy,
+// calcluz; calcnu fused into x) and, in imaginary time, the norm finish
+// (calcnorm).  A tile is 32 lines of one instance along one axis.  Resident
+// CTAs pop items from an atomic counter; before working on an item a CTA
+// waits until every item of the same instance's previous phase has
+// completed (a per-instance completion counter; the wait is bounded by
+// %globaltimer).  Items earlier in the queue are already held by running
+// CTAs, so the waits always end; instances at different phases overlap and
+// no grid-wide barrier separates the sweeps.
+//
+// Tile solver: one warp, 32 lines staged in shared memory (coalesced loads:
+// rows for x tiles, one point of 32 neighbouring lines at a time for y / z),
+// each lane runs the exact Thomas elimination of its line in place
+// (right-hand side (1 - 2 kappa) psi_i + kappa (psi_{i-1} + psi_{i+1}),
+// forward elimination overwriting psi with d', back substitution overwriting
+// d' with u), and the tile is written back.  Lines are at most 512 points
+// (complex64) / 384 (complex128).  The per-instance decomposition depends only
+// on the instance's own shape and its norm is summed in a fixed order, so an
+// instance's result is bit-identical alone and in any mix.
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gp.h"
+#include "sscn_accum.cuh"
+#include "sscn_internal.h"
+
+namespace {
+
+template <typename T> struct BC;
+template <> struct BC<double> { using c = double2; };
+template <> struct BC<float> { using c = float2; };
+
+template <typename T> __device__ __forceinline__ typename BC<T>::c mkb(T x, T y)
+{
+    typename BC<T>::c r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+
+constexpr int kTileLines = 32;
+constexpr int kObsWidthB = gp::kObsWidth;
+constexpr int kMaxEdge32 = 512, kMaxEdge64 = 384;
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+// Device descriptor of one active instance.
+struct Inst {
+    void *psi;
+    int n[3];               // nx, ny, nz
+    int mode;               // 0 imaginary, 1 real time
+    int last_axis;          // 1 (2D) or 2 (3D)
+    int tiles[3];           // tiles per axis (0 for z in 2D)
+    double kap[3];          // kappa / i (real time) or kappa (imaginary time)
+    const void *cp[3], *mult[3];    // current-mode tables, complex T, n - 1 entries
+    int conv[3];                    // index from which the table entries are constant
+    double2 cinf[3], minf[3];
+    const void *ph[3];              // current-mode potential factors, complex T, n entries
+    const double *x2[3], *v[3];     // x^2, omega^2 x^2 / 2 per axis (observables)
+    double dtg, w;
+    double *scale, *norm, *partials, *obs_rows;
+};
+
+struct LaunchArgs {
+    const Inst *inst;
+    int N;                  // active instances
+    int steps;
+    long long phase_total[4];       // items per phase of one step
+    long long ips;                  // items per step
+    const int *pref;                // [4][N + 1] item prefix per phase
+    const int *cum;                 // [N][4] items of the instance before phase p
+    const int *tot;                 // [N] items of the instance per step
+    unsigned long long *head;       // queue head
+    int *done;                      // [N] completed items per instance
+    int *err;
+    int *abort_flag;
+};
+
+__device__ __forceinline__ uint64_t gtime()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ bool wait_done(const int *ctr, int need, const int *abort_flag)
+{
+    if (ld_acquire(ctr) >= need) return true;
+    const uint64_t t0 = gtime();
+    while (ld_acquire(ctr) < need) {
+        if (*(volatile const int *)abort_flag) return false;
+        if (gtime() - t0 > kWaitNs) return false;
+        __nanosleep(64);
+    }
+    return true;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Crank-Nicolson arithmetic; MODE 0: kappa real, MODE 1: kappa = i k.
+template <typename T, int MODE> struct Cnb {
+    using C = typename BC<T>::c;
+    T k;
+    __device__ __forceinline__ C rhs(C l, C m, C r) const
+    {
+        if (MODE == 0) {
+            const T a = (T)1 - (T)2 * k;
+            return mkb<T>(fma(k, l.x + r.x, a * m.x), fma(k, l.y + r.y, a * m.y));
+        }
+        const T sx = l.x + r.x - (T)2 * m.x, sy = l.y + r.y - (T)2 * m.y;
+        return mkb<T>(fma(-k, sy, m.x), fma(k, sx, m.y));
+    }
+    __device__ __forceinline__ C fwd(C b, C d, C f) const      // (b + kappa d) f
+    {
+        if (MODE == 0) return mkb<T>(fma(k, d.x, b.x) * f.x, fma(k, d.y, b.y) * f.x);
+        const T tx = fma(-k, d.y, b.x), ty = fma(k, d.x, b.y);
+        return mkb<T>(fma(tx, f.x, -ty * f.y), fma(tx, f.y, ty * f.x));
+    }
+    __device__ __forceinline__ C back(C d, C c, C u) const     // d - c u
+    {
+        if (MODE == 0) return mkb<T>(fma(-c.x, u.x, d.x), fma(-c.x, u.y, d.y));
+        return mkb<T>(fma(-c.x, u.x, fma(c.y, u.y, d.x)), fma(-c.x, u.y, fma(-c.y, u.x, d.y)));
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ void phase_small(T a, T &c, T &s)
+{
+    if constexpr (sizeof(T) == 8) sincos(a, &s, &c);
+    else sincosf(a, &s, &c);
+}
+
+// The exact line update of one lane, in place on row[0 .. n-1] (shared
+// memory): calcnu first for x tiles (NL), the norm contribution of the
+// result into acc when NORM.
+template <typename T, int MODE>
+__device__ void solve_line(const Inst &I, int axis, typename BC<T>::c *row, int n, long long line,
+                           bool nl, bool norm, Acc<T> &acc)
+{
+    using C = typename BC<T>::c;
+    const int m = n - 1;
+    const Cnb<T, MODE> cn{(T)I.kap[axis]};
+    const C *cp = static_cast<const C *>(I.cp[axis]);
+    const C *mult = static_cast<const C *>(I.mult[axis]);
+    const int conv = I.conv[axis];
+    const C cinf = mkb<T>((T)I.cinf[axis].x, (T)I.cinf[axis].y);
+    const C minf = mkb<T>((T)I.minf[axis].x, (T)I.minf[axis].y);
+    if (nl) {
+        // x line: j = line % ny, k = line / ny
+        const int j = (int)(line % I.n[1]), k = (int)(line / I.n[1]);
+        const C *px = static_cast<const C *>(I.ph[0]);
+        const C qy = static_cast<const C *>(I.ph[1])[j], qz = static_cast<const C *>(I.ph[2])[k];
+        if (MODE == 0) {
+            const double sc = *I.scale;
+            const T f0 = (T)(sc * (double)qy.x * (double)qz.x), ac = (T)(I.dtg * sc * sc);
+            for (int i = 1; i <= m; ++i) {
+                C v = row[i];
+                T f;
+                if constexpr (sizeof(T) == 8) f = f0 * px[i].x * exp(-ac * (v.x * v.x + v.y * v.y));
+                else f = f0 * px[i].x * expf(-ac * (v.x * v.x + v.y * v.y));
+                row[i] = mkb<T>(v.x * f, v.y * f);
+            }
+        } else {
+            const C pyz = mkb<T>(qy.x * qz.x - qy.y * qz.y, qy.x * qz.y + qy.y * qz.x);
+            const T ac = (T)I.dtg;
+            for (int i = 1; i <= m; ++i) {
+                const C v = row[i], q = px[i];
+                T cs, sn;
+                phase_small<T>(ac * (v.x * v.x + v.y * v.y), cs, sn);
+                const T prx = fma(q.x, pyz.x, -q.y * pyz.y), pry = fma(q.x, pyz.y, q.y * pyz.x);
+                const T wx = fma(cs, v.x, sn * v.y), wy = fma(cs, v.y, -sn * v.x);
+                row[i] = mkb<T>(fma(prx, wx, -pry * wy), fma(prx, wy, pry * wx));
+            }
+        }
+    }
+    const C zero = mkb<T>((T)0, (T)0);
+    C left = zero, mid = row[1], d = zero;
+    for (int i = 1; i <= m; ++i) {
+        const C right = i < m ? row[i + 1] : zero;
+        const int t = i - 1;
+        d = cn.fwd(cn.rhs(left, mid, right), d, t < conv ? mult[t] : minf);
+        row[i] = d;
+        left = mid;
+        mid = right;
+    }
+    C u = d;
+    if (norm) acc.add(fma(u.x, u.x, u.y * u.y));
+    for (int i = m - 1; i >= 1; --i) {
+        const int t = i - 1;
+        u = cn.back(row[i], t < conv ? cp[t] : cinf, u);
+        row[i] = u;
+        if (norm) acc.add(fma(u.x, u.x, u.y * u.y));
+    }
+}
+
+// Line index -> offset of its point 0 and the stride between its points.
+__device__ __forceinline__ void line_geom(const Inst &I, int axis, long long L, long long &base,
+                                          long long &stride)
+{
+    const long long nx = I.n[0], ny = I.n[1];
+    if (axis == 0) { base = L * nx; stride = 1; }
+    else if (axis == 1) { base = (L / nx) * nx * ny + (L % nx); stride = nx; }
+    else { base = L; stride = nx * ny; }
+}
+
+template <typename T>
+__device__ void sweep_tile(const Inst &I, int axis, int tile, typename BC<T>::c *sm, int lane)
+{
+    using C = typename BC<T>::c;
+    const int n = I.n[axis];
+    const int P = n | 1;                   // odd row pitch: conflict-free columns
+    const long long lines = axis == 0 ? (long long)I.n[1] * I.n[2]
+                          : axis == 1 ? (long long)I.n[0] * I.n[2] : (long long)I.n[0] * I.n[1];
+    const long long L0 = (long long)tile * kTileLines;
+    const int rows = (int)min((long long)kTileLines, lines - L0);
+    C *psi = static_cast<C *>(I.psi);
+    long long base, stride;
+    if (axis == 0) {
+        for (int r = 0; r < rows; ++r) {
+            const C *src = psi + (L0 + r) * I.n[0];
+            for (int c = lane; c < n; c += 32) sm[r * P + c] = src[c];
+        }
+    } else if (lane < rows) {
+        line_geom(I, axis, L0 + lane, base, stride);
+        for (int c = 0; c < n; ++c) sm[lane * P + c] = psi[base + c * stride];
+    }
+    __syncwarp();
+    const bool norm = I.mode == 0 && axis == I.last_axis;
+    Acc<T> acc;
+    if (lane < rows) {
+        if (I.mode == 0) solve_line<T, 0>(I, axis, sm + lane * P, n, L0 + lane, axis == 0, norm, acc);
+        else solve_line<T, 1>(I, axis, sm + lane * P, n, L0 + lane, axis == 0, false, acc);
+    }
+    __syncwarp();
+    if (axis == 0) {
+        for (int r = 0; r < rows; ++r) {
+            C *dst = psi + (L0 + r) * I.n[0];
+            for (int c = lane; c < n; c += 32) dst[c] = sm[r * P + c];
+        }
+    } else if (lane < rows) {
+        line_geom(I, axis, L0 + lane, base, stride);
+        for (int c = 0; c < n; ++c) psi[base + c * stride] = sm[lane * P + c];
+    }
+    if (norm) {
+        const double v = warp_sum_d(acc.get());
+        if (lane == 0) I.partials[tile] = v;
+    }
+}
+
+// calcnorm of one instance: FP64 sum of its last-sweep tile partials in
+// fixed order, scale <- 1 / sqrt(N).
+__device__ void norm_item(const Inst &I, int lane, int *err)
+{
+    const int tiles = I.tiles[I.last_axis];
+    double v = 0.0;
+    for (int t = lane; t < tiles; t += 32) v += I.partials[t];
+    v = warp_sum_d(v);
+    if (lane == 0) {
+        const double nrm = I.w * v;
+        *I.norm = nrm;
+        if (!(nrm > 0.0) || !isfinite(nrm)) {
+            atomicOr(err, 1);
+            *I.scale = 1.0;
+        } else {
+            *I.scale = 1.0 / sqrt(nrm);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32) k_batch_steps(const LaunchArgs A)
+{
+    using C = typename BC<T>::c;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    const int lane = threadIdx.x;
+    const long long total = A.ips * A.steps;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(A.head, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if ((long long)it >= total) break;
+        if (*(volatile const int *)A.abort_flag) break;
+        const int s = (int)((long long)it / A.ips);
+        long long r = (long long)it - (long long)s * A.ips;
+        int p = 0;
+        while (r >= A.phase_total[p]) r -= A.phase_total[p++];
+        const int *pr = A.pref + p * (A.N + 1);
+        int lo = 0, hi = A.N;                  // pr[lo] <= r < pr[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (pr[mid] <= r) lo = mid;
+            else hi = mid;
+        }
+        const int i = lo, tile = (int)(r - pr[lo]);
+        const Inst &I = A.inst[i];
+        const int need = s * A.tot[i] + A.cum[i * 4 + p];
+        int ok = 1;
+        if (lane == 0) ok = wait_done(&A.done[i], need, A.abort_flag);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+            if (lane == 0) {
+                atomicOr(A.err, 2);
+                atomicExch(A.abort_flag, 1);
+            }
+            break;
+        }
+        __syncwarp();
+        __threadfence();
+        if (p < 3) sweep_tile<T>(I, p, tile, sm, lane);
+        else norm_item(I, lane, A.err);
+        __syncwarp();
+        __threadfence();
+        if (lane == 0) atomicAdd(&A.done[i], 1);
+    }
+}
+
+// ---------------------------------------------------------------- observables
+
+// One warp per x-line of every instance (line_pref: prefix of x-lines over
+// instances); per-line partials exactly as the single-grid observables pass.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_batch_obs(const Inst *inst, const long long *line_pref, int N)
+{
+    using C = typename BC<T>::c;
+    const int lane = threadIdx.x & 31;
+    const long long g = (long long)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (g >= line_pref[N]) return;
+    int lo = 0, hi = N;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (line_pref[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    const Inst &I = inst[lo];
+    const long long line = g - line_pref[lo];
+    const int nx = I.n[0], ny = I.n[1], nz = I.n[2];
+    const int j = (int)(line % ny), k = (int)(line / ny);
+    const long long plane = (long long)nx * ny;
+    const C *row = static_cast<const C *>(I.psi) + line * nx;
+    const bool has_y = j + 1 < ny, has_z = k + 1 < nz;
+    const C zero = mkb<T>((T)0, (T)0);
+    Acc<T> s0, sx, svx, s4, kx, ky, kz;
+    for (int i = lane; i < nx; i += 32) {
+        const C v = row[i];
+        const T am = fma(v.x, v.x, v.y * v.y);
+        s0.add(am);
+        sx.add_prod((T)I.x2[0][i], am);
+        svx.add_prod((T)I.v[0][i], am);
+        s4.add_prod(am, am);
+        const C nb = (i + 1 < nx) ? row[i + 1] : zero;
+        kx.add_sq2(nb.x - v.x, nb.y - v.y);
+        const C ny_ = has_y ? row[i + nx] : zero;
+        ky.add_sq2(ny_.x - v.x, ny_.y - v.y);
+        if (nz > 1) {
+            const C nz_ = has_z ? row[i + plane] : zero;
+            kz.add_sq2(nz_.x - v.x, nz_.y - v.y);
+        }
+    }
+    const double r0 = warp_sum_d(s0.get()), rx = warp_sum_d(sx.get()), rv = warp_sum_d(svx.get()),
+                 r4 = warp_sum_d(s4.get()), qx = warp_sum_d(kx.get()), qy = warp_sum_d(ky.get()),
+                 qz = warp_sum_d(kz.get());
+    if (lane == 0) {
+        const double sc = *I.scale, s2 = sc * sc;
+        double *out = I.obs_rows + line * kObsWidthB;
+        out[0] = s2 * r0;
+        out[1] = s2 * rx;
+        out[2] = s2 * I.x2[1][j] * r0;
+        out[3] = s2 * I.x2[2][k] * r0;
+        out[4] = s2 * (rv + (I.v[1][j] + I.v[2][k]) * r0);
+        out[5] = s2 * s2 * r4;
+        out[6] = s2 * qx;
+        out[7] = s2 * qy;
+        out[8] = s2 * qz;
+    }
+}
+
+// One block per instance: its rows summed in a fixed order into sums[i][9].
+__global__ void __launch_bounds__(256) k_batch_obs_finish(const Inst *inst, double *sums)
+{
+    __shared__ double red[8];
+    const Inst &I = inst[blockIdx.x];
+    const long long rows = (long long)I.n[1] * I.n[2];
+    for (int q = 0; q < kObsWidthB; ++q) {
+        double v = 0.0;
+        for (long long r = threadIdx.x; r < rows; r += blockDim.x) v += I.obs_rows[r * kObsWidthB + q];
+        v = warp_sum_d(v);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double t = threadIdx.x < 8 ? red[threadIdx.x] : 0.0;
+            t = warp_sum_d(t);
+            if (threadIdx.x == 0) sums[(long long)blockIdx.x * kObsWidthB + q] = t;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void k_batch_apply_scale(typename BC<T>::c *psi, long long count, double *scale)
+{
+    const T s = (T)*scale;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
+         p += (long long)gridDim.x * blockDim.x) {
+        auto v = psi[p];
+        v.x *= s;
+        v.y *= s;
+        psi[p] = v;
+    }
+}
+
+__global__ void k_batch_set_one(double *x) { *x = 1.0; }
+
+}  // namespace
+
+// ====================================================================== host
+
+struct gp_batch_slot {
+    bool used = false;
+    gp_grid grid{};
+    double h[3]{}, dt = 0, w[3]{}, g = 0;
+    int mode = 0;
+    int64_t step = 0;
+    bool scale_pending = false;
+    void *psi = nullptr;            // device, points * elem
+    unsigned char *aux = nullptr;   // device: tables, scalars, partials, rows
+    size_t bytes = 0;               // footprint charged against the cap
+    // device pointers into aux
+    void *cp[2][3]{}, *mult[2][3]{}, *ph[2][3]{};
+    double *x2[3]{}, *v[3]{};
+    double *scale = nullptr, *norm = nullptr, *partials = nullptr, *obs_rows = nullptr;
+    gp::AxisTables conv[2][3];      // convergence fields per mode/axis (host)
+};
+
+struct gp_batch {
+    int prec = GP_C64;
+    size_t cap = 0, used = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<gp_batch_slot> slots;
+    bool dirty = true;
+    // launch structures
+    std::vector<int> active;        // slot ids in launch order
+    Inst *d_inst = nullptr;
+    int *d_ints = nullptr;          // pref | cum | tot | done | err | abort
+    size_t ints_cap = 0;
+    unsigned long long *d_head = nullptr;
+    int *d_err = nullptr;           // error bits, abort flag
+    long long *d_line_pref = nullptr;
+    double *d_sums = nullptr;
+    size_t inst_cap = 0;
+    double *h_sums = nullptr;       // pinned
+    int *h_err = nullptr;           // pinned
+    LaunchArgs args{};
+    size_t smem = 0;
+    int grid = 0;
+    long long obs_lines = 0;
+    std::string last_error;
+};
+
+namespace {
+
+int bfail(gp_batch *b, int code, const std::string &msg)
+{
+    if (b) b->last_error = msg;
+    else gp::set_thread_error(msg.c_str());
+    return code;
+}
+
+#define GP_BCK(b, call)                                                            \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA, \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+size_t elem(int prec) { return prec == GP_C128 ? 16 : 8; }
+
+bool batch_grid_ok(const gp_grid *g, int prec)
+{
+    const int mx = prec == GP_C128 ? kMaxEdge64 : kMaxEdge32;
+    auto ok = [&](int n) { return n >= 3 && n <= mx; };
+    return g && ok(g->nx) && ok(g->ny) && (g->nz == 1 || ok(g->nz));
+}
+
+int edge_of(const gp_grid &g, int k) { return k == 0 ? g.nx : (k == 1 ? g.ny : g.nz); }
+int axes_of(const gp_grid &g) { return g.nz > 1 ? 3 : 2; }
+
+long long lines_of(const gp_grid &g, int axis)
+{
+    const long long nx = g.nx, ny = g.ny, nz = g.nz;
+    return axis == 0 ? ny * nz : axis == 1 ? nx * nz : nx * ny;
+}
+
+int tiles_of(const gp_grid &g, int axis)
+{
+    if (axis >= axes_of(g)) return 0;
+    return (int)((lines_of(g, axis) + kTileLines - 1) / kTileLines);
+}
+
+// Layout of a slot's aux block (byte offsets), 256-byte aligned pieces.
+struct AuxLayout {
+    size_t cp[2][3], mult[2][3], ph[2][3], x2[3], v[3], scale, norm, partials, rows, total;
+};
+
+AuxLayout aux_layout(const gp_grid &g, int prec)
+{
+    AuxLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off += (bytes + 255) & ~size_t(255);
+        return at;
+    };
+    const size_t e = elem(prec);
+    for (int mode = 0; mode < 2; ++mode)
+        for (int k = 0; k < 3; ++k) {
+            const size_t n = edge_of(g, k);
+            L.cp[mode][k] = take(n * e);
+            L.mult[mode][k] = take(n * e);
+            L.ph[mode][k] = take(n * e);
+        }
+    for (int k = 0; k < 3; ++k) {
+        L.x2[k] = take(edge_of(g, k) * sizeof(double));
+        L.v[k] = take(edge_of(g, k) * sizeof(double));
+    }
+    L.scale = take(sizeof(double));
+    L.norm = take(sizeof(double));
+    L.partials = take((size_t)std::max(1, tiles_of(g, axes_of(g) - 1)) * sizeof(double));
+    L.rows = take((size_t)lines_of(g, 0) * gp::kObsWidth * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+size_t slot_bytes(const gp_grid &g, int prec)
+{
+    return (size_t)g.nx * g.ny * g.nz * elem(prec) + aux_layout(g, prec).total;
+}
+
+double coord_b(int n, double h, int i) { return n == 1 ? 0.0 : -0.5 * n * h + i * h; }
+
+// Upload tables, potential factors and observables tables of a slot.
+int upload_slot(gp_batch *b, gp_batch_slot &s)
+{
+    const AuxLayout L = aux_layout(s.grid, b->prec);
+    const int nd = axes_of(s.grid);
+    std::vector<unsigned char> host(L.total, 0);
+    auto put = [&](size_t off, const void *src, size_t bytes) { std::memcpy(host.data() + off, src, bytes); };
+    for (int mode = 0; mode < 2; ++mode)
+        for (int k = 0; k < 3; ++k) {
+            const int n = edge_of(s.grid, k), m = n - 1;
+            if (k < nd) {
+                const double kap = s.dt / (4.0 * s.h[k] * s.h[k]);
+                std::vector<double2> cp(m), mult(m);
+                gp::host_thomas_tables(m, mode == 0 ? kap : 0.0, mode == 0 ? 0.0 : kap, cp.data(), mult.data());
+                gp::AxisTables &a = s.conv[mode][k];
+                a.kre = mode == 0 ? kap : 0.0;
+                a.kim = mode == 0 ? 0.0 : kap;
+                gp::set_converged(a, m, cp.data(), mult.data());
+                if (b->prec == GP_C128) {
+                    put(L.cp[mode][k], cp.data(), m * sizeof(double2));
+                    put(L.mult[mode][k], mult.data(), m * sizeof(double2));
+                } else {
+                    std::vector<float2> c32(m), m32(m);
+                    for (int i = 0; i < m; ++i) {
+                        c32[i] = make_float2((float)cp[i].x, (float)cp[i].y);
+                        m32[i] = make_float2((float)mult[i].x, (float)mult[i].y);
+                    }
+                    put(L.cp[mode][k], c32.data(), m * sizeof(float2));
+                    put(L.mult[mode][k], m32.data(), m * sizeof(float2));
+                }
+            }
+            std::vector<double2> ph(n);
+            for (int i = 0; i < n; ++i) {
+                const double x = coord_b(n, s.h[k], i);
+                const double th = s.dt * 0.5 * s.w[k] * s.w[k] * x * x;
+                ph[i] = mode == 0 ? make_double2(std::exp(-th), 0.0) : make_double2(std::cos(th), -std::sin(th));
+            }
+            if (b->prec == GP_C128) put(L.ph[mode][k], ph.data(), n * sizeof(double2));
+            else {
+                std::vector<float2> p32(n);
+                for (int i = 0; i < n; ++i) p32[i] = make_float2((float)ph[i].x, (float)ph[i].y);
+                put(L.ph[mode][k], p32.data(), n * sizeof(float2));
+            }
+        }
+    for (int k = 0; k < 3; ++k) {
+        const int n = edge_of(s.grid, k);
+        std::vector<double> x2(n), v(n);
+        for (int i = 0; i < n; ++i) {
+            const double x = coord_b(n, s.h[k], i);
+            x2[i] = x * x;
+            v[i] = 0.5 * s.w[k] * s.w[k] * x * x;
+        }
+        put(L.x2[k], x2.data(), n * sizeof(double));
+        put(L.v[k], v.data(), n * sizeof(double));
+    }
+    const double one = 1.0;
+    put(L.scale, &one, sizeof(double));
+    GP_BCK(b, cudaMemcpyAsync(s.aux, host.data(), L.total, cudaMemcpyHostToDevice, b->stream));
+    GP_BCK(b, cudaStreamSynchronize(b->stream));       // `host` goes out of scope
+    for (int mode = 0; mode < 2; ++mode)
+        for (int k = 0; k < 3; ++k) {
+            s.cp[mode][k] = s.aux + L.cp[mode][k];
+            s.mult[mode][k] = s.aux + L.mult[mode][k];
+            s.ph[mode][k] = s.aux + L.ph[mode][k];
+        }
+    for (int k = 0; k < 3; ++k) {
+        s.x2[k] = reinterpret_cast<double *>(s.aux + L.x2[k]);
+        s.v[k] = reinterpret_cast<double *>(s.aux + L.v[k]);
+    }
+    s.scale = reinterpret_cast<double *>(s.aux + L.scale);
+    s.norm = reinterpret_cast<double *>(s.aux + L.norm);
+    s.partials = reinterpret_cast<double *>(s.aux + L.partials);
+    s.obs_rows = reinterpret_cast<double *>(s.aux + L.rows);
+    return GP_OK;
+}
+
+Inst make_inst(const gp_batch_slot &s, int prec)
+{
+    Inst I{};
+    I.psi = s.psi;
+    I.n[0] = s.grid.nx;
+    I.n[1] = s.grid.ny;
+    I.n[2] = s.grid.nz;
+    I.mode = s.mode;
+    I.last_axis = axes_of(s.grid) - 1;
+    for (int k = 0; k < 3; ++k) {
+        I.tiles[k] = tiles_of(s.grid, k);
+        I.kap[k] = k < axes_of(s.grid) ? s.dt / (4.0 * s.h[k] * s.h[k]) : 0.0;
+        I.cp[k] = s.cp[s.mode][k];
+        I.mult[k] = s.mult[s.mode][k];
+        const gp::AxisTables &a = s.conv[s.mode][k];
+        if (prec == GP_C128) {
+            I.conv[k] = a.conv64;
+            I.cinf[k] = a.cinf64;
+            I.minf[k] = a.minf64;
+        } else {
+            I.conv[k] = a.conv32;
+            I.cinf[k] = make_double2(a.cinf32.x, a.cinf32.y);
+            I.minf[k] = make_double2(a.minf32.x, a.minf32.y);
+        }
+        I.ph[k] = s.ph[s.mode][k];
+        I.x2[k] = s.x2[k];
+        I.v[k] = s.v[k];
+    }
+    I.dtg = s.dt * s.g;
+    I.w = s.h[0] * s.h[1] * (s.grid.nz > 1 ? s.h[2] : 1.0);
+    I.scale = s.scale;
+    I.norm = s.norm;
+    I.partials = s.partials;
+    I.obs_rows = s.obs_rows;
+    return I;
+}
+
+int ensure_capacity(gp_batch *b, size_t n_inst)
+{
+    if (n_inst <= b->inst_cap && b->d_inst) return GP_OK;
+    const size_t cap = std::max<size_t>(64, n_inst * 2);
+    if (b->d_inst) cudaFreeAsync(b->d_inst, b->stream);
+    if (b->d_line_pref) cudaFreeAsync(b->d_line_pref, b->stream);
+    if (b->d_sums) cudaFreeAsync(b->d_sums, b->stream);
+    if (b->h_sums) {
+        cudaStreamSynchronize(b->stream);
+        cudaFreeHost(b->h_sums);
+        b->h_sums = nullptr;
+    }
+    GP_BCK(b, cudaMallocAsync((void **)&b->d_inst, cap * sizeof(Inst), b->stream));
+    GP_BCK(b, cudaMallocAsync((void **)&b->d_line_pref, (cap + 1) * sizeof(long long), b->stream));
+    GP_BCK(b, cudaMallocAsync((void **)&b->d_sums, cap * gp::kObsWidth * sizeof(double), b->stream));
+    GP_BCK(b, cudaMallocHost((void **)&b->h_sums, cap * gp::kObsWidth * sizeof(double)));
+    b->inst_cap = cap;
+    return GP_OK;
+}
+
+// Rebuild the instance descriptors and the item prefix arrays.
+int prepare(gp_batch *b)
+{
+    if (!b->dirty) return GP_OK;
+    b->active.clear();
+    for (size_t i = 0; i < b->slots.size(); ++i)
+        if (b->slots[i].used) b->active.push_back((int)i);
+    const int N = (int)b->active.size();
+    if (N == 0) {
+        b->dirty = false;
+        return GP_OK;
+    }
+    int rc = ensure_capacity(b, N);
+    if (rc) return rc;
+    std::vector<Inst> inst(N);
+    std::vector<int> pref(4 * (N + 1), 0), cum(4 * N, 0), tot(N, 0);
+    std::vector<long long> lpref(N + 1, 0);
+    long long ptot[4] = {0, 0, 0, 0};
+    int maxP = 1;
+    for (int a = 0; a < N; ++a) {
+        const gp_batch_slot &s = b->slots[b->active[a]];
+        inst[a] = make_inst(s, b->prec);
+        int items[4];
+        for (int k = 0; k < 3; ++k) items[k] = tiles_of(s.grid, k);
+        items[3] = s.mode == 0 ? 1 : 0;
+        int c = 0;
+        for (int p = 0; p < 4; ++p) {
+            cum[a * 4 + p] = c;
+            c += items[p];
+            pref[p * (N + 1) + a + 1] = pref[p * (N + 1) + a] + items[p];
+            ptot[p] += items[p];
+        }
+        tot[a] = c;
+        lpref[a + 1] = lpref[a] + lines_of(s.grid, 0);
+        for (int k = 0; k < axes_of(s.grid); ++k) maxP = std::max(maxP, edge_of(s.grid, k) | 1);
+    }
+    const size_t nints = pref.size() + cum.size() + tot.size() + N;
+    if (nints > b->ints_cap) {
+        if (b->d_ints) cudaFreeAsync(b->d_ints, b->stream);
+        b->ints_cap = nints * 2;
+        GP_BCK(b, cudaMallocAsync((void **)&b->d_ints, b->ints_cap * sizeof(int), b->stream));
+    }
+    std::vector<int> ints;
+    ints.insert(ints.end(), pref.begin(), pref.end());
+    ints.insert(ints.end(), cum.begin(), cum.end());
+    ints.insert(ints.end(), tot.begin(), tot.end());
+    GP_BCK(b, cudaMemcpyAsync(b->d_inst, inst.data(), N * sizeof(Inst), cudaMemcpyHostToDevice, b->stream));
+    GP_BCK(b, cudaMemcpyAsync(b->d_ints, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    GP_BCK(b, cudaMemcpyAsync(b->d_line_pref, lpref.data(), (N + 1) * sizeof(long long),
+                              cudaMemcpyHostToDevice, b->stream));
+    GP_BCK(b, cudaStreamSynchronize(b->stream));
+    LaunchArgs &A = b->args;
+    A.inst = b->d_inst;
+    A.N = N;
+    for (int p = 0; p < 4; ++p) A.phase_total[p] = ptot[p];
+    A.ips = ptot[0] + ptot[1] + ptot[2] + ptot[3];
+    A.pref = b->d_ints;
+    A.cum = A.pref + pref.size();
+    A.tot = A.cum + cum.size();
+    A.done = const_cast<int *>(A.tot) + N;
+    A.err = b->d_err;
+    A.abort_flag = b->d_err + 1;
+    A.head = b->d_head;
+    b->smem = (size_t)kTileLines * maxP * elem(b->prec);
+    b->obs_lines = lpref[N];
+    // persistent grid: as many warps as stay resident
+    int per_sm = 0, sms = 0, dev = 0;
+    GP_BCK(b, cudaGetDevice(&dev));
+    GP_BCK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (b->prec == GP_C128) {
+        GP_BCK(b, cudaFuncSetAttribute(k_batch_steps<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+        GP_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_steps<double>, 32, b->smem));
+    } else {
+        GP_BCK(b, cudaFuncSetAttribute(k_batch_steps<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+        GP_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_steps<float>, 32, b->smem));
+    }
+    b->grid = std::max(1, per_sm) * sms;
+    b->dirty = false;
+    return GP_OK;
+}
+
+int batch_sync_errors(gp_batch *b)
+{
+    GP_BCK(b, cudaMemcpyAsync(b->h_err, b->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    GP_BCK(b, cudaStreamSynchronize(b->stream));
+    if (b->h_err[0] & 2) return bfail(b, GP_ETIMEOUT, "a batched step's bounded dependency wait gave up");
+    if (b->h_err[0] & 1) return bfail(b, GP_ENONFINITE, "a norm became non-finite or zero");
+    return GP_OK;
+}
+
+int materialize(gp_batch *b, gp_batch_slot &s)
+{
+    if (!s.scale_pending) return GP_OK;
+    const long long n = (long long)s.grid.nx * s.grid.ny * s.grid.nz;
+    const int blocks = (int)std::min<long long>(1024, (n + 255) / 256);
+    if (b->prec == GP_C128) k_batch_apply_scale<double><<<blocks, 256, 0, b->stream>>>((double2 *)s.psi, n, s.scale);
+    else k_batch_apply_scale<float><<<blocks, 256, 0, b->stream>>>((float2 *)s.psi, n, s.scale);
+    GP_BCK(b, cudaGetLastError());
+    k_batch_set_one<<<1, 1, 0, b->stream>>>(s.scale);
+    GP_BCK(b, cudaGetLastError());
+    s.scale_pending = false;
+    return GP_OK;
+}
+
+bool valid_slot(gp_batch *b, int slot)
+{
+    return b && slot >= 0 && slot < (int)b->slots.size() && b->slots[slot].used;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+int gp_batch_footprint(const gp_grid *grid, int precision, size_t *bytes)
+{
+    if ((precision != GP_C128 && precision != GP_C64) || !batch_grid_ok(grid, precision) || !bytes)
+        return bfail(nullptr, GP_EINVAL, "gp_batch_footprint: invalid grid or precision");
+    *bytes = slot_bytes(*grid, precision);
+    return GP_OK;
+}
+
+int gp_batch_create(int precision, size_t cap_bytes, void *cuda_stream, gp_batch **out)
+{
+    if (out) *out = nullptr;
+    if (!out || (precision != GP_C128 && precision != GP_C64) || cap_bytes == 0)
+        return bfail(nullptr, GP_EINVAL, "gp_batch_create: bad precision or zero cap");
+    gp_batch *b = new (std::nothrow) gp_batch;
+    if (!b) return bfail(nullptr, GP_ENOMEM, "gp_batch_create: host allocation failed");
+    b->prec = precision;
+    b->cap = cap_bytes;
+    cudaError_t e = cudaSuccess;
+    if (cuda_stream) b->stream = (cudaStream_t)cuda_stream;
+    else {
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        b->own_stream = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_head, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_err, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_err, 2 * sizeof(int));
+    if (e != cudaSuccess) {
+        std::string msg = std::string("gp_batch_create: ") + cudaGetErrorString(e);
+        gp_batch_destroy(b);
+        return bfail(nullptr, e == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA, msg);
+    }
+    *out = b;
+    return GP_OK;
+}
+
+int gp_batch_add(gp_batch *b, const gp_grid *grid, const double dx[3], double dt, double gamma,
+                 double nu, double lambda, double g, int mode, int *slot)
+{
+    if (slot) *slot = -1;
+    if (!b || !slot || !dx) return bfail(b, GP_EINVAL, "gp_batch_add: null argument");
+    if (!batch_grid_ok(grid, b->prec))
+        return bfail(b, GP_EINVAL, "gp_batch_add: invalid grid (edges 3 .. 512 complex64, 384 complex128; nz == 1 for 2D)");
+    const int nd = grid->nz > 1 ? 3 : 2;
+    for (int k = 0; k < nd; ++k)
+        if (!(dx[k] > 0) || !std::isfinite(dx[k])) return bfail(b, GP_EINVAL, "gp_batch_add: dx must be > 0");
+    if (!(dt > 0) || !std::isfinite(dt) || !(gamma >= 0) || !(nu >= 0) || !(lambda >= 0) ||
+        !std::isfinite(g) || (mode != GP_IMAG && mode != GP_REAL))
+        return bfail(b, GP_EINVAL, "gp_batch_add: bad dt, trap, g or mode");
+    const size_t bytes = slot_bytes(*grid, b->prec);
+    if (b->used + bytes > b->cap) return bfail(b, GP_EFULL, "gp_batch_add: the memory cap is reached");
+    int id = -1;
+    for (size_t i = 0; i < b->slots.size(); ++i)
+        if (!b->slots[i].used) { id = (int)i; break; }
+    if (id < 0) {
+        b->slots.emplace_back();
+        id = (int)b->slots.size() - 1;
+    }
+    gp_batch_slot &s = b->slots[id];
+    s = gp_batch_slot{};
+    s.grid = *grid;
+    s.h[0] = dx[0];
+    s.h[1] = dx[1];
+    s.h[2] = nd == 3 ? dx[2] : 1.0;
+    s.dt = dt;
+    s.w[0] = gamma;
+    s.w[1] = nu;
+    s.w[2] = nd == 3 ? lambda : 0.0;
+    s.g = g;
+    s.mode = mode;
+    s.bytes = bytes;
+    const size_t psi_bytes = (size_t)grid->nx * grid->ny * grid->nz * elem(b->prec);
+    cudaError_t e = cudaMallocAsync(&s.psi, psi_bytes, b->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&s.aux, aux_layout(s.grid, b->prec).total, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.psi, 0, psi_bytes, b->stream);
+    if (e != cudaSuccess) {
+        if (s.psi) cudaFreeAsync(s.psi, b->stream);
+        if (s.aux) cudaFreeAsync(s.aux, b->stream);
+        s = gp_batch_slot{};
+        return bfail(b, e == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA,
+                     std::string("gp_batch_add: ") + cudaGetErrorString(e));
+    }
+    s.used = true;
+    int rc = upload_slot(b, s);
+    if (rc) {
+        cudaFreeAsync(s.psi, b->stream);
+        cudaFreeAsync(s.aux, b->stream);
+        s = gp_batch_slot{};
+        return rc;
+    }
+    b->used += bytes;
+    b->dirty = true;
+    *slot = id;
+    return GP_OK;
+}
+
+int gp_batch_load(gp_batch *b, int slot, const void *psi, int64_t count, int on_device)
+{
+    if (!valid_slot(b, slot)) return bfail(b, GP_EINVAL, "gp_batch_load: bad slot");
+    gp_batch_slot &s = b->slots[slot];
+    const long long n = (long long)s.grid.nx * s.grid.ny * s.grid.nz;
+    s.step = 0;
+    s.scale_pending = false;
+    if (!psi) {
+        GP_BCK(b, gp::launch_seed(b->prec, s.psi, s.grid.nx, s.grid.ny, s.grid.nz, s.h, s.w, b->stream));
+        // normalise: FP64 norm partials over the seed, finish into the scale
+        double *part = s.obs_rows;          // scratch: the rows are rewritten by observables
+        gp::Partials pp{part, 1};
+        const int blocks = (int)std::min<long long>(lines_of(s.grid, 0) * gp::kObsWidth, gp::kReduceBlocks);
+        GP_BCK(b, gp::launch_norm_partials(b->prec, s.psi, n, pp, blocks, b->stream));
+        const double w = s.h[0] * s.h[1] * (s.grid.nz > 1 ? s.h[2] : 1.0);
+        GP_BCK(b, gp::launch_norm_finish(part, blocks, w, s.scale, s.norm, b->d_err, b->stream));
+        s.scale_pending = true;
+        int rc = materialize(b, s);
+        if (rc) return rc;
+        GP_BCK(b, cudaStreamSynchronize(b->stream));
+        return GP_OK;
+    }
+    if (count != n) return bfail(b, GP_EINVAL, "gp_batch_load: count != nx*ny*nz");
+    GP_BCK(b, cudaMemcpyAsync(s.psi, psi, (size_t)n * elem(b->prec),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
+    GP_BCK(b, gp::launch_zero_boundary(b->prec, s.psi, s.grid.nx, s.grid.ny, s.grid.nz, b->stream));
+    k_batch_set_one<<<1, 1, 0, b->stream>>>(s.scale);
+    GP_BCK(b, cudaGetLastError());
+    GP_BCK(b, cudaStreamSynchronize(b->stream));
+    return GP_OK;
+}
+
+int gp_batch_store(gp_batch *b, int slot, void *out, int64_t count, int on_device)
+{
+    if (!valid_slot(b, slot) || !out) return bfail(b, GP_EINVAL, "gp_batch_store: bad slot or buffer");
+    gp_batch_slot &s = b->slots[slot];
+    const long long n = (long long)s.grid.nx * s.grid.ny * s.grid.nz;
+    if (count != n) return bfail(b, GP_EINVAL, "gp_batch_store: count != nx*ny*nz");
+    int rc = materialize(b, s);
+    if (rc) return rc;
+    GP_BCK(b, cudaMemcpyAsync(out, s.psi, (size_t)n * elem(b->prec),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+    GP_BCK(b, cudaStreamSynchronize(b->stream));
+    return batch_sync_errors(b);
+}
+
+int gp_batch_set_params(gp_batch *b, int slot, double g, int mode)
+{
+    if (!valid_slot(b, slot) || !std::isfinite(g) || (mode != GP_IMAG && mode != GP_REAL))
+        return bfail(b, GP_EINVAL, "gp_batch_set_params: bad slot, g or mode");
+    gp_batch_slot &s = b->slots[slot];
+    if (mode != s.mode) {
+        int rc = materialize(b, s);
+        if (rc) return rc;
+    }
+    s.g = g;
+    s.mode = mode;
+    b->dirty = true;
+    return GP_OK;
+}
+
+int gp_batch_remove(gp_batch *b, int slot)
+{
+    if (!valid_slot(b, slot)) return bfail(b, GP_EINVAL, "gp_batch_remove: bad slot");
+    gp_batch_slot &s = b->slots[slot];
+    cudaFreeAsync(s.psi, b->stream);
+    cudaFreeAsync(s.aux, b->stream);
+    b->used -= s.bytes;
+    s = gp_batch_slot{};
+    b->dirty = true;
+    return GP_OK;
+}
+
+int gp_batch_step(gp_batch *b, int64_t n)
+{
+    if (!b || n < 0) return bfail(b, GP_EINVAL, "gp_batch_step: bad arguments");
+    int rc = prepare(b);
+    if (rc) return rc;
+    if (n == 0 || b->active.empty()) return GP_OK;
+    LaunchArgs A = b->args;
+    const int N = A.N;
+    // at most 2^31 items per launch: split long runs into chunks of steps
+    const long long max_steps = std::max<long long>(1, (1LL << 30) / std::max<long long>(1, A.ips));
+    for (int64_t done = 0; done < n;) {
+        const int k = (int)std::min<long long>(n - done, max_steps);
+        A.steps = k;
+        GP_BCK(b, cudaMemsetAsync(b->d_head, 0, sizeof(unsigned long long), b->stream));
+        GP_BCK(b, cudaMemsetAsync(A.done, 0, N * sizeof(int), b->stream));
+        GP_BCK(b, cudaMemsetAsync(A.abort_flag, 0, sizeof(int), b->stream));
+        if (b->prec == GP_C128) k_batch_steps<double><<<b->grid, 32, b->smem, b->stream>>>(A);
+        else k_batch_steps<float><<<b->grid, 32, b->smem, b->stream>>>(A);
+        GP_BCK(b, cudaGetLastError());
+        done += k;
+    }
+    for (int id : b->active) {
+        b->slots[id].step += n;
+        if (b->slots[id].mode == GP_IMAG) b->slots[id].scale_pending = true;
+    }
+    return GP_OK;
+}
+
+int gp_batch_observables(gp_batch *b, gp_obs *out, int capacity)
+{
+    if (!b || (!out && capacity > 0)) return bfail(b, GP_EINVAL, "gp_batch_observables: null argument");
+    int rc = prepare(b);
+    if (rc) return rc;
+    for (int i = 0; i < capacity; ++i) {
+        std::memset(&out[i], 0, sizeof(gp_obs));
+        out[i].step = -1;
+    }
+    if (b->active.empty()) return GP_OK;
+    const int N = b->args.N;
+    const long long warps = b->obs_lines;
+    const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+    if (b->prec == GP_C128) k_batch_obs<double><<<blocks, 256, 0, b->stream>>>(b->d_inst, b->d_line_pref, N);
+    else k_batch_obs<float><<<blocks, 256, 0, b->stream>>>(b->d_inst, b->d_line_pref, N);
+    GP_BCK(b, cudaGetLastError());
+    k_batch_obs_finish<<<N, 256, 0, b->stream>>>(b->d_inst, b->d_sums);
+    GP_BCK(b, cudaGetLastError());
+    GP_BCK(b, cudaMemcpyAsync(b->h_sums, b->d_sums, N * gp::kObsWidth * sizeof(double),
+                              cudaMemcpyDeviceToHost, b->stream));
+    rc = batch_sync_errors(b);
+    int bad = 0;
+    for (int a = 0; a < N; ++a) {
+        const int id = b->active[a];
+        if (id >= capacity) continue;
+        const gp_batch_slot &s = b->slots[id];
+        const double *q = b->h_sums + (size_t)a * gp::kObsWidth;
+        const double w = s.h[0] * s.h[1] * (s.grid.nz > 1 ? s.h[2] : 1.0);
+        const double nrm = w * q[0];
+        double kin = 0.5 * (q[6] / (s.h[0] * s.h[0]) + q[7] / (s.h[1] * s.h[1]));
+        if (s.grid.nz > 1) kin += 0.5 * q[8] / (s.h[2] * s.h[2]);
+        gp_obs &o = out[id];
+        o.norm = nrm;
+        o.mu = w * (kin + q[4] + s.g * q[5]) / nrm;
+        o.energy = w * (kin + q[4] + 0.5 * s.g * q[5]) / nrm;
+        o.rms_x = std::sqrt(q[1] / q[0]);
+        o.rms_y = std::sqrt(q[2] / q[0]);
+        o.rms_z = std::sqrt(q[3] / q[0]);
+        o.rms_r = std::sqrt((q[1] + q[2] + q[3]) / q[0]);
+        o.step = s.step;
+        o.t = s.step * s.dt;
+        if (!std::isfinite(o.mu) || !std::isfinite(o.norm)) bad = 1;
+    }
+    if (rc) return rc;
+    if (bad) return bfail(b, GP_ENONFINITE, "gp_batch_observables: non-finite result");
+    return GP_OK;
+}
+
+int gp_batch_info(gp_batch *b, int *active, int *slots, size_t *used_bytes)
+{
+    if (!b) return bfail(nullptr, GP_EINVAL, "gp_batch_info: null batch");
+    int n = 0;
+    for (const auto &s : b->slots) n += s.used ? 1 : 0;
+    if (active) *active = n;
+    if (slots) *slots = (int)b->slots.size();
+    if (used_bytes) *used_bytes = b->used;
+    return GP_OK;
+}
+
+int gp_batch_sync(gp_batch *b)
+{
+    if (!b) return bfail(nullptr, GP_EINVAL, "gp_batch_sync: null batch");
+    GP_BCK(b, cudaStreamSynchronize(b->stream));
+    return batch_sync_errors(b);
+}
+
+const char *gp_batch_last_error(const gp_batch *b)
+{
+    return b ? b->last_error.c_str() : gp_last_error(nullptr);
+}
+
+void gp_batch_destroy(gp_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto &s : b->slots) {
+        if (s.psi) cudaFreeAsync(s.psi, b->stream);
+        if (s.aux) cudaFreeAsync(s.aux, b->stream);
+    }
+    if (b->d_inst) cudaFreeAsync(b->d_inst, b->stream);
+    if (b->d_ints) cudaFreeAsync(b->d_ints, b->stream);
+    if (b->d_line_pref) cudaFreeAsync(b->d_line_pref, b->stream);
+    if (b->d_sums) cudaFreeAsync(b->d_sums, b->stream);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->d_head) cudaFree(b->d_head);
+    if (b->d_err) cudaFree(b->d_err);
+    if (b->h_sums) cudaFreeHost(b->h_sums);
+    if (b->h_err) cudaFreeHost(b->h_err);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"

@@ -107,6 +107,7 @@ cudaError_t launch_norm_partials(int prec, const void *psi, long long count,
 struct ObsArgs {
     int nx, ny, nz;
     const double *x2, *y2, *z2, *vx, *vy, *vz;
+    const float *x2f, *vxf;    // FP32 roundings of x2, vx (complex64 form)
     const double *scale;   // pending scale (device)
 };
 // Doubles of scratch launch_observables needs for this grid.
@@ -130,6 +131,11 @@ cudaError_t make_sweep_map(int prec, int shape, void *psi, int nx, int ny, int n
 cudaError_t launch_sweep_tma(int prec, int shape, int mode, int axis, const CUtensorMap &map,
                              const AxisTables &ax, const SweepGeom &g, const NonlinArgs *nl,
                              const Partials *norm_out, int *err, cudaStream_t st);
+
+// Forward-elimination tables of (I - kappa L) with m unknowns, kappa = kre +
+// i kim: mult_i = 1 / (1 + 2 kappa + kappa c'_{i-1}), c'_i = -kappa mult_i
+// (c'_0 = 0), stored 0-based in FP64 on the host.
+void host_thomas_tables(int m, double kre, double kim, double2 *cp, double2 *mult);
 
 // Record msg as the message gp_last_error(NULL) returns in this thread.
 void set_thread_error(const char *msg);

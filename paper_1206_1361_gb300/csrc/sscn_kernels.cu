@@ -18,6 +18,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "sscn_accum.cuh"
 #include "sscn_internal.h"
 
 namespace gp {
@@ -231,7 +232,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
             nl.a_coef = (T)dtg;
         }
     }
-    double nacc = 0.0;
+    Acc<T> nacc;
     C d = mk<T>((T)0, (T)0);
     if (active) {
 #pragma unroll 2
@@ -256,7 +257,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
         vk = cn.fwd(pk, mk<T>(d.x + other.x, d.y + other.y), mid);
         const C u = Cn<T, MODE>::out(vk, pk);
         line[(long long)k * s] = u;
-        if (NORM) nacc += abs2d<T>(u);
+        if (NORM) nacc.add(abs2<T>(u));
     }
     const C vpair = shfl_xor16<T>(vk);
     C v = top ? vk : vpair;
@@ -268,12 +269,12 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
                 v = cn.back(wl[at], cp[t], v);
                 const C u = Cn<T, MODE>::out(v, line[at]);
                 line[at] = u;
-                if (NORM) nacc += abs2d<T>(u);
+                if (NORM) nacc.add(abs2<T>(u));
             }
         }
     }
     if (NORM) {
-        const double r = block_sum(nacc, red);
+        const double r = block_sum(nacc.get(), red);
         if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = r;
     }
 }
@@ -436,50 +437,43 @@ k_observables(const typename CT<T>::c *__restrict__ psi, ObsArgs a,
     const long long plane = (long long)nx * ny;
     const C *row = psi + line * nx;
     const bool has_y = j + 1 < ny, has_z = k + 1 < nz;
-    double s0 = 0, sx = 0, svx = 0, s4 = 0, kx = 0, ky = 0, kz = 0;
+    // per-point terms in T (exact FP64 for complex128, FP32 for complex64),
+    // summed per lane by Acc<T>, then FP64 across lanes and lines
+    const T *x2 = sizeof(T) == 8 ? (const T *)a.x2 : (const T *)a.x2f;
+    const T *vx = sizeof(T) == 8 ? (const T *)a.vx : (const T *)a.vxf;
+    Acc<T> s0, sx, svx, s4, kx, ky, kz;
+    const C zero = mk<T>((T)0, (T)0);
     for (int i = lane; i < nx; i += 32) {
         const C v = row[i];
-        const double vr = v.x, vi = v.y;
-        const double am = fma(vr, vr, vi * vi);
-        s0 += am;
-        sx = fma(a.x2[i], am, sx);
-        svx = fma(a.vx[i], am, svx);
-        s4 = fma(am, am, s4);
-        double dr, di;
-        const C nb = (i + 1 < nx) ? row[i + 1] : mk<T>((T)0, (T)0);
-        dr = (double)nb.x - vr;
-        di = (double)nb.y - vi;
-        kx = fma(dr, dr, fma(di, di, kx));
-        const C ny_ = has_y ? row[i + nx] : mk<T>((T)0, (T)0);
-        dr = (double)ny_.x - vr;
-        di = (double)ny_.y - vi;
-        ky = fma(dr, dr, fma(di, di, ky));
+        const T am = fma(v.x, v.x, v.y * v.y);
+        s0.add(am);
+        sx.add_prod(x2[i], am);
+        svx.add_prod(vx[i], am);
+        s4.add_prod(am, am);
+        const C nb = (i + 1 < nx) ? row[i + 1] : zero;
+        kx.add_sq2(nb.x - v.x, nb.y - v.y);
+        const C ny_ = has_y ? row[i + nx] : zero;
+        ky.add_sq2(ny_.x - v.x, ny_.y - v.y);
         if (nz > 1) {
-            const C nz_ = has_z ? row[i + plane] : mk<T>((T)0, (T)0);
-            dr = (double)nz_.x - vr;
-            di = (double)nz_.y - vi;
-            kz = fma(dr, dr, fma(di, di, kz));
+            const C nz_ = has_z ? row[i + plane] : zero;
+            kz.add_sq2(nz_.x - v.x, nz_.y - v.y);
         }
     }
-    s0 = warp_sum(s0);
-    sx = warp_sum(sx);
-    svx = warp_sum(svx);
-    s4 = warp_sum(s4);
-    kx = warp_sum(kx);
-    ky = warp_sum(ky);
-    kz = warp_sum(kz);
+    const double r0 = warp_sum(s0.get()), rx = warp_sum(sx.get()), rv = warp_sum(svx.get()),
+                 r4 = warp_sum(s4.get()), qx = warp_sum(kx.get()), qy = warp_sum(ky.get()),
+                 qz = warp_sum(kz.get());
     if (lane == 0) {
         const double sc = *a.scale, s2 = sc * sc;
         double *out = partials + line * kObsWidth;
-        out[0] = s2 * s0;
-        out[1] = s2 * sx;
-        out[2] = s2 * a.y2[j] * s0;
-        out[3] = s2 * a.z2[k] * s0;
-        out[4] = s2 * (svx + (a.vy[j] + a.vz[k]) * s0);
-        out[5] = s2 * s2 * s4;
-        out[6] = s2 * kx;
-        out[7] = s2 * ky;
-        out[8] = s2 * kz;
+        out[0] = s2 * r0;
+        out[1] = s2 * rx;
+        out[2] = s2 * a.y2[j] * r0;
+        out[3] = s2 * a.z2[k] * r0;
+        out[4] = s2 * (rv + (a.vy[j] + a.vz[k]) * r0);
+        out[5] = s2 * s2 * r4;
+        out[6] = s2 * qx;
+        out[7] = s2 * qy;
+        out[8] = s2 * qz;
     }
 }
 

@@ -32,6 +32,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include "sscn_accum.cuh"
 #include "sscn_internal.h"
 
 namespace gp {
@@ -286,7 +287,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
     __syncthreads();
 
     bool failed = false;
-    double nacc = 0.0;
+    Acc<T> nacc;
     if (producer) {
         if (lane == 0) {
             auto store = [&](int q) {
@@ -375,7 +376,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                         Cx *slot = at(q - 1, c);
                         const Cx u = CnT<T, MODE>::out(v, *slot);
                         *slot = u;
-                        if (NORM) nacc += (double)u.x * u.x + (double)u.y * u.y;
+                        if (NORM) nacc.add(fma(u.x, u.x, u.y * u.y));
                     }
                 } else if (last) {
                     // exact: v_m = d'_m, down through chunks q and q - 1
@@ -388,7 +389,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                         Cx *slot = at(qq, c);
                         const Cx u = CnT<T, MODE>::out(v, *slot);
                         *slot = u;
-                        if (NORM) nacc += (double)u.x * u.x + (double)u.y * u.y;
+                        if (NORM) nacc.add(fma(u.x, u.x, u.y * u.y));
                     }
                 }
             }
@@ -405,7 +406,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
     if (failed) atomicOr(args.err, kErrTimeout);
     if (NORM) {
         // block sum of the per-line norm contributions, fixed order
-        double v = nacc;
+        double v = nacc.get();
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         __syncthreads();
