@@ -17,15 +17,15 @@ LIB_PATH = os.path.join(HERE, "libgp.so")
 
 GP_IMAG, GP_REAL = 0, 1
 GP_C128, GP_C64 = 0, 1
-GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ENONFINITE, GP_ETIMEOUT, GP_EINTERNAL = (
-    0, -1, -2, -3, -4, -5, -6)
+GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ENONFINITE, GP_ETIMEOUT, GP_EINTERNAL, GP_EFULL = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 GP_MAX_EDGE = 8192
 GP_OPT_SWEEP_PATH, GP_OPT_TILE_SHAPE = 1, 2
 GP_PATH_AUTO, GP_PATH_EXACT, GP_PATH_TMA = 0, 1, 2
 
 ERROR_NAMES = {GP_EINVAL: "GP_EINVAL", GP_ENOMEM: "GP_ENOMEM", GP_ECUDA: "GP_ECUDA",
                GP_ENONFINITE: "GP_ENONFINITE", GP_ETIMEOUT: "GP_ETIMEOUT",
-               GP_EINTERNAL: "GP_EINTERNAL"}
+               GP_EINTERNAL: "GP_EINTERNAL", GP_EFULL: "GP_EFULL"}
 
 
 class GPError(RuntimeError):
@@ -73,6 +73,21 @@ SIGNATURES = {
                                 _vp]),
     "gp_last_error": (ctypes.c_char_p, [_vp]),
     "gp_destroy": (None, [_vp]),
+    "gp_batch_create": (_int, [_int, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
+    "gp_batch_footprint": (_int, [ctypes.POINTER(gp_grid), _int, ctypes.POINTER(ctypes.c_size_t)]),
+    "gp_batch_add": (_int, [_vp, ctypes.POINTER(gp_grid), ctypes.POINTER(ctypes.c_double), _dbl,
+                            _dbl, _dbl, _dbl, _dbl, _int, ctypes.POINTER(_int)]),
+    "gp_batch_load": (_int, [_vp, _int, _vp, _i64, _int]),
+    "gp_batch_store": (_int, [_vp, _int, _vp, _i64, _int]),
+    "gp_batch_set_params": (_int, [_vp, _int, _dbl, _int]),
+    "gp_batch_step": (_int, [_vp, _i64]),
+    "gp_batch_observables": (_int, [_vp, ctypes.POINTER(gp_obs), _int]),
+    "gp_batch_remove": (_int, [_vp, _int]),
+    "gp_batch_info": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int),
+                             ctypes.POINTER(ctypes.c_size_t)]),
+    "gp_batch_sync": (_int, [_vp]),
+    "gp_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "gp_batch_destroy": (None, [_vp]),
 }
 
 _lib = None
@@ -319,6 +334,157 @@ class Solver:
         if self.ctx:
             gp_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- batches
+
+def _berr(b, rc):
+    if rc != GP_OK:
+        msg = load_library().gp_batch_last_error(b)
+        raise GPError(rc, msg.decode() if msg else "")
+
+
+def gp_batch_create(precision=GP_C64, cap_bytes=1 << 34, cuda_stream=None):
+    out = _vp()
+    rc = load_library().gp_batch_create(int(precision), int(cap_bytes),
+                                        _stream_handle(cuda_stream), ctypes.byref(out))
+    if rc != GP_OK:
+        raise GPError(rc, gp_last_error(None))
+    return out.value
+
+
+def gp_batch_footprint(grid, precision=GP_C64):
+    gr = gp_grid(*[int(v) for v in grid])
+    b = ctypes.c_size_t()
+    rc = load_library().gp_batch_footprint(ctypes.byref(gr), int(precision), ctypes.byref(b))
+    if rc != GP_OK:
+        raise GPError(rc, gp_last_error(None))
+    return b.value
+
+
+def gp_batch_add(b, grid, dx, dt, gamma, nu, lam, g, mode=GP_IMAG):
+    gr = gp_grid(*[int(v) for v in grid])
+    h = (ctypes.c_double * 3)(*[float(v) for v in dx])
+    slot = _int()
+    _berr(b, load_library().gp_batch_add(b, ctypes.byref(gr), h, float(dt), float(gamma), float(nu),
+                                         float(lam), float(g), int(mode), ctypes.byref(slot)))
+    return slot.value
+
+
+def gp_batch_load(b, slot, psi=None, count=None, on_device=None):
+    addr, n, dev, _keep = _buffer(psi) if not isinstance(psi, int) else (psi, count, on_device, None)
+    if count is not None:
+        n = count
+    if on_device is not None:
+        dev = on_device
+    _berr(b, load_library().gp_batch_load(b, int(slot), addr, int(n or 0), int(dev or 0)))
+
+
+def gp_batch_store(b, slot, out, count=None, on_device=None):
+    addr, n, dev, _keep = _buffer(out) if not isinstance(out, int) else (out, count, on_device, None)
+    if count is not None:
+        n = count
+    if on_device is not None:
+        dev = on_device
+    _berr(b, load_library().gp_batch_store(b, int(slot), addr, int(n), int(dev)))
+    return out
+
+
+def gp_batch_set_params(b, slot, g, mode):
+    _berr(b, load_library().gp_batch_set_params(b, int(slot), float(g), int(mode)))
+
+
+def gp_batch_step(b, n):
+    _berr(b, load_library().gp_batch_step(b, int(n)))
+
+
+def gp_batch_observables(b, capacity):
+    """List of capacity dicts, one per slot id (step == -1: unused slot)."""
+    arr = (gp_obs * max(1, capacity))()
+    _berr(b, load_library().gp_batch_observables(b, arr, int(capacity)))
+    return [arr[i].as_dict() for i in range(capacity)]
+
+
+def gp_batch_remove(b, slot):
+    _berr(b, load_library().gp_batch_remove(b, int(slot)))
+
+
+def gp_batch_info(b):
+    """(active instances, slot table size, bytes charged against the cap)."""
+    a, s, u = _int(), _int(), ctypes.c_size_t()
+    _berr(b, load_library().gp_batch_info(b, ctypes.byref(a), ctypes.byref(s), ctypes.byref(u)))
+    return a.value, s.value, u.value
+
+
+def gp_batch_sync(b):
+    _berr(b, load_library().gp_batch_sync(b))
+
+
+def gp_batch_last_error(b=None):
+    msg = load_library().gp_batch_last_error(b)
+    return msg.decode() if msg else ""
+
+
+def gp_batch_destroy(b):
+    load_library().gp_batch_destroy(b)
+
+
+class Batch:
+    """Owns one batch; instances are addressed by slot id."""
+
+    def __init__(self, precision=GP_C64, cap_bytes=1 << 34, stream=None):
+        self.precision = precision
+        self.b = gp_batch_create(precision, cap_bytes, stream)
+        self.shapes = {}
+
+    def add(self, shape, dx, dt, gamma, nu, lam, g, mode=GP_IMAG, psi=None):
+        slot = gp_batch_add(self.b, shape, dx, dt, gamma, nu, lam, g, mode)
+        self.shapes[slot] = tuple(int(v) for v in shape)
+        gp_batch_load(self.b, slot, psi)
+        return slot
+
+    def step(self, n):
+        gp_batch_step(self.b, n)
+        return self
+
+    def observables(self):
+        cap = max(self.shapes) + 1 if self.shapes else 0
+        obs = gp_batch_observables(self.b, cap)
+        return {s: obs[s] for s in self.shapes}
+
+    def psi(self, slot):
+        nx, ny, nz = self.shapes[slot]
+        dt = np.complex128 if self.precision == GP_C128 else np.complex64
+        out = np.empty((nz, ny, nx), dt)
+        gp_batch_store(self.b, slot, out)
+        return out
+
+    def set_params(self, slot, g, mode):
+        gp_batch_set_params(self.b, slot, g, mode)
+
+    def remove(self, slot):
+        gp_batch_remove(self.b, slot)
+        self.shapes.pop(slot, None)
+
+    def info(self):
+        return gp_batch_info(self.b)
+
+    def close(self):
+        if self.b:
+            gp_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self
