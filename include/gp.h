@@ -175,7 +175,7 @@ int gp_device_psi(gp_ctx *ctx, void **dev_ptr);
  * that may only use the buffers it was given, or loops that cannot afford the
  * device-wide synchronisation of cudaMalloc / cudaFree.  It calls no device
  * allocator: the sweep's scratch and tables live in a static device array of
- * 16 MiB (+384 KiB of tables) that every GPU loading libgp holds until exit,
+ * 16 MiB (+512 KiB of tables) that every GPU loading libgp holds until exit,
  * so grids above 1048576 complex128 or 2097152 complex64 points are rejected
  * with GP_EINVAL.  The first call on each device looks up the array's device
  * address (make that first call before any stream capture).  All calls share
@@ -193,8 +193,10 @@ enum {
      * line per thread with the elimination scratch in device memory;
      * GP_PATH_TMA streams chunks of a tile of lines through shared memory with
      * TMA and back-substitutes over a window, which is only selected (and
-     * only accepted) when the window's truncation bound |c'|^(C+1) is below
-     * the precision's rounding (2^-26 complex64, 2^-55 complex128). */
+     * only accepted) when a window W <= C (the chunk) has a truncation bound
+     * max|c'|^(W+1) below 2^-40 (complex64) / 2^-55 (complex128): the
+     * truncation repeats identically every step, so it is kept far below
+     * one rounding. */
     GP_OPT_SWEEP_PATH = 1,
     /* Tile shape of the TMA sweep path: an index (0 .. GP_TILE_SHAPES - 1,
      * per precision) into the library's table of (lines per CTA, points per

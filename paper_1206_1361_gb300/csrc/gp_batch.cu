@@ -35,6 +35,7 @@
 #include "../../include/gp.h"
 #include "sscn_accum.cuh"
 #include "sscn_internal.h"
+#include "sscn_line.cuh"
 
 namespace {
 
@@ -63,10 +64,12 @@ struct Inst {
     int last_axis;          // 1 (2D) or 2 (3D)
     int tiles[3];           // tiles per axis (0 for z in 2D)
     double kap[3];          // kappa / i (real time) or kappa (imaginary time)
-    const void *cp[3], *mult[3];    // current-mode tables, complex T, n - 1 entries
+    const void *cp[3], *mult[3];    // current-mode tables (Coef<T>), n - 1 entries
     int conv[3];                    // index from which the table entries are constant
-    double2 cinf[3], minf[3];
-    const void *ph[3];              // current-mode potential factors, complex T, n entries
+    double2 cinf64[3], minf64[3];   // those constants, FP64 batches
+    float4 cinf32[3], minf32[3];    // and complex64 batches (hi + lo)
+    const void *ph[3];              // current-mode potential factors (Coef<T>), n entries
+    const float *th[3];             // dt omega^2 x^2 / 2 (FP32) per axis
     const double *x2[3], *v[3];     // x^2, omega^2 x^2 / 2 per axis (observables)
     double dtg, w;
     double *scale, *norm, *partials, *obs_rows;
@@ -120,39 +123,6 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
-// Crank-Nicolson arithmetic; MODE 0: kappa real, MODE 1: kappa = i k.
-template <typename T, int MODE> struct Cnb {
-    using C = typename BC<T>::c;
-    T k;
-    __device__ __forceinline__ C rhs(C l, C m, C r) const
-    {
-        if (MODE == 0) {
-            const T a = (T)1 - (T)2 * k;
-            return mkb<T>(fma(k, l.x + r.x, a * m.x), fma(k, l.y + r.y, a * m.y));
-        }
-        const T sx = l.x + r.x - (T)2 * m.x, sy = l.y + r.y - (T)2 * m.y;
-        return mkb<T>(fma(-k, sy, m.x), fma(k, sx, m.y));
-    }
-    __device__ __forceinline__ C fwd(C b, C d, C f) const      // (b + kappa d) f
-    {
-        if (MODE == 0) return mkb<T>(fma(k, d.x, b.x) * f.x, fma(k, d.y, b.y) * f.x);
-        const T tx = fma(-k, d.y, b.x), ty = fma(k, d.x, b.y);
-        return mkb<T>(fma(tx, f.x, -ty * f.y), fma(tx, f.y, ty * f.x));
-    }
-    __device__ __forceinline__ C back(C d, C c, C u) const     // d - c u
-    {
-        if (MODE == 0) return mkb<T>(fma(-c.x, u.x, d.x), fma(-c.x, u.y, d.y));
-        return mkb<T>(fma(-c.x, u.x, fma(c.y, u.y, d.x)), fma(-c.x, u.y, fma(-c.y, u.x, d.y)));
-    }
-};
-
-template <typename T>
-__device__ __forceinline__ void phase_small(T a, T &c, T &s)
-{
-    if constexpr (sizeof(T) == 8) sincos(a, &s, &c);
-    else sincosf(a, &s, &c);
-}
-
 // The exact line update of one lane, in place on row[0 .. n-1] (shared
 // memory): calcnu first for x tiles (NL), the norm contribution of the
 // result into acc when NORM.
@@ -161,40 +131,27 @@ __device__ void solve_line(const Inst &I, int axis, typename BC<T>::c *row, int 
                            bool nl, bool norm, Acc<T> &acc)
 {
     using C = typename BC<T>::c;
+    using F = typename Coef<T>::t;
     const int m = n - 1;
-    const Cnb<T, MODE> cn{(T)I.kap[axis]};
-    const C *cp = static_cast<const C *>(I.cp[axis]);
-    const C *mult = static_cast<const C *>(I.mult[axis]);
+    const LineOps<T, MODE> cn{(T)I.kap[axis]};
+    const F *cp = static_cast<const F *>(I.cp[axis]);
+    const F *mult = static_cast<const F *>(I.mult[axis]);
     const int conv = I.conv[axis];
-    const C cinf = mkb<T>((T)I.cinf[axis].x, (T)I.cinf[axis].y);
-    const C minf = mkb<T>((T)I.minf[axis].x, (T)I.minf[axis].y);
+    F cinf, minf;
+    if constexpr (sizeof(T) == 8) {
+        cinf = I.cinf64[axis];
+        minf = I.minf64[axis];
+    } else {
+        cinf = I.cinf32[axis];
+        minf = I.minf32[axis];
+    }
     if (nl) {
         // x line: j = line % ny, k = line / ny
         const int j = (int)(line % I.n[1]), k = (int)(line / I.n[1]);
-        const C *px = static_cast<const C *>(I.ph[0]);
-        const C qy = static_cast<const C *>(I.ph[1])[j], qz = static_cast<const C *>(I.ph[2])[k];
-        if (MODE == 0) {
-            const double sc = *I.scale;
-            const T f0 = (T)(sc * (double)qy.x * (double)qz.x), ac = (T)(I.dtg * sc * sc);
-            for (int i = 1; i <= m; ++i) {
-                C v = row[i];
-                T f;
-                if constexpr (sizeof(T) == 8) f = f0 * px[i].x * exp(-ac * (v.x * v.x + v.y * v.y));
-                else f = f0 * px[i].x * expf(-ac * (v.x * v.x + v.y * v.y));
-                row[i] = mkb<T>(v.x * f, v.y * f);
-            }
-        } else {
-            const C pyz = mkb<T>(qy.x * qz.x - qy.y * qz.y, qy.x * qz.y + qy.y * qz.x);
-            const T ac = (T)I.dtg;
-            for (int i = 1; i <= m; ++i) {
-                const C v = row[i], q = px[i];
-                T cs, sn;
-                phase_small<T>(ac * (v.x * v.x + v.y * v.y), cs, sn);
-                const T prx = fma(q.x, pyz.x, -q.y * pyz.y), pry = fma(q.x, pyz.y, q.y * pyz.x);
-                const T wx = fma(cs, v.x, sn * v.y), wy = fma(cs, v.y, -sn * v.x);
-                row[i] = mkb<T>(fma(prx, wx, -pry * wy), fma(prx, wy, pry * wx));
-            }
-        }
+        Calcnu<T, MODE> cu{};
+        cu.setup(static_cast<const F *>(I.ph[0]), static_cast<const F *>(I.ph[1]),
+                 static_cast<const F *>(I.ph[2]), I.th[0], I.th[1], I.th[2], j, k, I.dtg, I.scale);
+        for (int i = 1; i <= m; ++i) row[i] = cu.apply(row[i], i);
     }
     const C zero = mkb<T>((T)0, (T)0);
     C left = zero, mid = row[1], d = zero;
@@ -452,6 +409,7 @@ struct gp_batch_slot {
     // device pointers into aux
     void *cp[2][3]{}, *mult[2][3]{}, *ph[2][3]{};
     double *x2[3]{}, *v[3]{};
+    float *th[3]{};
     double *scale = nullptr, *norm = nullptr, *partials = nullptr, *obs_rows = nullptr;
     gp::AxisTables conv[2][3];      // convergence fields per mode/axis (host)
 };
@@ -525,7 +483,7 @@ int tiles_of(const gp_grid &g, int axis)
 
 // Layout of a slot's aux block (byte offsets), 256-byte aligned pieces.
 struct AuxLayout {
-    size_t cp[2][3], mult[2][3], ph[2][3], x2[3], v[3], scale, norm, partials, rows, total;
+    size_t cp[2][3], mult[2][3], ph[2][3], th[3], x2[3], v[3], scale, norm, partials, rows, total;
 };
 
 AuxLayout aux_layout(const gp_grid &g, int prec)
@@ -537,7 +495,8 @@ AuxLayout aux_layout(const gp_grid &g, int prec)
         off += (bytes + 255) & ~size_t(255);
         return at;
     };
-    const size_t e = elem(prec);
+    const size_t e = 16;                   // double2 or float4 (hi + lo) coefficients
+    (void)prec;
     for (int mode = 0; mode < 2; ++mode)
         for (int k = 0; k < 3; ++k) {
             const size_t n = edge_of(g, k);
@@ -546,6 +505,7 @@ AuxLayout aux_layout(const gp_grid &g, int prec)
             L.ph[mode][k] = take(n * e);
         }
     for (int k = 0; k < 3; ++k) {
+        L.th[k] = take(edge_of(g, k) * sizeof(float));
         L.x2[k] = take(edge_of(g, k) * sizeof(double));
         L.v[k] = take(edge_of(g, k) * sizeof(double));
     }
@@ -577,22 +537,16 @@ int upload_slot(gp_batch *b, gp_batch_slot &s)
             if (k < nd) {
                 const double kap = s.dt / (4.0 * s.h[k] * s.h[k]);
                 std::vector<double2> cp(m), mult(m);
-                gp::host_thomas_tables(m, mode == 0 ? kap : 0.0, mode == 0 ? 0.0 : kap, cp.data(), mult.data());
+                std::vector<float4> c32(m), m32(m);
                 gp::AxisTables &a = s.conv[mode][k];
-                a.kre = mode == 0 ? kap : 0.0;
-                a.kim = mode == 0 ? 0.0 : kap;
-                gp::set_converged(a, m, cp.data(), mult.data());
+                gp::fill_tables(a, m, mode == 0 ? kap : 0.0, mode == 0 ? 0.0 : kap, cp.data(), mult.data(),
+                                c32.data(), m32.data());
                 if (b->prec == GP_C128) {
                     put(L.cp[mode][k], cp.data(), m * sizeof(double2));
                     put(L.mult[mode][k], mult.data(), m * sizeof(double2));
                 } else {
-                    std::vector<float2> c32(m), m32(m);
-                    for (int i = 0; i < m; ++i) {
-                        c32[i] = make_float2((float)cp[i].x, (float)cp[i].y);
-                        m32[i] = make_float2((float)mult[i].x, (float)mult[i].y);
-                    }
-                    put(L.cp[mode][k], c32.data(), m * sizeof(float2));
-                    put(L.mult[mode][k], m32.data(), m * sizeof(float2));
+                    put(L.cp[mode][k], c32.data(), m * sizeof(float4));
+                    put(L.mult[mode][k], m32.data(), m * sizeof(float4));
                 }
             }
             std::vector<double2> ph(n);
@@ -603,9 +557,9 @@ int upload_slot(gp_batch *b, gp_batch_slot &s)
             }
             if (b->prec == GP_C128) put(L.ph[mode][k], ph.data(), n * sizeof(double2));
             else {
-                std::vector<float2> p32(n);
-                for (int i = 0; i < n; ++i) p32[i] = make_float2((float)ph[i].x, (float)ph[i].y);
-                put(L.ph[mode][k], p32.data(), n * sizeof(float2));
+                std::vector<float4> p32(n);
+                for (int i = 0; i < n; ++i) p32[i] = gp::split_coef(ph[i]);
+                put(L.ph[mode][k], p32.data(), n * sizeof(float4));
             }
         }
     for (int k = 0; k < 3; ++k) {
@@ -618,6 +572,9 @@ int upload_slot(gp_batch *b, gp_batch_slot &s)
         }
         put(L.x2[k], x2.data(), n * sizeof(double));
         put(L.v[k], v.data(), n * sizeof(double));
+        std::vector<float> th(n);
+        for (int i = 0; i < n; ++i) th[i] = (float)(s.dt * v[i]);
+        put(L.th[k], th.data(), n * sizeof(float));
     }
     const double one = 1.0;
     put(L.scale, &one, sizeof(double));
@@ -632,6 +589,7 @@ int upload_slot(gp_batch *b, gp_batch_slot &s)
     for (int k = 0; k < 3; ++k) {
         s.x2[k] = reinterpret_cast<double *>(s.aux + L.x2[k]);
         s.v[k] = reinterpret_cast<double *>(s.aux + L.v[k]);
+        s.th[k] = reinterpret_cast<float *>(s.aux + L.th[k]);
     }
     s.scale = reinterpret_cast<double *>(s.aux + L.scale);
     s.norm = reinterpret_cast<double *>(s.aux + L.norm);
@@ -655,16 +613,13 @@ Inst make_inst(const gp_batch_slot &s, int prec)
         I.cp[k] = s.cp[s.mode][k];
         I.mult[k] = s.mult[s.mode][k];
         const gp::AxisTables &a = s.conv[s.mode][k];
-        if (prec == GP_C128) {
-            I.conv[k] = a.conv64;
-            I.cinf[k] = a.cinf64;
-            I.minf[k] = a.minf64;
-        } else {
-            I.conv[k] = a.conv32;
-            I.cinf[k] = make_double2(a.cinf32.x, a.cinf32.y);
-            I.minf[k] = make_double2(a.minf32.x, a.minf32.y);
-        }
+        I.conv[k] = prec == GP_C128 ? a.conv64 : a.conv32;
+        I.cinf64[k] = a.cinf64;
+        I.minf64[k] = a.minf64;
+        I.cinf32[k] = a.cinf32;
+        I.minf32[k] = a.minf32;
         I.ph[k] = s.ph[s.mode][k];
+        I.th[k] = s.th[k];
         I.x2[k] = s.x2[k];
         I.v[k] = s.v[k];
     }

@@ -8,11 +8,12 @@
 // synchronisation.  For them the sweep's forward-elimination scratch (d'_i,
 // one complex value per grid point) and its coefficient tables live in the
 // file-scope device array below instead of context-owned memory.  Every GPU
-// that loads libgp holds this array (16 MiB plus 384 KiB of tables) until the
+// that loads libgp holds this array (16 MiB plus 512 KiB of tables) until the
 // process exits.
 
 #include <cmath>
 #include <complex>
+#include <vector>
 #include <cstring>
 #include <mutex>
 
@@ -27,7 +28,7 @@ namespace {
 // 2^21 complex64 points.
 constexpr size_t kScratchBytes = size_t(1) << 24;
 constexpr size_t kTableEntries = GP_MAX_EDGE;
-constexpr size_t kTableBytes = kTableEntries * (2 * sizeof(double2) + 2 * sizeof(float2));
+constexpr size_t kTableBytes = kTableEntries * (2 * sizeof(double2) + 2 * sizeof(float4));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes + kTableBytes];
 
@@ -35,7 +36,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;                       // guards the fields below
 void *g_scratch_addr[kMaxDevices];        // device address per device ordinal
 double2 g_cp64[kTableEntries], g_mult64[kTableEntries];
-float2 g_cp32[kTableEntries], g_mult32[kTableEntries];
+float4 g_cp32[kTableEntries], g_mult32[kTableEntries];
 
 int reject(int code, const char *msg)
 {
@@ -85,34 +86,20 @@ extern "C" int gp_sweep_noalloc(void *psi_device, const gp_grid *grid, int axis,
     const int n = axis == 0 ? grid->nx : (axis == 1 ? grid->ny : grid->nz);
     const int m = n - 1;
     const double kap = dt / (4.0 * h * h);
-    const std::complex<double> kappa = mode == GP_IMAG ? std::complex<double>(kap, 0.0)
-                                                       : std::complex<double>(0.0, kap);
-    std::complex<double> prev = 0.0;
-    for (int i = 0; i < m; ++i) {
-        const std::complex<double> f = 1.0 / ((1.0 + 2.0 * kappa) + kappa * prev);
-        const std::complex<double> c = -kappa * f;
-        g_mult64[i] = make_double2(f.real(), f.imag());
-        g_cp64[i] = make_double2(c.real(), c.imag());
-        g_mult32[i] = make_float2((float)f.real(), (float)f.imag());
-        g_cp32[i] = make_float2((float)c.real(), (float)c.imag());
-        prev = c;
-    }
     gp::AxisTables ax;
     ax.n = n;
     ax.h = h;
-    ax.kre = mode == GP_IMAG ? kap : 0.0;
-    ax.kim = mode == GP_IMAG ? 0.0 : kap;
-    gp::set_mid(ax, m, g_cp64);
-    gp::set_converged(ax, m, g_cp64, g_mult64);
+    gp::fill_tables(ax, m, mode == GP_IMAG ? kap : 0.0, mode == GP_IMAG ? 0.0 : kap, g_cp64, g_mult64,
+                    g_cp32, g_mult32);
     unsigned char *tab = base + kScratchBytes;
     ax.cp64 = reinterpret_cast<double2 *>(tab);
     ax.mult64 = ax.cp64 + kTableEntries;
-    ax.cp32 = reinterpret_cast<float2 *>(ax.mult64 + kTableEntries);
+    ax.cp32 = reinterpret_cast<float4 *>(ax.mult64 + kTableEntries);
     ax.mult32 = ax.cp32 + kTableEntries;
     // pageable sources: each copy returns once its bytes are staged
     const struct { void *dst; const void *src; size_t bytes; } copies[4] = {
         {ax.cp64, g_cp64, m * sizeof(double2)}, {ax.mult64, g_mult64, m * sizeof(double2)},
-        {ax.cp32, g_cp32, m * sizeof(float2)}, {ax.mult32, g_mult32, m * sizeof(float2)}};
+        {ax.cp32, g_cp32, m * sizeof(float4)}, {ax.mult32, g_mult32, m * sizeof(float4)}};
     for (const auto &cp : copies) {
         e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return reject(GP_ECUDA, cudaGetErrorString(e));

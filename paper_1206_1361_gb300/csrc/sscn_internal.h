@@ -10,34 +10,42 @@ namespace gp {
 
 // Per-axis constants of one Crank-Nicolson sweep: the line has n stored points
 // (m = n - 1 unknowns at indices 1 .. n-1), kappa = kre + i kim, and the
-// forward-elimination tables c'_i and mult_i (i = 1 .. m, stored 0-based) in
-// FP64, plus their FP32 roundings for the complex64 path.
+// forward-elimination tables c'_i and mult_i (i = 1 .. m, stored 0-based).
+// FP64 tables come from kappa; the complex64 tables come from the FP32
+// rounding of kappa (the value the FP32 kernels multiply by), computed in
+// FP64 and stored as hi + lo FP32 pairs (float4), so the FP32 elimination
+// solves exactly the system whose right-hand side it forms.
 // mid is the middle-row multiplier of the two-ended elimination,
 // 1 / (1 + 2 kappa + kappa (c'_{k-1} + c'_{m-k})) with k = ceil(m / 2), c'_0 = 0.
 struct AxisTables {
     int n = 0;
     double h = 0, kre = 0, kim = 0;
     double2 *cp64 = nullptr, *mult64 = nullptr;   // device, m entries each
-    float2 *cp32 = nullptr, *mult32 = nullptr;    // device, m entries each
+    float4 *cp32 = nullptr, *mult32 = nullptr;    // device, m entries each (hi, lo)
     double2 mid64{0, 0};
-    float2 mid32{0, 0};
+    float4 mid32{0, 0, 0, 0};
     // From index conv64 (conv32) on, every FP64 (FP32) table entry equals the
     // last one: the elimination coefficients converge geometrically along a
     // constant-coefficient line, so kernels may hold c'_inf and mult_inf in
     // registers there (0-based table indices).
     int conv64 = 0, conv32 = 0;
     double2 cinf64{0, 0}, minf64{0, 0};
-    float2 cinf32{0, 0}, minf32{0, 0};
+    float4 cinf32{0, 0, 0, 0}, minf32{0, 0, 0, 0};
     // Look-back window of the TMA path: smallest W with max|c'|^(W+1) below
-    // the precision's rounding (2^-55 / 2^-26); 0 if none up to the chunk.
+    // 2^-55 (FP64) / 2^-40 (complex64); 0 if none up to 64.
     int win64 = 0, win32 = 0;
 };
 
-// Fill the convergence fields of `a` from the host tables (m entries).
-void set_converged(AxisTables &a, int m, const double2 *cp, const double2 *mult);
+// Compute both table sets of one axis on the host and every derived field
+// of `a` (kappa, mid, convergence, window): cp64/mult64 (FP64, from kappa)
+// and cp32/mult32 (hi + lo pairs, from FP32 kappa), m entries each.
+void fill_tables(AxisTables &a, int m, double kre, double kim, double2 *cp64, double2 *mult64,
+                 float4 *cp32, float4 *mult32);
 
-// Fill a.mid64 / a.mid32 from the host copy of the c' table (m entries).
-void set_mid(AxisTables &a, int m, const double2 *cp_host);
+// A unit-modulus or real FP64 coefficient as an FP32 hi + lo pair.
+float4 split_coef(double2 v);
+
+
 
 // One sweep launch: lines are indexed by (a, b), the line's first stored point
 // sits at a * stride_a + b * stride_b and its points are pstride apart.
@@ -55,7 +63,9 @@ struct SweepGeom {
 // Only the nonlinear phase dt g |psi|^2 is evaluated per point.
 struct NonlinArgs {
     const double2 *px = nullptr, *py = nullptr, *pz = nullptr;   // FP64 tables
-    const float2 *px32 = nullptr, *py32 = nullptr, *pz32 = nullptr;
+    const float4 *px32 = nullptr, *py32 = nullptr, *pz32 = nullptr;   // hi + lo pairs
+    // complex64 real time: phase tables theta_k = dt omega_k^2 x^2 / 2 (FP32)
+    const float *tx32 = nullptr, *ty32 = nullptr, *tz32 = nullptr;
     double dtg = 0;
     const double *scale = nullptr;   // pending imaginary-time scale (device)
 };

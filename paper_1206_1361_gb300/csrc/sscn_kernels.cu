@@ -20,6 +20,7 @@
 
 #include "sscn_accum.cuh"
 #include "sscn_internal.h"
+#include "sscn_line.cuh"
 
 namespace gp {
 namespace {
@@ -85,92 +86,6 @@ __device__ double block_sum(double v, double *red /* >= 32 doubles */)
 // d'_i = (psi_i + kappa d'_{i-1}) mult_i into the scratch buffer; back
 // substitution: v_i = d'_i - c'_i v_{i+1}, u_i = 2 v_i - psi_i.
 
-// Crank-Nicolson coefficients specialised by mode: in imaginary time kappa
-// and the tables are real; in real time kappa = i kim and the tables complex.
-template <typename T, int MODE> struct Cn {
-    using C = typename CT<T>::c;
-    T k;                                   // kre (MODE 0) or kim (MODE 1)
-
-    // (p + kappa d) * f
-    __device__ __forceinline__ C fwd(C p, C d, C f) const
-    {
-        if (MODE == 0) return mk<T>(fma(k, d.x, p.x) * f.x, fma(k, d.y, p.y) * f.x);
-        const T tx = fma(-k, d.y, p.x), ty = fma(k, d.x, p.y);
-        return mk<T>(fma(tx, f.x, -ty * f.y), fma(tx, f.y, ty * f.x));
-    }
-    // d - c v
-    __device__ __forceinline__ C back(C d, C c, C v) const
-    {
-        if (MODE == 0) return mk<T>(fma(-c.x, v.x, d.x), fma(-c.x, v.y, d.y));
-        return mk<T>(fma(-c.x, v.x, fma(c.y, v.y, d.x)), fma(-c.x, v.y, fma(-c.y, v.x, d.y)));
-    }
-    // 2 v - p
-    static __device__ __forceinline__ C out(C v, C p)
-    {
-        return mk<T>(fma((T)2, v.x, -p.x), fma((T)2, v.y, -p.y));
-    }
-};
-
-// exp(-i a) and exp(-a) for the nonlinear phase a = dt g |psi|^2: Taylor
-// polynomials for |a| <= 1/16 (truncation below 3e-19 relative, under half an
-// FP64 ulp), the library functions beyond.
-__device__ __forceinline__ void expmi_small(double a, double &c, double &s)
-{
-    if (fabs(a) <= 0.0625) {
-        const double t = a * a;
-        c = fma(t, fma(t, fma(t, fma(t, 1.0 / 40320, -1.0 / 720), 1.0 / 24), -0.5), 1.0);
-        s = a * fma(t, fma(t, fma(t, fma(t, 1.0 / 362880, -1.0 / 5040), 1.0 / 120), -1.0 / 6), 1.0);
-    } else {
-        sincos(a, &s, &c);
-    }
-}
-
-__device__ __forceinline__ double expm_small(double a)
-{
-    if (fabs(a) <= 0.0625) {
-        double r = -1.0 / 362880;
-        r = fma(r, a, 1.0 / 40320);
-        r = fma(r, a, -1.0 / 5040);
-        r = fma(r, a, 1.0 / 720);
-        r = fma(r, a, -1.0 / 120);
-        r = fma(r, a, 1.0 / 24);
-        r = fma(r, a, -1.0 / 6);
-        r = fma(r, a, 0.5);
-        r = fma(r, a, -1.0);
-        return fma(r, a, 1.0);
-    }
-    return exp(-a);
-}
-
-__device__ __forceinline__ void expmi_small(float a, float &c, float &s) { sincosf(a, &s, &c); }
-__device__ __forceinline__ float expm_small(float a) { return expf(-a); }
-
-// calcnu at one point: imaginary time s P exp(-dt g |s psi|^2) psi (P real),
-// real time P exp(-i dt g |psi|^2) psi (P unit complex), with P = P_x[i] P_yz.
-template <typename T, int MODE> struct Nonlin {
-    using C = typename CT<T>::c;
-    const C *px;
-    C pyz;          // P_y[j] P_z[k] (times s in imaginary time)
-    T a_coef;       // dt g (times s^2 in imaginary time)
-
-    __device__ __forceinline__ C apply(C v, int i) const
-    {
-        const C q = px[i];
-        const T a = a_coef * abs2<T>(v);
-        if (MODE == 0) {
-            const T f = q.x * pyz.x * expm_small(a);
-            return mk<T>(v.x * f, v.y * f);
-        } else {
-            T cs, sn;
-            expmi_small(a, cs, sn);
-            // P = q * pyz; w = (cs - i sn) v; result P w
-            const T prx = fma(q.x, pyz.x, -q.y * pyz.y), pry = fma(q.x, pyz.y, q.y * pyz.x);
-            const T wx = fma(cs, v.x, sn * v.y), wy = fma(cs, v.y, -sn * v.x);
-            return mk<T>(fma(prx, wx, -pry * wy), fma(prx, wy, pry * wx));
-        }
-    }
-};
-
 // Two-ended elimination ("burn at both ends", a twisted factorisation): the
 // lane pair (l, l ^ 16) of a warp owns one line; the low lane eliminates from
 // the top (i = 1 .. k-1), the high lane from the bottom (i = m .. k+1) with the
@@ -196,10 +111,11 @@ __device__ __forceinline__ typename CT<T>::c shfl_xor16(typename CT<T>::c v)
 template <typename T, int MODE, bool NL, bool NORM>
 __global__ void __launch_bounds__(kSweepThreads)
 k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ work,
-        const typename CT<T>::c *__restrict__ cp,
-        const typename CT<T>::c *__restrict__ mult, typename CT<T>::c mid, SweepGeom g,
-        T kappa, const typename CT<T>::c *__restrict__ px,
-        const typename CT<T>::c *__restrict__ py, const typename CT<T>::c *__restrict__ pz,
+        const typename Coef<T>::t *__restrict__ cp,
+        const typename Coef<T>::t *__restrict__ mult, typename Coef<T>::t mid, SweepGeom g,
+        T kappa, const typename Coef<T>::t *__restrict__ px,
+        const typename Coef<T>::t *__restrict__ py, const typename Coef<T>::t *__restrict__ pz,
+        const float *__restrict__ tx, const float *__restrict__ ty, const float *__restrict__ tz,
         double dtg, const double *__restrict__ scale, double *__restrict__ partials)
 {
     using C = typename CT<T>::c;
@@ -217,21 +133,9 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
     const long long base = active ? (long long)a * g.stride_a + (long long)b * g.stride_b : 0;
     C *line = psi + base;
     C *wl = work + base;
-    const Cn<T, MODE> cn{kappa};
-    Nonlin<T, MODE> nl{};
-    if (NL && active) {
-        // x sweep: a is the y index, b the z index
-        const C qy = py[a], qz = pz[b];
-        nl.px = px;
-        if (MODE == 0) {
-            const double sc = *scale;
-            nl.pyz = mk<T>((T)(sc * (double)qy.x * (double)qz.x), (T)0);
-            nl.a_coef = (T)(dtg * sc * sc);
-        } else {
-            nl.pyz = mk<T>(qy.x * qz.x - qy.y * qz.y, qy.x * qz.y + qy.y * qz.x);
-            nl.a_coef = (T)dtg;
-        }
-    }
+    const LineOps<T, MODE> cn{kappa};
+    Calcnu<T, MODE> nl{};
+    if (NL && active) nl.setup(px, py, pz, tx, ty, tz, a, b, dtg, scale);   // x sweep: a = y, b = z
     Acc<T> nacc;
     C d = mk<T>((T)0, (T)0);
     if (active) {
@@ -255,7 +159,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
         C pk = line[(long long)k * s];
         if (NL) pk = nl.apply(pk, k);
         vk = cn.fwd(pk, mk<T>(d.x + other.x, d.y + other.y), mid);
-        const C u = Cn<T, MODE>::out(vk, pk);
+        const C u = LineOps<T, MODE>::out(vk, pk);
         line[(long long)k * s] = u;
         if (NORM) nacc.add(abs2<T>(u));
     }
@@ -267,7 +171,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
             if (t < len) {
                 const long long at = (long long)(top ? 1 + t : m - t) * s;
                 v = cn.back(wl[at], cp[t], v);
-                const C u = Cn<T, MODE>::out(v, line[at]);
+                const C u = LineOps<T, MODE>::out(v, line[at]);
                 line[at] = u;
                 if (NORM) nacc.add(abs2<T>(u));
             }
@@ -287,24 +191,26 @@ cudaError_t sweep_launch(void *psi, void *work, const AxisTables &ax,
                          const Partials *norm_out, cudaStream_t st)
 {
     using C = typename CT<T>::c;
+    using F = typename Coef<T>::t;
     dim3 grid((g.lines_a + kLinesPerBlock - 1) / kLinesPerBlock, g.lines_b);
-    const C *cp, *mult, *px = nullptr, *py = nullptr, *pz = nullptr;
-    C mid;
+    const F *cp, *mult, *px = nullptr, *py = nullptr, *pz = nullptr;
+    const float *tx = nl ? nl->tx32 : nullptr, *ty = nl ? nl->ty32 : nullptr, *tz = nl ? nl->tz32 : nullptr;
+    F mid;
     T kappa = (T)(MODE == 0 ? ax.kre : ax.kim);
     if constexpr (sizeof(T) == 8) {
-        cp = reinterpret_cast<const C *>(ax.cp64);
-        mult = reinterpret_cast<const C *>(ax.mult64);
+        cp = ax.cp64;
+        mult = ax.mult64;
         mid = ax.mid64;
-        if (nl) { px = (const C *)nl->px; py = (const C *)nl->py; pz = (const C *)nl->pz; }
+        if (nl) { px = nl->px; py = nl->py; pz = nl->pz; }
     } else {
-        cp = reinterpret_cast<const C *>(ax.cp32);
-        mult = reinterpret_cast<const C *>(ax.mult32);
+        cp = ax.cp32;
+        mult = ax.mult32;
         mid = ax.mid32;
-        if (nl) { px = (const C *)nl->px32; py = (const C *)nl->py32; pz = (const C *)nl->pz32; }
+        if (nl) { px = nl->px32; py = nl->py32; pz = nl->pz32; }
     }
     k_sweep<T, MODE, NL, NORM><<<grid, kSweepThreads, 0, st>>>(
         reinterpret_cast<C *>(psi), reinterpret_cast<C *>(work), cp, mult, mid, g, kappa,
-        px, py, pz, nl ? nl->dtg : 0.0, nl ? nl->scale : nullptr,
+        px, py, pz, tx, ty, tz, nl ? nl->dtg : 0.0, nl ? nl->scale : nullptr,
         norm_out ? norm_out->buf : nullptr);
     return cudaGetLastError();
 }

@@ -13,13 +13,19 @@
 // Each consumer thread runs the forward elimination of its line through the
 // tile, keeping d'_i for the last two chunks in a shared-memory ring, and
 // writes the finished values back into the tile in place; the producer then
-// stores the tile with a TMA store and reuses the stage.  Back substitution is windowed: the values of chunk q-1
+// stores the tile with a TMA store and reuses the stage.  The complex64 path
+// eliminates in increment form, (I - kappa L) D = kappa L psi, u = psi + 2 D,
+// so that only the final store rounds at full size: repeated every step on a
+// smooth state, the FP32 roundings of u = 2 v - psi do not average out and
+// the real-time norm drifts.  Its forward pass runs one point behind the
+// newest loaded point, which supplies psi_{i+1}.  Back substitution is windowed: the values of chunk q-1
 // are produced after the forward pass of chunk q, starting from v ~ d' at the
 // end of chunk q.  The dropped term is c'_e v_{e+1}, damped by |c'| at every
 // step back; the seed sits W points into chunk q, so every output carries an
 // error below |c'|^(W+1) max|v|.  The host picks the smallest W <= C for which
-// that bound is under 2^-26 (complex64) / 2^-55 (complex128) and otherwise
-// uses the exact one-line-per-thread kernel.
+// that bound is under 2^-40 (complex64) / 2^-55 (complex128) -- far below one
+// rounding, because the truncation is the same linear perturbation at every
+// step -- and otherwise uses the exact one-line-per-thread kernel.
 // The last two chunks are back-substituted exactly from v_m = d'_m.
 //
 // Layout of a stage: x sweep -> [L rows][C points] with the 128-byte TMA
@@ -34,6 +40,7 @@
 
 #include "sscn_accum.cuh"
 #include "sscn_internal.h"
+#include "sscn_line.cuh"
 
 namespace gp {
 namespace {
@@ -134,57 +141,6 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-// ------------------------------------------------------------- arithmetic
-
-template <typename T, int MODE> struct CnT {
-    using C = typename CT2<T>::c;
-    T k;
-    __device__ __forceinline__ C fwd(C p, C d, C f) const
-    {
-        if (MODE == 0) return mk2<T>(fma(k, d.x, p.x) * f.x, fma(k, d.y, p.y) * f.x);
-        const T tx = fma(-k, d.y, p.x), ty = fma(k, d.x, p.y);
-        return mk2<T>(fma(tx, f.x, -ty * f.y), fma(tx, f.y, ty * f.x));
-    }
-    __device__ __forceinline__ C back(C d, C c, C v) const
-    {
-        if (MODE == 0) return mk2<T>(fma(-c.x, v.x, d.x), fma(-c.x, v.y, d.y));
-        return mk2<T>(fma(-c.x, v.x, fma(c.y, v.y, d.x)), fma(-c.x, v.y, fma(-c.y, v.x, d.y)));
-    }
-    static __device__ __forceinline__ C out(C v, C p)
-    {
-        return mk2<T>(fma((T)2, v.x, -p.x), fma((T)2, v.y, -p.y));
-    }
-};
-
-__device__ __forceinline__ void expmi(float a, float &c, float &s) { sincosf(a, &s, &c); }
-__device__ __forceinline__ float expm(float a) { return expf(-a); }
-__device__ __forceinline__ void expmi(double a, double &c, double &s) { sincos(a, &s, &c); }
-__device__ __forceinline__ double expm(double a) { return exp(-a); }
-
-// calcnu: P_x[i] P_yz exp(-tau dt g |psi|^2) psi (P_yz carries the pending
-// imaginary-time scale, a_coef = dt g s^2).
-template <typename T, int MODE> struct NonlinT {
-    using C = typename CT2<T>::c;
-    const C *px;
-    C pyz;
-    T a_coef;
-    __device__ __forceinline__ C apply(C v, int i) const
-    {
-        const C q = px[i];
-        const T a = a_coef * (v.x * v.x + v.y * v.y);
-        if (MODE == 0) {
-            const T f = q.x * pyz.x * expm(a);
-            return mk2<T>(v.x * f, v.y * f);
-        } else {
-            T cs, sn;
-            expmi(a, cs, sn);
-            const T prx = fma(q.x, pyz.x, -q.y * pyz.y), pry = fma(q.x, pyz.y, q.y * pyz.x);
-            const T wx = fma(cs, v.x, sn * v.y), wy = fma(cs, v.y, -sn * v.x);
-            return mk2<T>(fma(prx, wx, -pry * wy), fma(prx, wy, pry * wx));
-        }
-    }
-};
-
 // ------------------------------------------------------------------ kernel
 
 struct TmaArgs {
@@ -192,9 +148,11 @@ struct TmaArgs {
     int lines_a;        // extent of the in-tile line index (y for x, x for y / z)
     int win;            // look-back window W (1 .. C)
     int conv;           // table index from which c' and mult are constant
-    double2 cinf, minf; // those constants (FP64; rounded to T in the kernel)
-    const void *cp, *mult;      // complex T tables, m entries
+    double2 cinf64, minf64;     // those constants, FP64 path
+    float4 cinf32, minf32;      // those constants, complex64 path (hi + lo)
+    const void *cp, *mult;      // coefficient tables (Coef<T>), m entries
     const void *px, *py, *pz;   // calcnu factor tables (x sweep)
+    const float *tx, *ty, *tz;  // complex64 phase tables (x sweep)
     double kappa;       // kre (imaginary time) or kim (real time)
     double dtg;
     const double *scale;
@@ -237,7 +195,7 @@ template <typename T, int MODE, int AXIS, bool NL, bool NORM, int K, int C, int 
 __global__ void __launch_bounds__(32 * (K + 1))
 k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
 {
-    using Cx = typename CT2<T>::c;
+    using Cv = typename CT2<T>::c;
     constexpr int L = 32 * K;
     using G = TileGeom<T, L, C, S, AXIS>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -245,7 +203,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *stages = smem;
-    Cx *ring = reinterpret_cast<Cx *>(stages + S * G::kStageBytes);     // [2][C][L]
+    Cv *ring = reinterpret_cast<Cv *>(stages + S * G::kStageBytes);     // [2][C][L]
     uint64_t *full = reinterpret_cast<uint64_t *>(ring + 2 * C * L);
     uint64_t *ready = full + S;
     double *red = reinterpret_cast<double *>(ready + S);
@@ -258,12 +216,19 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
     const bool active = !producer && a < args.lines_a;
     const int m = args.n - 1;
     const int Q = (args.n + C - 1) / C;             // chunks covering stored points 0 .. m
-    const Cx *cp_tab = static_cast<const Cx *>(args.cp);
-    const Cx *mult_tab = static_cast<const Cx *>(args.mult);
-    const CnT<T, MODE> cn{(T)args.kappa};
+    using F = typename Coef<T>::t;
+    const F *cp_tab = static_cast<const F *>(args.cp);
+    const F *mult_tab = static_cast<const F *>(args.mult);
+    const LineOps<T, MODE> cn{(T)args.kappa};
     const int conv = args.conv, win = args.win;
-    const Cx cinf = mk2<T>((T)args.cinf.x, (T)args.cinf.y);
-    const Cx minf = mk2<T>((T)args.minf.x, (T)args.minf.y);
+    F cinf, minf;
+    if constexpr (sizeof(T) == 8) {
+        cinf = args.cinf64;
+        minf = args.minf64;
+    } else {
+        cinf = args.cinf32;
+        minf = args.minf32;
+    }
     // table entry t (0-based): past `conv` every entry equals the last one
     auto cp = [&](int t) { return t < conv ? cp_tab[t] : cinf; };
     auto mult = [&](int t) { return t < conv ? mult_tab[t] : minf; };
@@ -275,7 +240,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
         else { c0 = tile0 * G::U; c1 = blockIdx.y; c2 = q * C; }
     };
     auto stage_ptr = [&](int q) { return stages + (q % S) * G::kStageBytes; };
-    auto at = [&](int q, int c) -> Cx * { return reinterpret_cast<Cx *>(stage_ptr(q) + G::off(l, c)); };
+    auto at = [&](int q, int c) -> Cv * { return reinterpret_cast<Cv *>(stage_ptr(q) + G::off(l, c)); };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -323,73 +288,86 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
             bulk_wait_all();
         }
     } else {
-        NonlinT<T, MODE> nl{};
+        Calcnu<T, MODE> nl{};
         if (NL && active) {
-            const Cx *py = static_cast<const Cx *>(args.py), *pz = static_cast<const Cx *>(args.pz);
-            const Cx qy = py[a], qz = pz[blockIdx.y];
-            nl.px = static_cast<const Cx *>(args.px);
-            if (MODE == 0) {
-                const double sc = *args.scale;
-                nl.pyz = mk2<T>((T)(sc * (double)qy.x * (double)qz.x), (T)0);
-                nl.a_coef = (T)(args.dtg * sc * sc);
-            } else {
-                nl.pyz = mk2<T>(qy.x * qz.x - qy.y * qz.y, qy.x * qz.y + qy.y * qz.x);
-                nl.a_coef = (T)args.dtg;
-            }
+            const F *py = static_cast<const F *>(args.py), *pz = static_cast<const F *>(args.pz);
+            nl.setup(static_cast<const F *>(args.px), py, pz, args.tx, args.ty, args.tz, a,
+                     blockIdx.y, args.dtg, args.scale);
         }
-        Cx d = mk2<T>((T)0, (T)0);
+        // complex64: increment form with the forward pass one point behind
+        // the newest point (it needs psi_{i+1}); FP64: u = 2 v - psi
+        constexpr bool INC = sizeof(T) == 4;
+        auto slot = [&](int i) -> Cv & { return ring[((i / C) & 1) * C * L + (i % C) * L + l]; };
+        auto output = [&](Cv v, Cv *tile_slot) {
+            const Cv u = INC ? LineOps<T, MODE>::out_inc(v, *tile_slot) : LineOps<T, MODE>::out(v, *tile_slot);
+            *tile_slot = u;
+            if (NORM) nacc.add(fma(u.x, u.x, u.y * u.y));
+        };
+        const Cv zero = mk2<T>((T)0, (T)0);
+        Cv d = zero, pa = zero, pb = zero;          // INC: psi~_{i-1}, psi~_i
         for (int q = 0; q < Q; ++q) {
             if (!mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs)) {
                 failed = true;
                 break;
             }
+            const bool last = q == Q - 1;
             // forward elimination through chunk q
-            Cx *rq = ring + (q & 1) * C * L;
             if (active) {
 #pragma unroll 4
                 for (int c = 0; c < C; ++c) {
-                    const int i = q * C + c;
-                    if (i >= 1 && i <= m) {
-                        Cx p = *at(q, c);
+                    const int j = q * C + c;
+                    if (INC) {
+                        Cv pj = zero;
+                        if (j <= m) {
+                            pj = *at(q, c);
+                            if (NL && j >= 1) {
+                                pj = nl.apply(pj, j);
+                                *at(q, c) = pj;
+                            }
+                        }
+                        const int i = j - 1;
+                        if (i >= 1 && i <= m) {
+                            d = cn.fwd(cn.lap(pa, pb, pj), d, mult(i - 1));
+                            slot(i) = d;
+                        }
+                        pa = pb;
+                        pb = pj;
+                    } else if (j >= 1 && j <= m) {
+                        Cv p = *at(q, c);
                         if (NL) {
-                            p = nl.apply(p, i);
+                            p = nl.apply(p, j);
                             *at(q, c) = p;
                         }
-                        d = cn.fwd(p, d, mult(i - 1));
-                        rq[c * L + l] = d;
+                        d = cn.fwd(p, d, mult(j - 1));
+                        slot(j) = d;
                     }
                 }
+                if (INC && last && Q * C - 1 == m) {
+                    // point m: its right neighbour is the virtual zero node
+                    d = cn.fwd(cn.lap(pa, pb, zero), d, mult(m - 1));
+                    slot(m) = d;
+                }
             }
-            const bool last = q == Q - 1;
             if (active) {
                 if (!last && q >= 1) {
                     // windowed: seed W points into chunk q, output chunk q - 1
-                    Cx v = rq[(win - 1) * L + l];
+                    Cv v = slot(q * C + win - 1);
                     for (int c = win - 2; c >= 0; --c)
-                        v = cn.back(rq[c * L + l], cp(q * C + c - 1), v);
-                    Cx *rp = ring + ((q - 1) & 1) * C * L;
+                        v = cn.back(slot(q * C + c), cp(q * C + c - 1), v);
 #pragma unroll 4
                     for (int c = C - 1; c >= 0; --c) {
                         const int i = (q - 1) * C + c;
                         if (i < 1) break;
-                        v = cn.back(rp[c * L + l], cp(i - 1), v);
-                        Cx *slot = at(q - 1, c);
-                        const Cx u = CnT<T, MODE>::out(v, *slot);
-                        *slot = u;
-                        if (NORM) nacc.add(fma(u.x, u.x, u.y * u.y));
+                        v = cn.back(slot(i), cp(i - 1), v);
+                        output(v, at(q - 1, c));
                     }
                 } else if (last) {
                     // exact: v_m = d'_m, down through chunks q and q - 1
-                    Cx v = d;
+                    Cv v = d;
                     const int lo = q >= 1 ? (q - 1) * C : 0;
                     for (int i = m; i >= lo && i >= 1; --i) {
-                        const int qq = i / C, c = i - qq * C;
-                        const Cx *rr = ring + (qq & 1) * C * L;
-                        if (i < m) v = cn.back(rr[c * L + l], cp(i - 1), v);
-                        Cx *slot = at(qq, c);
-                        const Cx u = CnT<T, MODE>::out(v, *slot);
-                        *slot = u;
-                        if (NORM) nacc.add(fma(u.x, u.x, u.y * u.y));
+                        if (i < m) v = cn.back(slot(i), cp(i - 1), v);
+                        output(v, at(i / C, i % C));
                     }
                 }
             }
@@ -556,20 +534,23 @@ cudaError_t launch_sweep_tma(int prec, int shape, int mode, int axis, const CUte
         args.mult = ax.mult64;
         args.conv = ax.conv64;
         args.win = ax.win64;
-        args.cinf = ax.cinf64;
-        args.minf = ax.minf64;
+        args.cinf64 = ax.cinf64;
+        args.minf64 = ax.minf64;
     } else {
         args.cp = ax.cp32;
         args.mult = ax.mult32;
         args.conv = ax.conv32;
         args.win = ax.win32;
-        args.cinf = make_double2(ax.cinf32.x, ax.cinf32.y);
-        args.minf = make_double2(ax.minf32.x, ax.minf32.y);
+        args.cinf32 = ax.cinf32;
+        args.minf32 = ax.minf32;
     }
     if (nl) {
         args.px = prec == kC128 ? (const void *)nl->px : (const void *)nl->px32;
         args.py = prec == kC128 ? (const void *)nl->py : (const void *)nl->py32;
         args.pz = prec == kC128 ? (const void *)nl->pz : (const void *)nl->pz32;
+        args.tx = nl->tx32;
+        args.ty = nl->ty32;
+        args.tz = nl->tz32;
         args.dtg = nl->dtg;
         args.scale = nl->scale;
     }
