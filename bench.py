@@ -211,6 +211,13 @@ def reduce_max(value, world):
     return float(t.item())
 
 
+def aggregate(local_ms, units_per_rank, world):
+    """Job time = the slowest rank's time; value = the units all ranks
+    processed over that time.  Returns (ms_max, units per second)."""
+    ms_max = reduce_max(local_ms, world)
+    return ms_max, world * units_per_rank / (ms_max / 1e3)
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -337,10 +344,8 @@ def run_ours(args):
         clk = clocks.stop()
         barrier(world)
         ms = ev0.elapsed_time(ev1)
-        ms_max = reduce_max(ms, world)
+        ms_max, value = aggregate(ms, args.steps * STEPS_PER_BENCH_STEP * case.points, world)
         obs_end = gp.gp_observables(ctx)
-        units = world * args.steps * STEPS_PER_BENCH_STEP * case.points
-        value = units / (ms_max / 1e3)
         per_step, per_obs = gp.gp_launches_per_step(ctx)
         launches = args.steps * (STEPS_PER_BENCH_STEP * per_step + per_obs)
 
@@ -396,7 +401,8 @@ def run_ours(args):
 
         forms = None
         if world == 1 and not args.no_forms:
-            forms = {"precision": precision_form(gp, torch, stream, args)}
+            forms = {"precision": precision_form(gp, torch, stream, args),
+                     "batched": batched_form(gp), "serving": serving_form(gp)}
 
         extra = {"prep_imag_steps": prep, "prep_dmu": dmu,
                  "norm_drift": abs(obs_end["norm"] / obs0["norm"] - 1),
@@ -480,6 +486,45 @@ def precision_form(gp, torch, stream, args):
             "complex64": out["complex64"], "complex128": out["complex128"],
             "speedup_c64_over_fp64": out["complex64"]["value"] / out["complex128"]["value"],
             "rel_error_vs_fp64": err}
+
+
+def batched_form(gp):
+    """256 uneven imaginary-time problems (seed 3) solved to convergence in
+    one batch, against the same problems solved one at a time on complex64
+    single-grid contexts."""
+    from paper_1206_1361_gb300 import workloads
+    from paper_1206_1361_gb300.serve import solve_batch, solve_sequential
+    insts = workloads.batched_instances()
+    b = solve_batch(insts, gp.GP_C64, max_steps=40000)
+    seq = solve_sequential([workloads.Request(0.0, "ground", i) for i in insts], gp.GP_C64,
+                           realtime=False, max_steps=40000)
+    bs, ss = b.summary(), seq.summary()
+    return {"workload": "256 imaginary-time instances, edges {32..128}, 25% 2D, complex64, "
+                        "to |dmu| < max(1e-6, 2^-22 mu)",
+            "value": bs["point_steps_per_s"], "unit": UNIT, "wall_s": bs["wall_s"],
+            "points_total": sum(i.points for i in insts),
+            "max_steps": max(r.total_steps for r in b.results),
+            "sequential_c64": {"value": ss["point_steps_per_s"], "wall_s": ss["wall_s"]},
+            "speedup_vs_sequential": ss["wall_s"] / bs["wall_s"]}
+
+
+def serving_form(gp, requests=40):
+    """The seeded Poisson request stream (200 req/s; 70 % ground state, 30 %
+    quench; complex64; 120 GB cap) through the continuous-batching server, and
+    the same requests served one at a time by plain FP64 solves."""
+    from paper_1206_1361_gb300 import workloads
+    from paper_1206_1361_gb300.serve import Server, solve_sequential
+    reqs = workloads.request_stream(count=requests)
+    with Server(gp.GP_C64) as srv:
+        st = srv.run(reqs, realtime=True)
+    seq = solve_sequential(reqs, gp.GP_C128, realtime=True)
+    a, b = st.summary(), seq.summary()
+    keys = ("requests", "wall_s", "requests_per_s", "point_steps_per_s", "p50_latency_s",
+            "p99_latency_s", "mean_latency_s", "peak_bytes")
+    return {"workload": "first %d requests of the seeded stream (200 req/s)" % requests,
+            "server": {k: a[k] for k in keys},
+            "sequential_fp64": {k: b[k] for k in keys if k != "peak_bytes"},
+            "throughput_ratio": a["point_steps_per_s"] / b["point_steps_per_s"]}
 
 
 def run_probe(args):

@@ -209,6 +209,18 @@ enum { GP_PATH_AUTO = 0, GP_PATH_EXACT = 1, GP_PATH_TMA = 2 };
  * GP_PATH_TMA, if some axis cannot take it.  Takes effect at the next step. */
 int gp_set_option(gp_ctx *ctx, int option, int value);
 
+/*
+ * Autotune the sweep kernels for this context's grid, precision, dt and mode:
+ * run `steps` SSCN steps (after one warm-up step) with every eligible (sweep
+ * path, tile shape) candidate on the current state, timing each with CUDA
+ * events on the context's stream, restore the state after each, and keep
+ * the fastest (GP_OPT_SWEEP_PATH / GP_OPT_TILE_SHAPE are set to it).  psi,
+ * the pending scale and the step counter are left as they were.  Allocates a
+ * temporary copy of psi.  *path_out, *shape_out and *ms_out (mean ms per
+ * step of the pick) may be NULL.  Synchronises.
+ */
+int gp_autotune(gp_ctx *ctx, int steps, int *path_out, int *shape_out, double *ms_out);
+
 /* Read an option's current value into *value. */
 int gp_get_option(gp_ctx *ctx, int option, int *value);
 

@@ -787,6 +787,91 @@ int gp_set_option(gp_ctx *c, int option, int value)
     return GP_OK;
 }
 
+int gp_autotune(gp_ctx *c, int steps, int *path_out, int *shape_out, double *ms_out)
+{
+    if (!c || steps < 1) return fail(c, GP_EINVAL, "gp_autotune: need steps >= 1");
+    const size_t bytes = (size_t)points(c->grid) * elem_bytes(c->prec);
+    void *saved = nullptr;
+    double *saved_scale = nullptr;
+    GP_CK(c, cudaMalloc(&saved, bytes));
+    cudaError_t e = cudaMalloc((void **)&saved_scale, sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(saved);
+        return cuda_fail(c, e, "cudaMalloc");
+    }
+    auto cleanup = [&]() {
+        cudaFree(saved);
+        cudaFree(saved_scale);
+    };
+    const int path0 = c->path_opt, shape0 = c->tile_shape;
+    const int64_t step0 = c->step;
+    const bool pending0 = c->scale_pending;
+    e = cudaMemcpyAsync(saved, c->psi, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(saved_scale, c->scale, sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(c, e, "gp_autotune: save state");
+    }
+    struct Cand { int path, shape; };
+    std::vector<Cand> cands{{GP_PATH_EXACT, shape0}};
+    for (int sh = 0; sh < gp::tma_shapes(c->prec); ++sh) {
+        c->tile_shape = sh;
+        setup_tma(c);
+        bool ok = true;
+        for (int k = 0; k < naxes(c->grid); ++k) ok = ok && c->tma_ok[c->mode][k];
+        if (ok) cands.push_back({GP_PATH_TMA, sh});
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e300;
+    Cand pick = cands[0];
+    int rc = GP_OK;
+    for (const Cand &cd : cands) {
+        c->tile_shape = cd.shape;
+        setup_tma(c);
+        c->path_opt = cd.path;
+        drop_graph(c);
+        if ((rc = enqueue_step(c))) break;             // warm-up
+        cudaEventRecord(e0, c->stream);
+        for (int s = 0; s < steps && rc == GP_OK; ++s) rc = enqueue_step(c);
+        cudaEventRecord(e1, c->stream);
+        if (rc) break;
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            pick = cd;
+        }
+        // back to the saved state for the next candidate
+        cudaMemcpyAsync(c->psi, saved, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(c->scale, saved_scale, sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    e = cudaStreamSynchronize(c->stream);
+    cleanup();
+    c->step = step0;
+    c->scale_pending = pending0;
+    if (rc == GP_OK && e != cudaSuccess) rc = cuda_fail(c, e, "gp_autotune");
+    if (rc != GP_OK) {
+        c->path_opt = path0;
+        c->tile_shape = shape0;
+        setup_tma(c);
+        drop_graph(c);
+        return rc;
+    }
+    c->tile_shape = pick.shape;
+    setup_tma(c);
+    c->path_opt = pick.path;
+    drop_graph(c);
+    if (path_out) *path_out = pick.path;
+    if (shape_out) *shape_out = pick.shape;
+    if (ms_out) *ms_out = best / steps;
+    return GP_OK;
+}
+
 int gp_get_option(gp_ctx *c, int option, int *value)
 {
     if (!c || !value) return fail(c, GP_EINVAL, "gp_get_option: null argument");

@@ -116,6 +116,22 @@ __device__ bool wait_done(const int *ctr, int need, const int *abort_flag)
     return true;
 }
 
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Asynchronous global -> shared copy of one complex value (8 or 16 bytes):
+// all copies of a tile are in flight together, then one wait.
+template <int BYTES> __device__ __forceinline__ void cp_async(void *dst, const void *src)
+{
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll
@@ -195,15 +211,17 @@ __device__ void sweep_tile(const Inst &I, int axis, int tile, typename BC<T>::c 
     const int rows = (int)min((long long)kTileLines, lines - L0);
     C *psi = static_cast<C *>(I.psi);
     long long base, stride;
+    constexpr int B = (int)sizeof(C);
     if (axis == 0) {
         for (int r = 0; r < rows; ++r) {
             const C *src = psi + (L0 + r) * I.n[0];
-            for (int c = lane; c < n; c += 32) sm[r * P + c] = src[c];
+            for (int c = lane; c < n; c += 32) cp_async<B>(&sm[r * P + c], &src[c]);
         }
     } else if (lane < rows) {
         line_geom(I, axis, L0 + lane, base, stride);
-        for (int c = 0; c < n; ++c) sm[lane * P + c] = psi[base + c * stride];
+        for (int c = 0; c < n; ++c) cp_async<B>(&sm[lane * P + c], &psi[base + c * stride]);
     }
+    cp_async_wait_all();
     __syncwarp();
     const bool norm = I.mode == 0 && axis == I.last_axis;
     Acc<T> acc;

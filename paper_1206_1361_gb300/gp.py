@@ -64,6 +64,8 @@ SIGNATURES = {
     "gp_set_option": (_int, [_vp, _int, _int]),
     "gp_sweep_paths": (_int, [_vp, ctypes.POINTER(_int)]),
     "gp_get_option": (_int, [_vp, _int, ctypes.POINTER(_int)]),
+    "gp_autotune": (_int, [_vp, _int, ctypes.POINTER(_int), ctypes.POINTER(_int),
+                           ctypes.POINTER(ctypes.c_double)]),
     "gp_tile_shapes": (_int, [_int, ctypes.POINTER(_int)]),
     "gp_time_kernels": (_int, [_vp, _i64, ctypes.POINTER(ctypes.c_double), _int]),
     "gp_launches_per_step": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
@@ -219,6 +221,14 @@ def gp_get_option(ctx, option):
     v = ctypes.c_int()
     _err(ctx, load_library().gp_get_option(ctx, int(option), ctypes.byref(v)))
     return v.value
+
+
+def gp_autotune(ctx, steps=5):
+    """(sweep path, tile shape, ms per step) of the fastest candidate, now set."""
+    p, sh, ms = _int(), _int(), ctypes.c_double()
+    _err(ctx, load_library().gp_autotune(ctx, int(steps), ctypes.byref(p), ctypes.byref(sh),
+                                         ctypes.byref(ms)))
+    return p.value, sh.value, ms.value
 
 
 def gp_tile_shapes(precision):
