@@ -156,7 +156,8 @@ def measured_peaks():
         return {}
 
 
-KERNEL_SOURCES = ("sscn_kernels.cu", "sscn_internal.h")
+KERNEL_SOURCES = ("sscn_kernels.cu", "sscn_tma.cu", "sscn_internal.h", "sscn_line.cuh",
+                  "sscn_coef.cuh", "sscn_accum.cuh")
 
 
 def kernel_source_sha():
