@@ -1,0 +1,106 @@
+"""GPU parity at the benchmark's full sizes, in the launch configuration the
+benchmark times (the 10-step graph, an observables report every 10 steps,
+the automatic sweep path):
+
+* 256^3 FP64: imaginary-time ground-state steps at g = 20, then the quench to
+  g = 18 in real time for 2000 steps, element by element against the oracle
+  (relative L2 of psi <= 1e-10; observables <= 1e-10; norm drift of both
+  within the rounding bound);
+* 512 x 512 x 256 complex64 real time from the Gaussian seed against the FP64
+  oracle (relative L2 bound derived from FP32 rounding per pass; mu <= 1e-6);
+* the 256 batched instances advanced together, sampled instances against
+  their solo runs (bitwise) and against the oracle.
+
+The oracle runs on every host core; these are the slowest GPU tests."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1206_1361_gb300 import gp
+from paper_1206_1361_gb300.workloads import PRECISION_512, REAL_256, batched_instances
+from tests.gpu_util import oracle_params, rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_real_256_quench_2000_steps_matches_oracle():
+    require_gpu()
+    c = REAL_256
+    prep, every = 100, c.extra["report_every"]
+    with gp.Solver(c.shape, c.h, c.dt, *c.trap, c.extra["g_ground"], gp.GP_IMAG) as s:
+        s.load(None).step(prep)
+        s.set_params(c.g, gp.GP_REAL)
+        for _ in range(c.steps // every):
+            s.step(every)
+            obs = s.observables()
+        got = s.psi()
+    pi = oracle_params(c.shape, c.h, c.dt, c.trap, c.extra["g_ground"], 0)
+    want = oracle.seed(pi)
+    oracle.step(pi, want, prep)
+    pr = oracle_params(c.shape, c.h, c.dt, c.trap, c.g, 1)
+    n0 = oracle.observables(pr, want)["norm"]
+    oracle.step(pr, want, c.steps)
+    assert rel_l2(got, want) <= 1e-10
+    ref = oracle.observables(pr, want)
+    for k in ("norm", "mu", "energy", "rms_x", "rms_y", "rms_z", "rms_r"):
+        assert abs(obs[k] - ref[k]) <= 1e-10 * abs(ref[k]), (k, obs[k], ref[k])
+    # Real time conserves N up to the unitarity defect of the rounded
+    # arithmetic: the stored LU factors reproduce I - kappa L with a
+    # Hermitian part off by ~2 ulp, which the Cayley step u = (2 (I - kappa
+    # L)^-1 - I) psi turns into a norm change of up to ~4 2^-52 per sweep,
+    # and the phase factor's modulus is off by ~2 2^-52.  Those defects are
+    # fixed, so on a slowly varying state they add up linearly in the steps
+    # (both sides drift ~1.5e-15 per step here).
+    bound = c.steps * (3 * 4 + 2) * 2.0 ** -52
+    assert abs(obs["norm"] - n0) <= bound and abs(ref["norm"] - n0) <= bound, \
+        (obs["norm"] - n0, ref["norm"] - n0)
+
+
+def test_precision_512_complex64_matches_fp64_oracle():
+    """FP32 storage rounds psi once per pass (3 sweeps, with the phase fused
+    into the first), 2^-24 relative each; over n steps the rounding errors
+    add at most linearly: relative L2 <= n * 4 * 2^-23 (a factor 2 for the
+    complex modulus).  mu within 1e-6 relative."""
+    require_gpu()
+    c = PRECISION_512
+    steps = 20
+    with gp.Solver(c.shape, c.h, c.dt, *c.trap, c.g, gp.GP_REAL, gp.GP_C64) as s:
+        s.load(None)
+        for _ in range(steps // 10):
+            s.step(10)
+            obs = s.observables()
+        got = s.psi()
+    assert got.dtype == np.complex64
+    p = oracle_params(c.shape, c.h, c.dt, c.trap, c.g, 1)
+    want = oracle.seed(p)
+    oracle.step(p, want, steps)
+    err = rel_l2(got.astype(np.complex128), want)
+    assert err <= steps * 4 * 2.0 ** -23, err
+    ref = oracle.observables(p, want)
+    assert abs(obs["mu"] - ref["mu"]) <= 1e-6 * abs(ref["mu"]), (obs["mu"], ref["mu"])
+    assert abs(obs["norm"] - ref["norm"]) <= 1e-6
+
+
+def test_batched_256_instances_sampled_against_solo_and_oracle():
+    require_gpu()
+    insts = batched_instances()
+    steps = 30
+    sample = (0, 77, 255)
+    with gp.Batch(gp.GP_C64) as b:
+        slots = [b.add(i.shape, i.h, i.dt, *i.trap, i.g, gp.GP_IMAG) for i in insts]
+        b.step(steps)
+        mix = {k: b.psi(slots[k]) for k in sample}
+        obs_mix = b.observables()
+    for k in sample:
+        i = insts[k]
+        with gp.Batch(gp.GP_C64) as b:
+            slot = b.add(i.shape, i.h, i.dt, *i.trap, i.g, gp.GP_IMAG)
+            b.step(steps)
+            alone = b.psi(slot)
+        assert np.array_equal(alone, mix[k]), k
+        p = oracle_params(i.shape, i.h, i.dt, i.trap, i.g, 0)
+        want = oracle.seed(p)
+        oracle.step(p, want, steps)
+        assert rel_l2(mix[k].astype(np.complex128), want) <= steps * 4 * 2.0 ** -23, k
+        ref = oracle.observables(p, want)
+        assert abs(obs_mix[slots[k]]["mu"] - ref["mu"]) <= 1e-6 * max(1.0, abs(ref["mu"])), k
