@@ -98,6 +98,10 @@ __device__ double block_sum(double v, double *red /* >= 32 doubles */)
 //   middle: v_k  = (psi_k + kappa (d'_{k-1} + e_{k+1})) mid,
 //           mid  = 1 / (1 + 2 kappa + kappa (c'_{k-1} + c'_{m-k})), c'_0 = 0.
 constexpr int kSweepThreads = 64;
+#ifndef GP_SWEEP_PREFETCH
+#define GP_SWEEP_PREFETCH 4
+#endif
+constexpr int kPrefetch = GP_SWEEP_PREFETCH;     // points loaded ahead per thread
 constexpr unsigned kFull = 0xffffffffu;
 
 template <typename T>
@@ -128,7 +132,6 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
     const int m = g.n - 1;
     const int k = (m + 1) >> 1;              // middle unknown
     const int len = top ? k - 1 : m - k;     // points this lane eliminates
-    const int span = m - k;                  // >= k - 1
     const long long s = g.pstride;
     const long long base = active ? (long long)a * g.stride_a + (long long)b * g.stride_b : 0;
     C *line = psi + base;
@@ -139,17 +142,27 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
     Acc<T> nacc;
     C d = mk<T>((T)0, (T)0);
     if (active) {
-#pragma unroll 2
-        for (int t = 0; t < span; ++t) {
-            if (t < len) {
-                const long long at = (long long)(top ? 1 + t : m - t) * s;
-                C p = line[at];
-                if (NL) {
-                    p = nl.apply(p, top ? 1 + t : m - t);
-                    line[at] = p;
+        // loads are issued kPrefetch points at a time, ahead of the
+        // recurrence that consumes them
+        for (int t0 = 0; t0 < len; t0 += kPrefetch) {
+            C pv[kPrefetch];
+#pragma unroll
+            for (int q = 0; q < kPrefetch; ++q)
+                if (t0 + q < len) pv[q] = line[(long long)(top ? 1 + t0 + q : m - t0 - q) * s];
+#pragma unroll
+            for (int q = 0; q < kPrefetch; ++q) {
+                const int t = t0 + q;
+                if (t < len) {
+                    const int i = top ? 1 + t : m - t;
+                    const long long at = (long long)i * s;
+                    C p = pv[q];
+                    if (NL) {
+                        p = nl.apply(p, i);
+                        line[at] = p;
+                    }
+                    d = cn.fwd(p, d, mult[t]);
+                    wl[at] = d;
                 }
-                d = cn.fwd(p, d, mult[t]);
-                wl[at] = d;
             }
         }
     }
@@ -166,14 +179,25 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
     const C vpair = shfl_xor16<T>(vk);
     C v = top ? vk : vpair;
     if (active) {
-#pragma unroll 2
-        for (int t = span - 1; t >= 0; --t) {
-            if (t < len) {
-                const long long at = (long long)(top ? 1 + t : m - t) * s;
-                v = cn.back(wl[at], cp[t], v);
-                const C u = LineOps<T, MODE>::out(v, line[at]);
-                line[at] = u;
-                if (NORM) nacc.add(abs2<T>(u));
+        for (int t0 = len - 1; t0 >= 0; t0 -= kPrefetch) {
+            C wv[kPrefetch], lv[kPrefetch];
+#pragma unroll
+            for (int q = 0; q < kPrefetch; ++q)
+                if (t0 - q >= 0) {
+                    const long long at = (long long)(top ? 1 + t0 - q : m - t0 + q) * s;
+                    wv[q] = wl[at];
+                    lv[q] = line[at];
+                }
+#pragma unroll
+            for (int q = 0; q < kPrefetch; ++q) {
+                const int t = t0 - q;
+                if (t >= 0) {
+                    const long long at = (long long)(top ? 1 + t : m - t) * s;
+                    v = cn.back(wv[q], cp[t], v);
+                    const C u = LineOps<T, MODE>::out(v, lv[q]);
+                    line[at] = u;
+                    if (NORM) nacc.add(abs2<T>(u));
+                }
             }
         }
     }
