@@ -25,6 +25,15 @@ __device__ __forceinline__ float2 cmulc(float2 v, float4 f)
     return make_float2(fmaf(v.x, f.x, fmaf(-v.y, f.y, lx)), fmaf(v.x, f.y, fmaf(v.y, f.x, ly)));
 }
 
+// v * the hi part alone: for recurrences whose coefficient rounding is
+// scaled down by a small right-hand side (the increment form), where one
+// FP32 rounding of the coefficient is far below the result's own rounding
+__device__ __forceinline__ float2 cmulc_hi(float2 v, float4 f)
+{
+    return make_float2(fmaf(v.x, f.x, -v.y * f.y), fmaf(v.x, f.y, v.y * f.x));
+}
+__device__ __forceinline__ float rmulc_hi(float v, float4 f) { return v * f.x; }
+
 // real part of a coefficient (imaginary time: tables are real) times v
 __device__ __forceinline__ double rmulc(double v, double2 f) { return v * f.x; }
 __device__ __forceinline__ float rmulc(float v, float4 f) { return fmaf(v, f.x, v * f.z); }

@@ -36,10 +36,22 @@ __device__ __forceinline__ float2 fms_c(float2 d, float2 v, float4 f)
 
 // Crank-Nicolson line arithmetic.  MODE 0 (imaginary time): kappa = k real,
 // coefficient tables real.  MODE 1 (real time): kappa = i k, tables complex.
-template <typename T, int MODE> struct LineOps {
+// HI (complex64 only): apply the hi part of each FP32 hi + lo coefficient.
+template <typename T, int MODE, bool HI = false> struct LineOps {
     using C = typename Cx<T>::t;
     using F = typename Coef<T>::t;
     T k;
+
+    static __device__ __forceinline__ T rmul(T v, F f)
+    {
+        if constexpr (HI && sizeof(T) == 4) return rmulc_hi(v, f);
+        else return rmulc(v, f);
+    }
+    static __device__ __forceinline__ C cmul(C v, F f)
+    {
+        if constexpr (HI && sizeof(T) == 4) return cmulc_hi(v, f);
+        else return cmulc(v, f);
+    }
 
     // right-hand side (1 - 2 kappa) m + kappa (l + r)
     __device__ __forceinline__ C rhs(C l, C m, C r) const
@@ -55,14 +67,19 @@ template <typename T, int MODE> struct LineOps {
     // forward elimination step (p + kappa d) f
     __device__ __forceinline__ C fwd(C p, C d, F f) const
     {
-        if (MODE == 0) return cx<T>(rmulc(fma(k, d.x, p.x), f), rmulc(fma(k, d.y, p.y), f));
-        return cmulc(cx<T>(fma(-k, d.y, p.x), fma(k, d.x, p.y)), f);
+        if (MODE == 0) return cx<T>(rmul(fma(k, d.x, p.x), f), rmul(fma(k, d.y, p.y), f));
+        return cmul(cx<T>(fma(-k, d.y, p.x), fma(k, d.x, p.y)), f);
     }
     // back substitution step d - c v
     __device__ __forceinline__ C back(C d, F c, C v) const
     {
-        if (MODE == 0) return cx<T>(fms_re(d.x, v.x, c), fms_re(d.y, v.y, c));
-        return fms_c(d, v, c);
+        if constexpr (HI && sizeof(T) == 4) {
+            if (MODE == 0) return cx<T>(fmaf(-c.x, v.x, d.x), fmaf(-c.x, v.y, d.y));
+            return cx<T>(fmaf(-c.x, v.x, fmaf(c.y, v.y, d.x)), fmaf(-c.x, v.y, fmaf(-c.y, v.x, d.y)));
+        } else {
+            if (MODE == 0) return cx<T>(fms_re(d.x, v.x, c), fms_re(d.y, v.y, c));
+            return fms_c(d, v, c);
+        }
     }
     // u = 2 v - p  (the update when the line solves (I - kappa L) v = p)
     static __device__ __forceinline__ C out(C v, C p)

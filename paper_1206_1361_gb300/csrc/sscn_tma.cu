@@ -42,6 +42,10 @@
 #include "sscn_internal.h"
 #include "sscn_line.cuh"
 
+#ifndef GP_TMA_HI_ONLY
+#define GP_TMA_HI_ONLY 1
+#endif
+
 namespace gp {
 namespace {
 
@@ -219,7 +223,12 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
     using F = typename Coef<T>::t;
     const F *cp_tab = static_cast<const F *>(args.cp);
     const F *mult_tab = static_cast<const F *>(args.mult);
-    const LineOps<T, MODE> cn{(T)args.kappa};
+    // complex64 eliminates in increment form (below), where the rounding of
+    // the coefficients enters scaled by the small kappa L psi, so the hi
+    // parts suffice
+    constexpr bool INC = sizeof(T) == 4;
+    constexpr bool HI = INC && GP_TMA_HI_ONLY;
+    const LineOps<T, MODE, HI> cn{(T)args.kappa};
     const int conv = args.conv, win = args.win;
     F cinf, minf;
     if constexpr (sizeof(T) == 8) {
@@ -296,7 +305,6 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
         }
         // complex64: increment form with the forward pass one point behind
         // the newest point (it needs psi_{i+1}); FP64: u = 2 v - psi
-        constexpr bool INC = sizeof(T) == 4;
         auto slot = [&](int i) -> Cv & { return ring[((i / C) & 1) * C * L + (i % C) * L + l]; };
         auto output = [&](Cv v, Cv *tile_slot) {
             const Cv u = INC ? LineOps<T, MODE>::out_inc(v, *tile_slot) : LineOps<T, MODE>::out(v, *tile_slot);
