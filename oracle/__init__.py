@@ -14,7 +14,8 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Params", "lib", "coord", "seed", "step", "nonlinear", "sweep",
+__all__ = ["Params", "lib", "coord", "seed", "step", "step_ext", "nonlinear",
+           "nonlinear_part", "g_integral", "sweep",
            "norm", "observables", "energy_parts", "sums", "thomas_tables",
            "thomas_solve", "set_threads", "get_threads"]
 
@@ -57,6 +58,9 @@ def lib():
             "ref_thomas_tables": (None, [i32, dbl, dbl, vp, vp]),
             "ref_thomas_solve": (None, [i32, dbl, dbl, vp, vp, vp]),
             "ref_nonlinear": (None, [P, vp]),
+            "ref_nonlinear_part": (None, [P, vp, dbl, dbl]),
+            "ref_g_integral": (dbl, [dbl, dbl, dbl, dbl, dbl]),
+            "ref_step_ext": (None, [P, vp, i64, i64, i32, dbl, dbl]),
             "ref_sweep": (None, [P, i32, vp]),
             "ref_norm": (dbl, [P, vp]),
             "ref_scale": (None, [P, vp, dbl]),
@@ -107,6 +111,27 @@ def step(p, psi, n):
     """n SSCN steps in place."""
     _check(p, psi)
     lib().ref_step(ctypes.byref(p), _ptr(psi), int(n))
+    return psi
+
+
+def step_ext(p, psi, n, step0=0, strang=False, g1=0.0, omega=0.0):
+    """n steps in place from step index step0 with g(t) = p.g + g1 cos(omega t)
+    and the Lie (strang=False) or Strang splitting."""
+    _check(p, psi)
+    lib().ref_step_ext(ctypes.byref(p), _ptr(psi), int(n), int(step0), int(bool(strang)),
+                       float(g1), float(omega))
+    return psi
+
+
+def g_integral(g, g1, omega, ta, tb):
+    """Integral of g + g1 cos(omega t) over [ta, tb]."""
+    return lib().ref_g_integral(float(g), float(g1), float(omega), float(ta), float(tb))
+
+
+def nonlinear_part(p, psi, frac, G):
+    """Pointwise step theta = frac dt V + G |psi|^2."""
+    _check(p, psi)
+    lib().ref_nonlinear_part(ctypes.byref(p), _ptr(psi), float(frac), float(G))
     return psi
 
 

@@ -42,6 +42,23 @@
  *  calcrms  rms_k = sqrt(sum x_k^2 |psi|^2 / sum |psi|^2), rms_r likewise
  *           with r^2 = x^2 + y^2 + z^2.
  *
+ * Two extensions the paper's applications use (its cited work on a harmonic
+ * modulation of the scattering length and on Faraday waves) and the paper does
+ * not spell out either:
+ *  g(t)     g(t) = g + g1 cos(omega t).  A pointwise step over the interval
+ *           [t_a, t_b] applies the exact integral G = int g(t) dt in place of
+ *           dt g: in real time |psi| is constant during that step, so
+ *           psi exp(-i |psi|^2 G) solves i dpsi/dt = g(t) |psi|^2 psi exactly.
+ *           Step n covers [n dt, (n + 1) dt].
+ *  Strang   the symmetric splitting: a half pointwise step over the first half
+ *           of the interval, the x, y, z sweeps over dt, a half pointwise step
+ *           over the second half.  Second order in dt where the plain (Lie)
+ *           order above is first order.  In imaginary time the state is
+ *           renormalised before the second half step as well as after it:
+ *           the sweeps change N by O(dt), and a nonlinear half step taken on
+ *           the unnormalised state would see g scaled by that factor, which
+ *           costs the fixed point its second order.
+ *
  * Layout: psi[(k * n_y + j) * n_x + i], x fastest, C99 double complex.
  * Sweeps and the pointwise step may run their independent lines / points on
  * OpenMP threads (as the paper's threaded programs do); every reduction is a
@@ -210,6 +227,39 @@ void ref_nonlinear(const ref_params *p, cplx *psi)
     }
 }
 
+/*
+ * The pointwise step over part of a time step: theta = frac dt V + G |psi|^2,
+ * psi <- exp(-theta) psi (imaginary time) or exp(-i theta) psi (real time),
+ * where G is the integral of g over the part (frac dt g for constant g).
+ */
+void ref_nonlinear_part(const ref_params *p, cplx *psi, double frac, double G)
+{
+    const int32_t nx = p->nx, ny = p->ny, nz = p->nz;
+#pragma omp parallel for schedule(static)
+    for (int32_t k = 0; k < nz; k++) {
+        double z = ref_coord(nz, p->hz, k);
+        for (int32_t j = 0; j < ny; j++) {
+            double y = ref_coord(ny, p->hy, j);
+            for (int32_t i = 0; i < nx; i++) {
+                double x = ref_coord(nx, p->hx, i);
+                size_t at = ((size_t)k * ny + j) * nx + i;
+                cplx v = psi[at];
+                double a = creal(v) * creal(v) + cimag(v) * cimag(v);
+                double theta = frac * p->dt * potential(p, x, y, z) + G * a;
+                cplx f = p->mode == 1 ? cexp(-theta * I) : exp(-theta) + 0.0 * I;
+                psi[at] = f * v;
+            }
+        }
+    }
+}
+
+/* int_{ta}^{tb} (g + g1 cos(omega t)) dt */
+double ref_g_integral(double g, double g1, double omega, double ta, double tb)
+{
+    if (omega == 0.0) return (g + g1) * (tb - ta);
+    return g * (tb - ta) + g1 * (sin(omega * tb) - sin(omega * ta)) / omega;
+}
+
 /* calclux / calcluy / calcluz: the Crank-Nicolson sweep along one axis. */
 void ref_sweep(const ref_params *p, int32_t axis, cplx *psi)
 {
@@ -274,6 +324,37 @@ void ref_step(const ref_params *p, cplx *psi, int64_t nsteps)
         ref_sweep(p, 0, psi);
         ref_sweep(p, 1, psi);
         ref_sweep(p, 2, psi);
+        if (p->mode == 0) ref_scale(p, psi, 1.0 / sqrt(ref_norm(p, psi)));
+    }
+}
+
+/*
+ * n steps starting at step index step0 (time step0 dt) with the modulated
+ * g(t) = g + g1 cos(omega t) and either splitting: strang == 0 is the order of
+ * ref_step with G over [t_n, t_n + dt] in place of dt g; strang == 1 is a
+ * half pointwise step over [t_n, t_n + dt/2], the sweeps, (imaginary time: the
+ * renormalisation), half pointwise step over [t_n + dt/2, t_n + dt], then the
+ * renormalisation in imaginary time.
+ */
+void ref_step_ext(const ref_params *p, cplx *psi, int64_t nsteps, int64_t step0, int32_t strang,
+                  double g1, double omega)
+{
+    for (int64_t s = 0; s < nsteps; s++) {
+        double t0 = (double)(step0 + s) * p->dt;
+        if (strang) {
+            double th = t0 + 0.5 * p->dt, t1 = t0 + p->dt;
+            ref_nonlinear_part(p, psi, 0.5, ref_g_integral(p->g, g1, omega, t0, th));
+            ref_sweep(p, 0, psi);
+            ref_sweep(p, 1, psi);
+            ref_sweep(p, 2, psi);
+            if (p->mode == 0) ref_scale(p, psi, 1.0 / sqrt(ref_norm(p, psi)));
+            ref_nonlinear_part(p, psi, 0.5, ref_g_integral(p->g, g1, omega, th, t1));
+        } else {
+            ref_nonlinear_part(p, psi, 1.0, ref_g_integral(p->g, g1, omega, t0, t0 + p->dt));
+            ref_sweep(p, 0, psi);
+            ref_sweep(p, 1, psi);
+            ref_sweep(p, 2, psi);
+        }
         if (p->mode == 0) ref_scale(p, psi, 1.0 / sqrt(ref_norm(p, psi)));
     }
 }
