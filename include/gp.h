@@ -201,9 +201,34 @@ enum {
     /* Tile shape of the TMA sweep path: an index (0 .. GP_TILE_SHAPES - 1,
      * per precision) into the library's table of (lines per CTA, points per
      * chunk, pipeline stages); gp_get_option reads it back. */
-    GP_OPT_TILE_SHAPE = 2
+    GP_OPT_TILE_SHAPE = 2,
+    /* Operator splitting of one step (the paper's method is split-step
+     * Crank-Nicolson; the symmetric variant is what its cited applications
+     * with time-dependent interactions call for).  GP_SPLIT_LIE (default):
+     * pointwise step over dt, then the x, y, z sweeps.  GP_SPLIT_STRANG: half
+     * pointwise step, the sweeps, half pointwise step -- second order in dt in
+     * real time, where the plain order is first order.  In imaginary time the
+     * state is also renormalised before the second half step, which costs one
+     * extra pass over psi per step; its fixed point stays first order in dt
+     * (renormalisation does not commute with the nonlinear step) with a much
+     * smaller error. */
+    GP_OPT_SPLITTING = 3
 };
 enum { GP_PATH_AUTO = 0, GP_PATH_EXACT = 1, GP_PATH_TMA = 2 };
+enum { GP_SPLIT_LIE = 0, GP_SPLIT_STRANG = 1 };
+
+/*
+ * Harmonic modulation of the interaction (a modulated s-wave scattering
+ * length, as in the paper's cited work on parametric resonances and Faraday
+ * waves): from the next step on, g(t) = g + g1 cos(omega t), with g the value
+ * set by gp_create / gp_set_params and t = step * dt (the step counter is
+ * reset by gp_load).  Each pointwise (sub)step over [t_a, t_b] applies the
+ * exact integral of g(t) over it, which makes the real-time nonlinear phase
+ * exact.  gp_observables evaluates mu and E with g(t) at the current t.
+ * g1 = 0 switches it off.  GP_EINVAL for non-finite arguments.  Adds one
+ * one-thread launch per step (the device step counter).
+ */
+int gp_set_modulation(gp_ctx *ctx, double g1, double omega);
 
 /* Set an option; GP_EINVAL if the option or value is unknown or, for
  * GP_PATH_TMA, if some axis cannot take it.  Takes effect at the next step. */

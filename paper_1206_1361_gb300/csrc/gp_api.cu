@@ -32,6 +32,12 @@ struct gp_ctx {
     double2 *ph[2][3]{};            // [mode][axis] exp(-tau w_k^2 x^2 / 2)
     float4 *ph32[2][3]{};           // hi + lo pairs
     float *th32[3]{};               // dt w_k^2 x^2 / 2 per axis (FP32)
+    double2 *phh[2][3]{};           // half-step factors exp(-tau w_k^2 x^2 / 4)
+    float4 *phh32[2][3]{};
+    float *thh32[3]{};              // dt w_k^2 x^2 / 4 (FP32)
+    int split = GP_SPLIT_LIE;
+    double g1 = 0, omega = 0;       // g(t) = g + g1 cos(omega t)
+    long long *step_dev = nullptr;  // device step counter (modulated g)
     double *partials = nullptr;     // norm partials, >= max sweep blocks
     int partial_cap = 0;
     double *obs_partials = nullptr; // observables scratch (rows + finish stage)
@@ -178,16 +184,27 @@ int upload_tables(gp_ctx *c)
             }
             GP_CK(c, cudaMemcpy(c->ph[mode][k], t.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
             GP_CK(c, cudaMemcpy(c->ph32[mode][k], t32.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+            for (int i = 0; i < n; ++i) {
+                const double x = coord(n, c->h[k], i);
+                const double th = 0.5 * (c->dt * 0.5 * c->w[k] * c->w[k] * x * x);
+                t[i] = mode == 0 ? make_double2(std::exp(-th), 0.0)
+                                 : make_double2(std::cos(th), -std::sin(th));
+                t32[i] = gp::split_coef(t[i]);
+            }
+            GP_CK(c, cudaMemcpy(c->phh[mode][k], t.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+            GP_CK(c, cudaMemcpy(c->phh32[mode][k], t32.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
         }
     }
     for (int k = 0; k < 3; ++k) {
         const int n = edge(c->grid, k);
-        std::vector<float> th(n);
+        std::vector<float> th(n), thh(n);
         for (int i = 0; i < n; ++i) {
             const double x = coord(n, c->h[k], i);
             th[i] = (float)(c->dt * 0.5 * c->w[k] * c->w[k] * x * x);
+            thh[i] = 0.5f * th[i];
         }
         GP_CK(c, cudaMemcpy(c->th32[k], th.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+        GP_CK(c, cudaMemcpy(c->thh32[k], thh.data(), n * sizeof(float), cudaMemcpyHostToDevice));
     }
     return GP_OK;
 }
@@ -218,7 +235,8 @@ size_t footprint_bytes(const gp_grid &g, int prec)
     size_t tables = 0;
     for (int k = 0; k < 3; ++k) {
         const size_t n = edge(g, k);
-        tables += 2 * 2 * n * (sizeof(double2) + sizeof(float4)) + 2 * n * (sizeof(double2) + sizeof(float4));
+        tables += 2 * 2 * n * (sizeof(double2) + sizeof(float4)) + 2 * 2 * n * (sizeof(double2) + sizeof(float4)) +
+                  2 * n * sizeof(float);
     }
     int blocks = 0;
     for (int k = 0; k < naxes(g); ++k)
@@ -232,7 +250,8 @@ size_t footprint_bytes(const gp_grid &g, int prec)
     const size_t red = (size_t)blocks * sizeof(double) +
                        (size_t)gp::obs_scratch_doubles(oa) * sizeof(double) +
                        2 * (size_t)(g.nx + g.ny + g.nz) * sizeof(double) +
-                       gp::kObsWidth * sizeof(double) + 2 * sizeof(double) + sizeof(int);
+                       gp::kObsWidth * sizeof(double) + 2 * sizeof(double) + sizeof(int) +
+                       sizeof(long long);
     return 2 * psi + tables + red;
 }
 
@@ -245,8 +264,14 @@ void release(gp_ctx *c)
     for (auto &row : c->ax)
         for (auto &a : row) { fr(a.cp64); fr(a.mult64); fr(a.cp32); fr(a.mult32); }
     for (int mode = 0; mode < 2; ++mode)
-        for (int k = 0; k < 3; ++k) { fr(c->ph[mode][k]); fr(c->ph32[mode][k]); }
-    for (int k = 0; k < 3; ++k) fr(c->th32[k]);
+        for (int k = 0; k < 3; ++k) {
+            fr(c->ph[mode][k]);
+            fr(c->ph32[mode][k]);
+            fr(c->phh[mode][k]);
+            fr(c->phh32[mode][k]);
+        }
+    for (int k = 0; k < 3; ++k) { fr(c->th32[k]); fr(c->thh32[k]); }
+    fr(c->step_dev);
     fr(c->partials);
     fr(c->obs_partials);
     fr(c->obs_tab);
@@ -271,56 +296,105 @@ int sweep_path(const gp_ctx *c, int axis)
     return c->prec == GP_C64 ? GP_PATH_TMA : GP_PATH_EXACT;
 }
 
-cudaError_t launch_sweep(gp_ctx *c, int axis, const gp::NonlinArgs *nl, const Partials *norm,
-                         int *blocks)
+cudaError_t launch_sweep(gp_ctx *c, int axis, const gp::NonlinArgs *nl, bool nl_at_output,
+                         const Partials *norm, int *blocks)
 {
     const SweepGeom g = geom(c->grid, axis);
     const gp::AxisTables &ax = c->ax[c->mode][axis];
     if (sweep_path(c, axis) == GP_PATH_TMA) {
         if (blocks) *blocks = gp::tma_blocks(c->prec, c->tile_shape, g);
         return gp::launch_sweep_tma(c->prec, c->tile_shape, c->mode, axis, c->maps[axis], ax, g,
-                                    nl, norm, c->err_dev, c->stream);
+                                    nl, norm, c->err_dev, c->stream, nl_at_output);
     }
     if (blocks) *blocks = gp::sweep_blocks(g);
-    if (nl) return gp::launch_sweep_x(c->prec, c->mode, c->psi, c->work, ax, g, *nl, c->grid.ny,
-                                      c->grid.nz, norm, c->stream);
-    return gp::launch_sweep_yz(c->prec, c->mode, c->psi, c->work, ax, g, norm, c->stream);
+    if (nl && !nl_at_output)
+        return gp::launch_sweep_x(c->prec, c->mode, c->psi, c->work, ax, g, *nl, c->grid.ny,
+                                  c->grid.nz, norm, c->stream);
+    return gp::launch_sweep_yz(c->prec, c->mode, c->psi, c->work, ax, g, norm, c->stream,
+                               nl_at_output ? nl : nullptr);
+}
+
+bool modulated(const gp_ctx *c) { return c->g1 != 0.0; }
+
+// calcnu of the part [fa dt, fb dt] of a step, for a sweep along `axis`: the
+// factor tables along the axis first, then those of the line's (a, b) axes;
+// half selects the half-step tables.
+gp::NonlinArgs pointwise_args(const gp_ctx *c, int axis, bool half, double fa, double fb,
+                              const double *scale)
+{
+    const int order[3] = {axis, axis == 0 ? 1 : 0, axis == 2 ? 1 : 2};
+    const int mode = c->mode;
+    gp::NonlinArgs nl;
+    double2 *const *P = half ? c->phh[mode] : c->ph[mode];
+    float4 *const *P32 = half ? c->phh32[mode] : c->ph32[mode];
+    float *const *TH = half ? c->thh32 : c->th32;
+    nl.px = P[order[0]];
+    nl.py = P[order[1]];
+    nl.pz = P[order[2]];
+    nl.px32 = P32[order[0]];
+    nl.py32 = P32[order[1]];
+    nl.pz32 = P32[order[2]];
+    nl.tx32 = TH[order[0]];
+    nl.ty32 = TH[order[1]];
+    nl.tz32 = TH[order[2]];
+    nl.g.G = c->g * (fb - fa) * c->dt;
+    if (modulated(c)) {
+        nl.g.step = c->step_dev;
+        nl.g.g0 = c->g;
+        nl.g.g1 = c->g1;
+        nl.g.omega = c->omega;
+        nl.g.dt = c->dt;
+        nl.g.fa = fa;
+        nl.g.fb = fb;
+    }
+    nl.scale = scale;
+    return nl;
 }
 
 // Enqueue one SSCN step.  With ev != nullptr, record ev[0] before the first
-// kernel and ev[1 + k] after kernel slot k (x, y, z sweep, norm finish); slots
-// a step does not launch get their event recorded back to back.
+// kernel and ev[1 + k] after kernel slot k (x, y, z sweep, then the norm
+// finish and the rest of the step); slots a step does not launch get their
+// event recorded back to back.
+//   plain (Lie): calcnu(dt) fused into the x sweep; y, z sweeps; imaginary
+//                time: norm partials in the last sweep, norm finish.
+//   symmetric:   calcnu(dt/2) in the x sweep; y, z sweeps; calcnu(dt/2) fused
+//                into the last sweep's stores (real time), or (imaginary time)
+//                norm finish, calcnu(dt/2) pass with norm partials, norm finish.
 int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
 {
     const int mode = c->mode;
     const bool three_d = c->grid.nz > 1;
+    const bool strang = c->split == GP_SPLIT_STRANG;
+    const bool imag = mode == GP_IMAG;
+    const int last = three_d ? 2 : 1;
     Partials part{c->partials, 1};
-    const Partials *norm_x = nullptr;
-    gp::NonlinArgs nl;
-    nl.px = c->ph[mode][0];
-    nl.py = c->ph[mode][1];
-    nl.pz = c->ph[mode][2];
-    nl.px32 = c->ph32[mode][0];
-    nl.py32 = c->ph32[mode][1];
-    nl.pz32 = c->ph32[mode][2];
-    nl.tx32 = c->th32[0];
-    nl.ty32 = c->th32[1];
-    nl.tz32 = c->th32[2];
-    nl.dtg = c->dt * c->g;
-    nl.scale = c->scale;
+    const gp::NonlinArgs nl = pointwise_args(c, 0, strang, 0.0, strang ? 0.5 : 1.0, c->scale);
+    const gp::NonlinArgs nl2 =
+        pointwise_args(c, imag ? 0 : last, true, 0.5, 1.0, imag ? c->scale : nullptr);
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], c->stream) : cudaSuccess; };
     GP_CK(c, mark(0));
-    GP_CK(c, launch_sweep(c, 0, &nl, norm_x, nullptr));
+    GP_CK(c, launch_sweep(c, 0, &nl, false, nullptr, nullptr));
     GP_CK(c, mark(1));
-    const bool imag = mode == GP_IMAG;
     int last_blocks = 0;
-    GP_CK(c, launch_sweep(c, 1, nullptr, (imag && !three_d) ? &part : nullptr, &last_blocks));
-    GP_CK(c, mark(2));
-    if (three_d) GP_CK(c, launch_sweep(c, 2, nullptr, imag ? &part : nullptr, &last_blocks));
-    GP_CK(c, mark(3));
-    if (imag)
+    for (int axis = 1; axis <= last; ++axis) {
+        const bool is_last = axis == last;
+        const gp::NonlinArgs *out_nl = (is_last && strang && !imag) ? &nl2 : nullptr;
+        GP_CK(c, launch_sweep(c, axis, out_nl, out_nl != nullptr,
+                              (is_last && imag) ? &part : nullptr, &last_blocks));
+        GP_CK(c, mark(axis + 1));
+    }
+    if (!three_d) GP_CK(c, mark(3));
+    if (imag) {
         GP_CK(c, gp::launch_norm_finish(c->partials, last_blocks, cell_volume(c), c->scale,
                                         c->norm_dev, c->err_dev, c->stream));
+        if (strang) {
+            GP_CK(c, gp::launch_calcnu_pass(c->prec, mode, c->psi, c->grid.nx, c->grid.ny,
+                                            c->grid.nz, nl2, part, gp::kReduceBlocks, c->stream));
+            GP_CK(c, gp::launch_norm_finish(c->partials, gp::kReduceBlocks, cell_volume(c),
+                                            c->scale, c->norm_dev, c->err_dev, c->stream));
+        }
+    }
+    if (modulated(c)) GP_CK(c, gp::launch_add_step(c->step_dev, c->stream));
     GP_CK(c, mark(4));
     return GP_OK;
 }
@@ -328,7 +402,9 @@ int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
 // Kernel launches per step (for launch accounting).
 int kernels_per_step(const gp_ctx *c)
 {
-    return (c->grid.nz > 1 ? 3 : 2) + (c->mode == GP_IMAG ? 1 : 0);
+    const bool imag = c->mode == GP_IMAG, strang = c->split == GP_SPLIT_STRANG;
+    return (c->grid.nz > 1 ? 3 : 2) + (imag ? 1 : 0) + (imag && strang ? 2 : 0) +
+           (modulated(c) ? 1 : 0);
 }
 
 void drop_graph(gp_ctx *c)
@@ -575,9 +651,14 @@ int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, 
             const size_t n = edge(c->grid, k);
             if ((rc = alloc(c, (void **)&c->ph[mode_i][k], n * sizeof(double2)))) return bail(rc);
             if ((rc = alloc(c, (void **)&c->ph32[mode_i][k], n * sizeof(float4)))) return bail(rc);
+            if ((rc = alloc(c, (void **)&c->phh[mode_i][k], n * sizeof(double2)))) return bail(rc);
+            if ((rc = alloc(c, (void **)&c->phh32[mode_i][k], n * sizeof(float4)))) return bail(rc);
         }
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 3; ++k) {
         if ((rc = alloc(c, (void **)&c->th32[k], edge(c->grid, k) * sizeof(float)))) return bail(rc);
+        if ((rc = alloc(c, (void **)&c->thh32[k], edge(c->grid, k) * sizeof(float)))) return bail(rc);
+    }
+    if ((rc = alloc(c, (void **)&c->step_dev, sizeof(long long)))) return bail(rc);
     int blocks = gp::kReduceBlocks;
     for (int k = 0; k < naxes(c->grid); ++k)
         for (int sh = 0; sh < gp::tma_shapes(precision); ++sh)
@@ -610,6 +691,7 @@ int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, 
     {
         cudaError_t e = cudaMemsetAsync(c->psi, 0, psi_bytes, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->step_dev, 0, sizeof(long long), c->stream);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemsetAsync"));
         const double one = 1.0;
         e = cudaMemcpyAsync(c->scale, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream);
@@ -626,6 +708,7 @@ int gp_load(gp_ctx *c, const void *psi, int64_t count, int on_device)
     const long long n = points(c->grid);
     c->scale_pending = false;
     c->step = 0;
+    GP_CK(c, gp::launch_set_step(c->step_dev, 0, c->stream));
     if (psi == nullptr) {
         GP_CK(c, gp::launch_seed(c->prec, c->psi, c->grid.nx, c->grid.ny, c->grid.nz, c->h,
                                  c->w, c->stream));
@@ -675,6 +758,18 @@ int gp_set_params(gp_ctx *c, double g, int mode)
     return GP_OK;
 }
 
+int gp_set_modulation(gp_ctx *c, double g1, double omega)
+{
+    if (!c) return fail(nullptr, GP_EINVAL, "gp_set_modulation: null context");
+    if (!std::isfinite(g1) || !std::isfinite(omega))
+        return fail(c, GP_EINVAL, "gp_set_modulation: g1 and omega must be finite");
+    c->g1 = g1;
+    c->omega = omega;
+    GP_CK(c, gp::launch_set_step(c->step_dev, c->step, c->stream));
+    drop_graph(c);
+    return GP_OK;
+}
+
 int gp_step(gp_ctx *c, int64_t n)
 {
     if (!c) return fail(nullptr, GP_EINVAL, "gp_step: null context");
@@ -706,9 +801,11 @@ int gp_observables(gp_ctx *c, gp_obs *o)
     const double n = w * s[0];
     double kin = 0.5 * (s[6] / (c->h[0] * c->h[0]) + s[7] / (c->h[1] * c->h[1]));
     if (c->grid.nz > 1) kin += 0.5 * s[8] / (c->h[2] * c->h[2]);
+    // g at the current time (modulated: g + g1 cos(omega t))
+    const double g_now = modulated(c) ? c->g + c->g1 * std::cos(c->omega * (c->step * c->dt)) : c->g;
     o->norm = n;
-    o->mu = w * (kin + s[4] + c->g * s[5]) / n;
-    o->energy = w * (kin + s[4] + 0.5 * c->g * s[5]) / n;
+    o->mu = w * (kin + s[4] + g_now * s[5]) / n;
+    o->energy = w * (kin + s[4] + 0.5 * g_now * s[5]) / n;
     o->rms_x = std::sqrt(s[1] / s[0]);
     o->rms_y = std::sqrt(s[2] / s[0]);
     o->rms_z = std::sqrt(s[3] / s[0]);
@@ -763,6 +860,13 @@ int gp_time_kernels(gp_ctx *c, int64_t steps, double *ms_out, int n_out)
 int gp_set_option(gp_ctx *c, int option, int value)
 {
     if (!c) return fail(nullptr, GP_EINVAL, "gp_set_option: null context");
+    if (option == GP_OPT_SPLITTING) {
+        if (value != GP_SPLIT_LIE && value != GP_SPLIT_STRANG)
+            return fail(c, GP_EINVAL, "gp_set_option: unknown splitting");
+        c->split = value;
+        drop_graph(c);
+        return GP_OK;
+    }
     if (option == GP_OPT_TILE_SHAPE) {
         if (value < 0 || value >= gp::tma_shapes(c->prec))
             return fail(c, GP_EINVAL, "gp_set_option: tile shape out of range");
@@ -850,6 +954,8 @@ int gp_autotune(gp_ctx *c, int steps, int *path_out, int *shape_out, double *ms_
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (gp::launch_set_step(c->step_dev, step0, c->stream) != cudaSuccess && rc == GP_OK)
+        rc = fail(c, GP_ECUDA, "gp_autotune: restore the step counter");
     e = cudaStreamSynchronize(c->stream);
     cleanup();
     c->step = step0;
@@ -877,6 +983,7 @@ int gp_get_option(gp_ctx *c, int option, int *value)
     if (!c || !value) return fail(c, GP_EINVAL, "gp_get_option: null argument");
     if (option == GP_OPT_SWEEP_PATH) *value = c->path_opt;
     else if (option == GP_OPT_TILE_SHAPE) *value = c->tile_shape;
+    else if (option == GP_OPT_SPLITTING) *value = c->split;
     else return fail(c, GP_EINVAL, "gp_get_option: unknown option");
     return GP_OK;
 }

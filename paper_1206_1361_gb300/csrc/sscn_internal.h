@@ -56,18 +56,43 @@ struct SweepGeom {
     long long stride_a, stride_b, pstride;
 };
 
-// Fused potential / nonlinearity data for the x sweep.  V is separable, so
-// exp(-tau V) = P_x[i] P_y[j] P_z[k] with per-axis factor tables
-// P_k[i] = exp(-tau omega_k^2 x_i^2 / 2) (tau = dt: real factors stored as
-// (f, 0); tau = i dt: unit complex numbers), computed on the host in FP64.
-// Only the nonlinear phase dt g |psi|^2 is evaluated per point.
+// G, the integral of g(t) over the part [fa dt, fb dt] of step n (t = n dt)
+// that one pointwise step covers: the constant G when step == nullptr, else
+// for g(t) = g0 + g1 cos(omega t) read from the device step counter.  In
+// real time |psi| is constant during the pointwise step, so exp(-i G |psi|^2)
+// is its exact nonlinear phase for any g(t).
+struct StepG {
+    const long long *step = nullptr;
+    double G = 0;
+    double g0 = 0, g1 = 0, omega = 0, dt = 0, fa = 0, fb = 1;
+
+#ifdef __CUDACC__
+    __device__ __forceinline__ double value() const
+    {
+        if (!step) return G;
+        const double t0 = (double)*step * dt;
+        const double ta = t0 + fa * dt, tb = t0 + fb * dt;
+        if (omega == 0.0) return (g0 + g1) * (tb - ta);
+        return g0 * (tb - ta) + g1 * (sin(omega * tb) - sin(omega * ta)) / omega;
+    }
+#endif
+};
+
+// Fused potential / nonlinearity data (calcnu) of one sweep.  V is
+// separable, so exp(-tau V) = P_x[i] P_y[j] P_z[k] with per-axis factor tables
+// P_k[i] = exp(-tau omega_k^2 x_i^2 / 2) (tau = dt, or dt / 2 for a half step:
+// real factors stored as (f, 0); tau = i dt or i dt / 2: unit complex numbers),
+// computed on the host in FP64.  Only the nonlinear phase G |psi|^2 is
+// evaluated per point.  The tables come in the order the sweep needs them:
+// px along the sweep's lines, py and pz indexed by the line's (a, b) (x
+// sweep: x; y, z.  z sweep: z; x, y.  y sweep in 2D: y; x, z).
 struct NonlinArgs {
     const double2 *px = nullptr, *py = nullptr, *pz = nullptr;   // FP64 tables
     const float4 *px32 = nullptr, *py32 = nullptr, *pz32 = nullptr;   // hi + lo pairs
-    // complex64 real time: phase tables theta_k = dt omega_k^2 x^2 / 2 (FP32)
+    // complex64 real time: phase tables theta_k = tau omega_k^2 x^2 / 2 (FP32)
     const float *tx32 = nullptr, *ty32 = nullptr, *tz32 = nullptr;
-    double dtg = 0;
-    const double *scale = nullptr;   // pending imaginary-time scale (device)
+    StepG g;                         // G of the (sub)step
+    const double *scale = nullptr;   // pending imaginary-time scale (device); nullptr: none
 };
 
 // Reduction partials of one sweep / observables pass.
@@ -87,10 +112,22 @@ cudaError_t launch_sweep_x(int prec, int mode, void *psi, void *work,
                            const AxisTables &ax, const SweepGeom &g,
                            const NonlinArgs &nl, int ny, int nz,
                            const Partials *norm_out, cudaStream_t st);
-// y or z sweep; norm_out != nullptr adds the FP64 sum |u|^2 per block.
+// y or z sweep; norm_out != nullptr adds the FP64 sum |u|^2 per block;
+// nlout != nullptr (real time, no norm) applies calcnu to every result
+// before it is stored, with the tables in this sweep's order.
 cudaError_t launch_sweep_yz(int prec, int mode, void *psi, void *work,
                             const AxisTables &ax, const SweepGeom &g,
-                            const Partials *norm_out, cudaStream_t st);
+                            const Partials *norm_out, cudaStream_t st,
+                            const NonlinArgs *nlout = nullptr);
+// calcnu as its own pass over every point (x lines; tables in x, y, z order)
+// with the FP64 sums |psi|^2 into `blocks` partials: the imaginary-time
+// symmetric splitting's second half step, after the renormalisation.
+cudaError_t launch_calcnu_pass(int prec, int mode, void *psi, int nx, int ny, int nz,
+                               const NonlinArgs &nl, const Partials &norm_out, int blocks,
+                               cudaStream_t st);
+// Device step counter (modulated g): set it, or add one.
+cudaError_t launch_set_step(long long *step, long long value, cudaStream_t st);
+cudaError_t launch_add_step(long long *step, cudaStream_t st);
 int sweep_blocks(const SweepGeom &g);
 
 // scale <- 1 / sqrt(w * sum(partials)); flags a non-finite or non-positive sum.
@@ -136,11 +173,14 @@ int tma_blocks(int prec, int shape, const SweepGeom &g);
 // layout breaks a TMA rule (complex64 rows must be a multiple of 16 bytes).
 cudaError_t make_sweep_map(int prec, int shape, void *psi, int nx, int ny, int nz, int axis,
                            CUtensorMap *out);
-// Windowed, TMA-staged sweep; nl != nullptr fuses calcnu (x sweep);
-// norm_out adds FP64 sum |u|^2 per block; err receives bit 2 on a wait timeout.
+// Windowed, TMA-staged sweep; nl != nullptr fuses calcnu: on every loaded
+// point (x sweep), or with nl_at_output on every result before it is stored
+// (real time, y or z sweep, no norm); norm_out adds FP64 sum |u|^2 per block;
+// err receives bit 2 on a wait timeout.
 cudaError_t launch_sweep_tma(int prec, int shape, int mode, int axis, const CUtensorMap &map,
                              const AxisTables &ax, const SweepGeom &g, const NonlinArgs *nl,
-                             const Partials *norm_out, int *err, cudaStream_t st);
+                             const Partials *norm_out, int *err, cudaStream_t st,
+                             bool nl_at_output = false);
 
 // Forward-elimination tables of (I - kappa L) with m unknowns, kappa = kre +
 // i kim: mult_i = 1 / (1 + 2 kappa + kappa c'_{i-1}), c'_i = -kappa mult_i

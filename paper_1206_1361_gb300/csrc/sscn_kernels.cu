@@ -112,7 +112,10 @@ __device__ __forceinline__ typename CT<T>::c shfl_xor16(typename CT<T>::c v)
     return v;
 }
 
-template <typename T, int MODE, bool NL, bool NORM>
+// NL: calcnu on each point as it is loaded (the x sweep); NLOUT: calcnu on
+// each result before it is stored (the second half step of the symmetric
+// splitting, in the last sweep).
+template <typename T, int MODE, bool NL, bool NORM, bool NLOUT = false>
 __global__ void __launch_bounds__(kSweepThreads)
 k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ work,
         const typename Coef<T>::t *__restrict__ cp,
@@ -120,7 +123,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
         T kappa, const typename Coef<T>::t *__restrict__ px,
         const typename Coef<T>::t *__restrict__ py, const typename Coef<T>::t *__restrict__ pz,
         const float *__restrict__ tx, const float *__restrict__ ty, const float *__restrict__ tz,
-        double dtg, const double *__restrict__ scale, double *__restrict__ partials)
+        StepG sg, const double *__restrict__ scale, double *__restrict__ partials)
 {
     using C = typename CT<T>::c;
     __shared__ double red[32];
@@ -138,7 +141,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
     C *wl = work + base;
     const LineOps<T, MODE> cn{kappa};
     Calcnu<T, MODE> nl{};
-    if (NL && active) nl.setup(px, py, pz, tx, ty, tz, a, b, dtg, scale);   // x sweep: a = y, b = z
+    if ((NL || NLOUT) && active) nl.setup(px, py, pz, tx, ty, tz, a, b, sg.value(), scale);
     Acc<T> nacc;
     C d = mk<T>((T)0, (T)0);
     if (active) {
@@ -172,7 +175,8 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
         C pk = line[(long long)k * s];
         if (NL) pk = nl.apply(pk, k);
         vk = cn.fwd(pk, mk<T>(d.x + other.x, d.y + other.y), mid);
-        const C u = LineOps<T, MODE>::out(vk, pk);
+        C u = LineOps<T, MODE>::out(vk, pk);
+        if (NLOUT) u = nl.apply(u, k);
         line[(long long)k * s] = u;
         if (NORM) nacc.add(abs2<T>(u));
     }
@@ -194,7 +198,8 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
                 if (t >= 0) {
                     const long long at = (long long)(top ? 1 + t : m - t) * s;
                     v = cn.back(wv[q], cp[t], v);
-                    const C u = LineOps<T, MODE>::out(v, lv[q]);
+                    C u = LineOps<T, MODE>::out(v, lv[q]);
+                    if (NLOUT) u = nl.apply(u, top ? 1 + t : m - t);
                     line[at] = u;
                     if (NORM) nacc.add(abs2<T>(u));
                 }
@@ -209,7 +214,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
 
 constexpr int kLinesPerBlock = kSweepThreads / 2;
 
-template <typename T, int MODE, bool NL, bool NORM>
+template <typename T, int MODE, bool NL, bool NORM, bool NLOUT = false>
 cudaError_t sweep_launch(void *psi, void *work, const AxisTables &ax,
                          const SweepGeom &g, const NonlinArgs *nl,
                          const Partials *norm_out, cudaStream_t st)
@@ -232,9 +237,9 @@ cudaError_t sweep_launch(void *psi, void *work, const AxisTables &ax,
         mid = ax.mid32;
         if (nl) { px = nl->px32; py = nl->py32; pz = nl->pz32; }
     }
-    k_sweep<T, MODE, NL, NORM><<<grid, kSweepThreads, 0, st>>>(
+    k_sweep<T, MODE, NL, NORM, NLOUT><<<grid, kSweepThreads, 0, st>>>(
         reinterpret_cast<C *>(psi), reinterpret_cast<C *>(work), cp, mult, mid, g, kappa,
-        px, py, pz, tx, ty, tz, nl ? nl->dtg : 0.0, nl ? nl->scale : nullptr,
+        px, py, pz, tx, ty, tz, nl ? nl->g : StepG{}, nl ? nl->scale : nullptr,
         norm_out ? norm_out->buf : nullptr);
     return cudaGetLastError();
 }
@@ -339,6 +344,43 @@ __global__ void k_norm_partials(const typename CT<T>::c *__restrict__ psi, long 
     const double r = block_sum(v, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = r;
 }
+
+// calcnu as a pass of its own: one warp per x line (j, k), fixed line-to-warp
+// assignment, FP64 sum |u|^2 per block (imaginary-time symmetric splitting:
+// the second half step after the renormalisation, with the pending scale).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+k_calcnu_pass(typename CT<T>::c *__restrict__ psi, int nx, int ny, int nz,
+              const typename Coef<T>::t *__restrict__ px, const typename Coef<T>::t *__restrict__ py,
+              const typename Coef<T>::t *__restrict__ pz, const float *__restrict__ tx,
+              const float *__restrict__ ty, const float *__restrict__ tz, StepG sg,
+              const double *__restrict__ scale, double *__restrict__ partials)
+{
+    using C = typename CT<T>::c;
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const double G = sg.value();
+    const long long lines = (long long)ny * nz;
+    double acc = 0.0;
+    for (long long L = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); L < lines;
+         L += warps) {
+        const int j = (int)(L % ny), k = (int)(L / ny);
+        Calcnu<T, MODE> nl{};
+        nl.setup(px, py, pz, tx, ty, tz, j, k, G, scale);
+        C *line = psi + L * nx;
+        for (int i = lane; i < nx; i += 32) {
+            const C u = nl.apply(line[i], i);
+            line[i] = u;
+            acc += abs2d<T>(u);
+        }
+    }
+    const double r = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = r;
+}
+
+__global__ void k_set_step(long long *step, long long value) { *step = value; }
+__global__ void k_add_step(long long *step) { *step += 1; }
 
 // ------------------------------------------------------------ observables
 //
@@ -454,8 +496,16 @@ cudaError_t launch_sweep_x(int prec, int mode, void *psi, void *work,
 
 cudaError_t launch_sweep_yz(int prec, int mode, void *psi, void *work,
                             const AxisTables &ax, const SweepGeom &g,
-                            const Partials *norm_out, cudaStream_t st)
+                            const Partials *norm_out, cudaStream_t st, const NonlinArgs *nlout)
 {
+    if (nlout) {
+        // the symmetric splitting's second half step, fused where the real-time
+        // last sweep stores (imaginary time takes a separate pass after the
+        // renormalisation)
+        if (mode != 1 || norm_out) return cudaErrorInvalidValue;
+        if (prec == kC128) return sweep_launch<double, 1, false, false, true>(psi, work, ax, g, nlout, nullptr, st);
+        return sweep_launch<float, 1, false, false, true>(psi, work, ax, g, nlout, nullptr, st);
+    }
     if (prec == kC128) return sweep_dispatch<double, false>(mode, psi, work, ax, g, nullptr, norm_out, st);
     return sweep_dispatch<float, false>(mode, psi, work, ax, g, nullptr, norm_out, st);
 }
@@ -511,6 +561,34 @@ cudaError_t launch_norm_partials(int prec, const void *psi, long long count,
         k_norm_partials<double><<<blocks, kPointThreads, 0, st>>>((const double2 *)psi, count, out.buf);
     else
         k_norm_partials<float><<<blocks, kPointThreads, 0, st>>>((const float2 *)psi, count, out.buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_calcnu_pass(int prec, int mode, void *psi, int nx, int ny, int nz,
+                               const NonlinArgs &nl, const Partials &norm_out, int blocks,
+                               cudaStream_t st)
+{
+    if (prec == kC128) {
+        auto k = mode == 0 ? k_calcnu_pass<double, 0> : k_calcnu_pass<double, 1>;
+        k<<<blocks, 256, 0, st>>>((double2 *)psi, nx, ny, nz, nl.px, nl.py, nl.pz, nl.tx32, nl.ty32,
+                                  nl.tz32, nl.g, nl.scale, norm_out.buf);
+    } else {
+        auto k = mode == 0 ? k_calcnu_pass<float, 0> : k_calcnu_pass<float, 1>;
+        k<<<blocks, 256, 0, st>>>((float2 *)psi, nx, ny, nz, nl.px32, nl.py32, nl.pz32, nl.tx32,
+                                  nl.ty32, nl.tz32, nl.g, nl.scale, norm_out.buf);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_step(long long *step, long long value, cudaStream_t st)
+{
+    k_set_step<<<1, 1, 0, st>>>(step, value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_step(long long *step, cudaStream_t st)
+{
+    k_add_step<<<1, 1, 0, st>>>(step);
     return cudaGetLastError();
 }
 

@@ -4,6 +4,9 @@
 #pragma once
 
 #include "sscn_coef.cuh"
+#include "sscn_internal.h"
+
+using gp::StepG;
 
 template <typename T> struct Cx;
 template <> struct Cx<double> { using t = double2; };
@@ -179,7 +182,8 @@ __device__ __forceinline__ void phase_delta(float a, float &cm1, float &s)
     }
 }
 
-// calcnu at one point of an x line: imaginary time s P exp(-dt g |s psi|^2)
+// calcnu at one point of a line (written for an x line; any axis works with
+// the tables passed in that order): imaginary time s P exp(-dt g |s psi|^2)
 // psi (P real), real time P exp(-i dt g |psi|^2) psi (P unit complex), with
 // P = P_x[i] P_y[j] P_z[k] from per-axis factor tables (V is separable).
 // Complex64 real time instead forms the whole phase Theta = theta_x[i] +
@@ -207,7 +211,9 @@ template <typename T, int MODE> struct Calcnu {
         f = make_float4(hx, hy, (float)(v.x - (double)hx), (float)(v.y - (double)hy));
     }
 
-    // per line (j, k): factor tables, phase tables, dt g, pending scale
+    // per line (j, k): factor tables (px along the line, py[j] and pz[k] for
+    // the line), phase tables likewise, G (dt g for a whole step at constant
+    // g), pending scale (nullptr: none)
     __device__ __forceinline__ void setup(const F *px_, const F *py, const F *pz, const float *tx_,
                                           const float *ty, const float *tz, int j, int k,
                                           double dtg, const double *scale)
@@ -216,7 +222,7 @@ template <typename T, int MODE> struct Calcnu {
         tx = tx_;
         const double2 y = as_d(py[j]), z = as_d(pz[k]);
         if (MODE == 0) {
-            const double sc = *scale;
+            const double sc = scale ? *scale : 1.0;
             to_f(make_double2(sc * y.x * z.x, 0.0), pyz);
             a_coef = (T)(dtg * sc * sc);
             tyz = 0.f;

@@ -158,7 +158,7 @@ struct TmaArgs {
     const void *px, *py, *pz;   // calcnu factor tables (x sweep)
     const float *tx, *ty, *tz;  // complex64 phase tables (x sweep)
     double kappa;       // kre (imaginary time) or kim (real time)
-    double dtg;
+    StepG g;            // G of the fused pointwise step
     const double *scale;
     double *partials;   // norm partials (NORM)
     int *err;           // device error bits
@@ -195,7 +195,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 // (one arrival per warp).  The producer stores a chunk once it is ready and
 // reuses its stage only after that store has read shared memory, so the
 // consumers never wait on a store.
-template <typename T, int MODE, int AXIS, bool NL, bool NORM, int K, int C, int S>
+// NL: calcnu on each point as it arrives (x sweep); NLOUT: calcnu on each
+// result before it is stored (the symmetric splitting's second half step in
+// the last real-time sweep).
+template <typename T, int MODE, int AXIS, bool NL, bool NORM, int K, int C, int S,
+          bool NLOUT = false>
 __global__ void __launch_bounds__(32 * (K + 1))
 k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
 {
@@ -298,16 +302,17 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
         }
     } else {
         Calcnu<T, MODE> nl{};
-        if (NL && active) {
+        if ((NL || NLOUT) && active) {
             const F *py = static_cast<const F *>(args.py), *pz = static_cast<const F *>(args.pz);
             nl.setup(static_cast<const F *>(args.px), py, pz, args.tx, args.ty, args.tz, a,
-                     blockIdx.y, args.dtg, args.scale);
+                     blockIdx.y, args.g.value(), args.scale);
         }
         // complex64: increment form with the forward pass one point behind
         // the newest point (it needs psi_{i+1}); FP64: u = 2 v - psi
         auto slot = [&](int i) -> Cv & { return ring[((i / C) & 1) * C * L + (i % C) * L + l]; };
-        auto output = [&](Cv v, Cv *tile_slot) {
-            const Cv u = INC ? LineOps<T, MODE>::out_inc(v, *tile_slot) : LineOps<T, MODE>::out(v, *tile_slot);
+        auto output = [&](Cv v, Cv *tile_slot, int i) {
+            Cv u = INC ? LineOps<T, MODE>::out_inc(v, *tile_slot) : LineOps<T, MODE>::out(v, *tile_slot);
+            if (NLOUT) u = nl.apply(u, i);
             *tile_slot = u;
             if (NORM) nacc.add(fma(u.x, u.x, u.y * u.y));
         };
@@ -367,7 +372,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                         const int i = (q - 1) * C + c;
                         if (i < 1) break;
                         v = cn.back(slot(i), cp(i - 1), v);
-                        output(v, at(q - 1, c));
+                        output(v, at(q - 1, c), i);
                     }
                 } else if (last) {
                     // exact: v_m = d'_m, down through chunks q and q - 1
@@ -375,7 +380,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                     const int lo = q >= 1 ? (q - 1) * C : 0;
                     for (int i = m; i >= lo && i >= 1; --i) {
                         if (i < m) v = cn.back(slot(i), cp(i - 1), v);
-                        output(v, at(i / C, i % C));
+                        output(v, at(i / C, i % C), i);
                     }
                 }
             }
@@ -416,11 +421,12 @@ constexpr size_t tma_smem_bytes()
            32 * sizeof(double);
 }
 
-template <typename T, int MODE, int AXIS, bool NL, bool NORM, int K, int C, int S>
+template <typename T, int MODE, int AXIS, bool NL, bool NORM, int K, int C, int S,
+          bool NLOUT = false>
 cudaError_t launch_tma_inst(const CUtensorMap &map, const TmaArgs &args, int tiles, int lines_b,
                             cudaStream_t st)
 {
-    auto kern = k_sweep_tma<T, MODE, AXIS, NL, NORM, K, C, S>;
+    auto kern = k_sweep_tma<T, MODE, AXIS, NL, NORM, K, C, S, NLOUT>;
     constexpr size_t smem = tma_smem_bytes<T, K, C, S>();
     constexpr int threads = 32 * (K + 1);
     static bool configured[64] = {};          // per device ordinal
@@ -441,9 +447,18 @@ cudaError_t launch_tma_inst(const CUtensorMap &map, const TmaArgs &args, int til
 }
 
 template <typename T, int AXIS, int K, int C, int S>
-cudaError_t launch_tma_axis(int mode, bool nl, bool norm, const CUtensorMap &map,
+cudaError_t launch_tma_axis(int mode, bool nl, bool norm, bool nlout, const CUtensorMap &map,
                             const TmaArgs &args, int tiles, int lines_b, cudaStream_t st)
 {
+    // the symmetric splitting's second half step: real time, y or z sweep
+    if (nlout) {
+        if constexpr (AXIS == 0) return cudaErrorInvalidValue;
+        else {
+            if (mode != 1 || norm || nl) return cudaErrorInvalidValue;
+            return launch_tma_inst<T, 1, AXIS, false, false, K, C, S, true>(map, args, tiles,
+                                                                           lines_b, st);
+        }
+    }
     // calcnu is fused into the x sweep only
 #define GP_TMA(MODE, NLV, NORMV)                                                             \
     return launch_tma_inst<T, MODE, AXIS, (NLV && AXIS == 0), NORMV, K, C, S>(map, args, tiles, \
@@ -470,12 +485,12 @@ constexpr Shape kShapes64[] = {{1, 8, 4}, {2, 8, 4}, {4, 8, 3}};
 constexpr int kNumShapes32 = 5, kNumShapes64 = 3;
 
 template <typename T, int K, int C, int S>
-cudaError_t launch_shape(int mode, int axis, bool nl, bool norm, const CUtensorMap &map,
+cudaError_t launch_shape(int mode, int axis, bool nl, bool norm, bool nlout, const CUtensorMap &map,
                          const TmaArgs &args, int tiles, int lines_b, cudaStream_t st)
 {
-    if (axis == 0) return launch_tma_axis<T, 0, K, C, S>(mode, nl, norm, map, args, tiles, lines_b, st);
-    if (axis == 1) return launch_tma_axis<T, 1, K, C, S>(mode, nl, norm, map, args, tiles, lines_b, st);
-    return launch_tma_axis<T, 2, K, C, S>(mode, nl, norm, map, args, tiles, lines_b, st);
+    if (axis == 0) return launch_tma_axis<T, 0, K, C, S>(mode, nl, norm, nlout, map, args, tiles, lines_b, st);
+    if (axis == 1) return launch_tma_axis<T, 1, K, C, S>(mode, nl, norm, nlout, map, args, tiles, lines_b, st);
+    return launch_tma_axis<T, 2, K, C, S>(mode, nl, norm, nlout, map, args, tiles, lines_b, st);
 }
 
 Shape shape_of(int prec, int shape)
@@ -529,7 +544,7 @@ cudaError_t make_sweep_map(int prec, int shape, void *psi, int nx, int ny, int n
 
 cudaError_t launch_sweep_tma(int prec, int shape, int mode, int axis, const CUtensorMap &map,
                              const AxisTables &ax, const SweepGeom &g, const NonlinArgs *nl,
-                             const Partials *norm_out, int *err, cudaStream_t st)
+                             const Partials *norm_out, int *err, cudaStream_t st, bool nl_at_output)
 {
     TmaArgs args{};
     args.n = g.n;
@@ -559,16 +574,17 @@ cudaError_t launch_sweep_tma(int prec, int shape, int mode, int axis, const CUte
         args.tx = nl->tx32;
         args.ty = nl->ty32;
         args.tz = nl->tz32;
-        args.dtg = nl->dtg;
+        args.g = nl->g;
         args.scale = nl->scale;
     }
     const int tiles = (g.lines_a + tma_lines(prec, shape) - 1) / tma_lines(prec, shape);
-    const bool norm = norm_out != nullptr, has_nl = nl != nullptr;
+    const bool norm = norm_out != nullptr, has_nl = nl != nullptr && !nl_at_output;
+    const bool nlout = nl != nullptr && nl_at_output;
     const int lb = g.lines_b;
 #define GP_SHAPE(T, SH, I)                                                                   \
     if (shape == I)                                                                          \
-        return launch_shape<T, SH[I].K, SH[I].C, SH[I].S>(mode, axis, has_nl, norm, map, args, \
-                                                          tiles, lb, st)
+        return launch_shape<T, SH[I].K, SH[I].C, SH[I].S>(mode, axis, has_nl, norm, nlout, map, \
+                                                          args, tiles, lb, st)
     if (prec == kC128) {
         GP_SHAPE(double, kShapes64, 1);
         GP_SHAPE(double, kShapes64, 2);

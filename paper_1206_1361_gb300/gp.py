@@ -20,8 +20,9 @@ GP_C128, GP_C64 = 0, 1
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ENONFINITE, GP_ETIMEOUT, GP_EINTERNAL, GP_EFULL = (
     0, -1, -2, -3, -4, -5, -6, -7)
 GP_MAX_EDGE = 8192
-GP_OPT_SWEEP_PATH, GP_OPT_TILE_SHAPE = 1, 2
+GP_OPT_SWEEP_PATH, GP_OPT_TILE_SHAPE, GP_OPT_SPLITTING = 1, 2, 3
 GP_PATH_AUTO, GP_PATH_EXACT, GP_PATH_TMA = 0, 1, 2
+GP_SPLIT_LIE, GP_SPLIT_STRANG = 0, 1
 
 ERROR_NAMES = {GP_EINVAL: "GP_EINVAL", GP_ENOMEM: "GP_ENOMEM", GP_ECUDA: "GP_ECUDA",
                GP_ENONFINITE: "GP_ENONFINITE", GP_ETIMEOUT: "GP_ETIMEOUT",
@@ -62,6 +63,7 @@ SIGNATURES = {
     "gp_observables": (_int, [_vp, ctypes.POINTER(gp_obs)]),
     "gp_sync": (_int, [_vp]),
     "gp_set_option": (_int, [_vp, _int, _int]),
+    "gp_set_modulation": (_int, [_vp, _dbl, _dbl]),
     "gp_sweep_paths": (_int, [_vp, ctypes.POINTER(_int)]),
     "gp_get_option": (_int, [_vp, _int, ctypes.POINTER(_int)]),
     "gp_autotune": (_int, [_vp, _int, ctypes.POINTER(_int), ctypes.POINTER(_int),
@@ -213,6 +215,11 @@ def gp_launches_per_step(ctx):
     return k.value, o.value
 
 
+def gp_set_modulation(ctx, g1, omega):
+    """g(t) = g + g1 cos(omega t) from the next step on (g1 = 0: off)."""
+    _err(ctx, load_library().gp_set_modulation(ctx, float(g1), float(omega)))
+
+
 def gp_set_option(ctx, option, value):
     _err(ctx, load_library().gp_set_option(ctx, int(option), int(value)))
 
@@ -335,6 +342,14 @@ class Solver:
 
     def set_path(self, path):
         gp_set_option(self.ctx, GP_OPT_SWEEP_PATH, path)
+        return self
+
+    def set_splitting(self, split):
+        gp_set_option(self.ctx, GP_OPT_SPLITTING, split)
+        return self
+
+    def set_modulation(self, g1, omega):
+        gp_set_modulation(self.ctx, g1, omega)
         return self
 
     def paths(self):
