@@ -403,7 +403,8 @@ def run_ours(args):
         forms = None
         if world == 1 and not args.no_forms:
             forms = {"precision": precision_form(gp, torch, stream, args),
-                     "batched": batched_form(gp), "serving": serving_form(gp)}
+                     "batched": batched_form(gp), "serving": serving_form(gp),
+                     "splitting": splitting_form(gp, torch, stream)}
 
         extra = {"prep_imag_steps": prep, "prep_dmu": dmu,
                  "norm_drift": abs(obs_end["norm"] / obs0["norm"] - 1),
@@ -487,6 +488,48 @@ def precision_form(gp, torch, stream, args):
             "complex64": out["complex64"], "complex128": out["complex128"],
             "speedup_c64_over_fp64": out["complex64"]["value"] / out["complex128"]["value"],
             "rel_error_vs_fp64": err}
+
+
+def splitting_form(gp, torch, stream):
+    """The symmetric (Strang) splitting and a modulated g(t): its cost on the
+    benchmark workload (256^3 FP64 real time, ms per SSCN step against the
+    plain splitting), and what it buys: the error at T = 0.2 of a 64^3
+    real-time run with g(t) = 10 + 5 cos(20 t), plain and symmetric, at two
+    dt, against the symmetric run at dt / 16 (observed orders 1 and 2)."""
+    from paper_1206_1361_gb300.workloads import REAL_256 as case
+    out = {}
+    with gp.Solver(case.shape, case.h, case.dt, *case.trap, case.g, gp.GP_REAL, gp.GP_C128,
+                   stream) as s:
+        s.load(None)
+        for name, split in (("lie", gp.GP_SPLIT_LIE), ("strang", gp.GP_SPLIT_STRANG)):
+            s.set_splitting(split)
+            s.step(STEPS_PER_BENCH_STEP)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            s.step(10 * STEPS_PER_BENCH_STEP)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            out[name + "_ms_per_sscn_step"] = ev0.elapsed_time(ev1) / (10 * STEPS_PER_BENCH_STEP)
+    out["strang_cost_ratio"] = out["strang_ms_per_sscn_step"] / out["lie_ms_per_sscn_step"]
+    shape, h, T = (64, 64, 64), (0.2, 0.2, 0.2), 0.2
+
+    def run(dt, split):
+        with gp.Solver(shape, h, dt, 1.0, 1.5, 2.0, 10.0, gp.GP_REAL, gp.GP_C128, stream) as s:
+            s.set_splitting(split).set_modulation(5.0, 20.0)
+            s.load(None).step(int(round(T / dt)))
+            return torch.from_numpy(s.psi())
+
+    ref = run(0.004 / 16, gp.GP_SPLIT_STRANG)
+    err = {}
+    for name, split in (("lie", gp.GP_SPLIT_LIE), ("strang", gp.GP_SPLIT_STRANG)):
+        e = [float(torch.linalg.vector_norm(run(dt, split) - ref) / torch.linalg.vector_norm(ref))
+             for dt in (0.004, 0.002)]
+        err[name] = {"dt": [0.004, 0.002], "rel_l2": e, "observed_order": math.log2(e[0] / e[1])}
+    out["accuracy_64cubed_modulated_T0.2"] = err
+    out["workload"] = case.name + " (cost); 64^3 real time, g(t) = 10 + 5 cos(20 t) (accuracy)"
+    return out
 
 
 def batched_form(gp):

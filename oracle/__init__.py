@@ -17,7 +17,9 @@ from . import build as _build
 __all__ = ["Params", "lib", "coord", "seed", "step", "step_ext", "nonlinear",
            "nonlinear_part", "g_integral", "sweep",
            "norm", "observables", "energy_parts", "sums", "thomas_tables",
-           "thomas_solve", "set_threads", "get_threads"]
+           "thomas_solve", "set_threads", "get_threads", "AxialParams", "axial_seed",
+           "axial_step", "axial_sweep", "axial_nonlinear_part", "axial_norm",
+           "axial_observables", "axial_rho", "axial_weights", "tridiag_solve"]
 
 
 class Params(ctypes.Structure):
@@ -41,6 +43,22 @@ class Params(ctypes.Structure):
         return (self.nz, self.ny, self.nx)
 
 
+class AxialParams(ctypes.Structure):
+    """Mirror of ``ref_axial`` in sscn_ref.c (axially symmetric psi(rho, z))."""
+    _fields_ = [("nr", ctypes.c_int32), ("nz", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("hr", ctypes.c_double), ("hz", ctypes.c_double),
+                ("dt", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("g", ctypes.c_double)]
+
+    @classmethod
+    def make(cls, nr, nz, hr, hz, dt, gamma, lam, g, mode):
+        return cls(nr, nz, mode, 0, hr, hz, dt, gamma, lam, g)
+
+    @property
+    def shape2(self):
+        return (self.nz, self.nr)
+
+
 _lib = None
 
 
@@ -50,6 +68,7 @@ def lib():
         path = _build.build()
         L = ctypes.CDLL(path)
         P = ctypes.POINTER(Params)
+        A = ctypes.POINTER(AxialParams)
         vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
         sig = {
             "ref_set_threads": (None, [ctypes.c_int]),
@@ -69,6 +88,15 @@ def lib():
             "ref_sums": (None, [P, vp, vp]),
             "ref_energy_parts": (None, [P, vp, vp]),
             "ref_observables": (None, [P, vp, vp]),
+            "ref_axial_rho": (dbl, [dbl, i32]),
+            "ref_axial_weights": (None, [i32, vp, vp]),
+            "ref_tridiag_solve": (None, [i32, dbl, dbl, vp, vp, vp, vp, vp]),
+            "ref_axial_nonlinear_part": (None, [A, vp, dbl, dbl]),
+            "ref_axial_sweep": (None, [A, i32, vp]),
+            "ref_axial_norm": (dbl, [A, vp]),
+            "ref_axial_step_ext": (None, [A, vp, i64, i64, i32, dbl, dbl]),
+            "ref_axial_seed": (None, [A, vp]),
+            "ref_axial_observables": (None, [A, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -193,3 +221,73 @@ def thomas_solve(kappa, b):
     work = np.zeros(2 * m, np.complex128)
     lib().ref_thomas_solve(m, kappa.real, kappa.imag, _ptr(b), _ptr(u), _ptr(work))
     return u
+
+
+# ------------------------------------------------------- axially symmetric
+
+def _check_axial(p, psi):
+    if psi.dtype != np.complex128 or not psi.flags.c_contiguous:
+        raise TypeError("psi must be C-contiguous complex128")
+    if psi.shape != p.shape2:
+        raise ValueError("psi shape %s != (nz, nr) %s" % (psi.shape, p.shape2))
+
+
+def axial_rho(hr, i):
+    return lib().ref_axial_rho(float(hr), int(i))
+
+
+def axial_weights(n):
+    """(a, c): sub- and super-diagonal weights of the radial operator."""
+    a, c = np.zeros(n), np.zeros(n)
+    lib().ref_axial_weights(int(n), _ptr(a), _ptr(c))
+    return a, c
+
+
+def tridiag_solve(kappa, a, c, b):
+    """Solve (I - kappa tridiag(a, -2, c)) u = b, zero beyond both ends."""
+    a = np.ascontiguousarray(a, np.float64)
+    c = np.ascontiguousarray(c, np.float64)
+    b = np.ascontiguousarray(b, np.complex128)
+    m = b.shape[0]
+    u = np.zeros(m, np.complex128)
+    work = np.zeros(2 * m, np.complex128)
+    lib().ref_tridiag_solve(m, kappa.real, kappa.imag, _ptr(a), _ptr(c), _ptr(b), _ptr(u),
+                            _ptr(work))
+    return u
+
+
+def axial_seed(p):
+    psi = np.zeros(p.shape2, np.complex128)
+    lib().ref_axial_seed(ctypes.byref(p), _ptr(psi))
+    return psi
+
+
+def axial_step(p, psi, n, step0=0, strang=False, g1=0.0, omega=0.0):
+    _check_axial(p, psi)
+    lib().ref_axial_step_ext(ctypes.byref(p), _ptr(psi), int(n), int(step0), int(bool(strang)),
+                             float(g1), float(omega))
+    return psi
+
+
+def axial_sweep(p, axis, psi):
+    _check_axial(p, psi)
+    lib().ref_axial_sweep(ctypes.byref(p), int(axis), _ptr(psi))
+    return psi
+
+
+def axial_nonlinear_part(p, psi, frac, G):
+    _check_axial(p, psi)
+    lib().ref_axial_nonlinear_part(ctypes.byref(p), _ptr(psi), float(frac), float(G))
+    return psi
+
+
+def axial_norm(p, psi):
+    _check_axial(p, psi)
+    return lib().ref_axial_norm(ctypes.byref(p), _ptr(psi))
+
+
+def axial_observables(p, psi):
+    _check_axial(p, psi)
+    out = np.zeros(7)
+    lib().ref_axial_observables(ctypes.byref(p), _ptr(psi), _ptr(out))
+    return dict(zip(OBS_NAMES, out.tolist()))

@@ -77,6 +77,8 @@
 
 typedef double complex cplx;
 
+static const double kPi = 3.14159265358979323846;
+
 typedef struct {
     int32_t nx, ny, nz;      /* stored points per axis; nz == 1 is 2D        */
     int32_t mode;            /* 0 = imaginary time, 1 = real time            */
@@ -460,4 +462,235 @@ void ref_observables(const ref_params *p, const cplx *psi, double out[7])
     out[4] = sqrt(s[2] / s[0]);
     out[5] = sqrt(s[3] / s[0]);
     out[6] = sqrt((s[1] + s[2] + s[3]) / s[0]);
+}
+
+/* ======================================================= axially symmetric
+ *
+ * The axially symmetric programs (program summaries vii, viii, xvi, xvii):
+ * psi(rho, z) in a trap (gamma^2 rho^2 + lambda^2 z^2) / 2 with no angular
+ * momentum,
+ *     i dpsi/dt = [ -(1/2)(d^2/drho^2 + (1/rho) d/drho + d^2/dz^2) + V + g|psi|^2 ] psi.
+ * The paper prints no formula; this is the discretisation used:
+ *  grid    rho_i = (i + 1/2) h_r, i = 0 .. n_r - 1, all unknowns, with a zero
+ *          node at i = n_r; z as the Cartesian axes (zero node at k = 0 and
+ *          a virtual one at k = n_z).
+ *  radial  the conservative 3-point form
+ *            (L psi)_i = [rho_{i+1/2} (psi_{i+1} - psi_i) - rho_{i-1/2} (psi_i - psi_{i-1})] / (rho_i h_r^2),
+ *          rho_{i +- 1/2} = rho_i +- h_r / 2, so rho_{-1/2} = 0 (no flux through
+ *          the axis) and L = tridiag(a_i, -2, c_i) / h_r^2 with
+ *          a_i = 1 - 1/(2i+1), c_i = 1 + 1/(2i+1).  L is self-adjoint in
+ *          the inner product sum_i rho_i conj(phi_i) psi_i, so the
+ *          Crank-Nicolson sweep (I - kappa L) u = (I + kappa L) psi conserves
+ *          that norm in real time.
+ *  norm    N = 2 pi h_r h_z sum rho_i |psi_ik|^2.
+ *  E, mu   2 pi h_r h_z [ 1/2 sum rho_{i+1/2} |psi_{i+1,k} - psi_ik|^2 / h_r^2
+ *          + 1/2 sum rho_i |psi_{i,k+1} - psi_ik|^2 / h_z^2 + sum rho_i V |psi|^2
+ *          + (g/2 or g) sum rho_i |psi|^4 ] / N (summation by parts of L).
+ *  rms     <rho^2> and <z^2> with the weights rho_i; rms_x = rms_y =
+ *          sqrt(<rho^2> / 2), rms_r = sqrt(<rho^2> + <z^2>).
+ * Layout psi[k * n_r + i], rho fastest.
+ */
+typedef struct {
+    int32_t nr, nz;          /* radial points, axial points (>= 3)            */
+    int32_t mode;            /* 0 imaginary, 1 real time                      */
+    int32_t pad;
+    double hr, hz, dt;
+    double gamma, lambda;    /* radial and axial trap frequencies             */
+    double g;
+} ref_axial;
+
+double ref_axial_rho(double hr, int32_t i) { return ((double)i + 0.5) * hr; }
+
+static double axial_potential(const ref_axial *p, double r, double z)
+{
+    return 0.5 * (p->gamma * p->gamma * r * r + p->lambda * p->lambda * z * z);
+}
+
+/* Sub- and super-diagonal weights of the radial operator at point i. */
+void ref_axial_weights(int32_t n, double *a, double *c)
+{
+    for (int32_t i = 0; i < n; i++) {
+        double f = 1.0 / (2.0 * (double)i + 1.0);
+        a[i] = 1.0 - f;
+        c[i] = 1.0 + f;
+    }
+}
+
+/*
+ * Solve (I - kappa T) u = b with T = tridiag(a_i, -2, c_i), m unknowns and
+ * zero values beyond both ends, by forward elimination and back
+ * substitution: mult_i = 1 / (1 + 2 kappa + kappa a_i c'_{i-1}),
+ * c'_i = -kappa c_i mult_i, d'_i = (b_i + kappa a_i d'_{i-1}) mult_i,
+ * u_i = d'_i - c'_i u_{i+1}.  u may alias b; work needs 2 m entries.
+ */
+void ref_tridiag_solve(int32_t m, double kre, double kim, const double *a, const double *c,
+                       const cplx *b, cplx *u, cplx *work)
+{
+    cplx kappa = kre + kim * I;
+    cplx *cp = work, *d = work + m;
+    cplx cprev = 0.0, dprev = 0.0;
+    for (int32_t i = 0; i < m; i++) {
+        cplx mult = 1.0 / (1.0 + 2.0 * kappa + kappa * a[i] * cprev);
+        cp[i] = -kappa * c[i] * mult;
+        d[i] = (b[i] + kappa * a[i] * dprev) * mult;
+        cprev = cp[i];
+        dprev = d[i];
+    }
+    cplx v = d[m - 1];
+    u[m - 1] = v;
+    for (int32_t i = m - 2; i >= 0; i--) {
+        v = d[i] - cp[i] * v;
+        u[i] = v;
+    }
+}
+
+void ref_axial_nonlinear_part(const ref_axial *p, cplx *psi, double frac, double G)
+{
+    const int32_t nr = p->nr, nz = p->nz;
+#pragma omp parallel for schedule(static)
+    for (int32_t k = 0; k < nz; k++) {
+        double z = ref_coord(nz, p->hz, k);
+        for (int32_t i = 0; i < nr; i++) {
+            double r = ref_axial_rho(p->hr, i);
+            size_t at = (size_t)k * nr + i;
+            cplx v = psi[at];
+            double a = creal(v) * creal(v) + cimag(v) * cimag(v);
+            double theta = frac * p->dt * axial_potential(p, r, z) + G * a;
+            cplx f = p->mode == 1 ? cexp(-theta * I) : exp(-theta) + 0.0 * I;
+            psi[at] = f * v;
+        }
+    }
+}
+
+/* Radial (axis 0) or axial (axis 1) Crank-Nicolson sweep. */
+void ref_axial_sweep(const ref_axial *p, int32_t axis, cplx *psi)
+{
+    const int32_t nr = p->nr, nz = p->nz;
+    const double h = axis == 0 ? p->hr : p->hz;
+    const double kap = p->dt / (4.0 * h * h);
+    const cplx kappa = p->mode == 1 ? kap * I : kap + 0.0 * I;
+    /* radial lines: all n_r points are unknowns; axial lines: 1 .. n_z - 1 */
+    const int32_t m = axis == 0 ? nr : nz - 1;
+    const int32_t lines = axis == 0 ? nz : nr;
+    double *a = malloc(sizeof(double) * m), *c = malloc(sizeof(double) * m);
+    if (axis == 0) {
+        ref_axial_weights(m, a, c);
+    } else {
+        for (int32_t i = 0; i < m; i++) a[i] = c[i] = 1.0;
+    }
+#pragma omp parallel
+    {
+        cplx *b = malloc(sizeof(cplx) * m), *work = malloc(sizeof(cplx) * 2 * m);
+#pragma omp for schedule(static)
+        for (int32_t l = 0; l < lines; l++) {
+            /* unknown j (0-based) sits at stored index j (radial) or j + 1 (axial) */
+            for (int32_t j = 0; j < m; j++) {
+                size_t at, at_l = 0, at_r = 0;
+                if (axis == 0) { at = (size_t)l * nr + j; at_l = at - 1; at_r = at + 1; }
+                else { at = (size_t)(j + 1) * nr + l; at_l = at - nr; at_r = at + nr; }
+                cplx left = j > 0 ? psi[at_l] : 0.0;
+                cplx right = j + 1 < m ? psi[at_r] : 0.0;
+                b[j] = (1.0 - 2.0 * kappa) * psi[at] + kappa * (a[j] * left + c[j] * right);
+            }
+            ref_tridiag_solve(m, creal(kappa), cimag(kappa), a, c, b, b, work);
+            for (int32_t j = 0; j < m; j++) {
+                size_t at = axis == 0 ? (size_t)l * nr + j : (size_t)(j + 1) * nr + l;
+                psi[at] = b[j];
+            }
+        }
+        free(b);
+        free(work);
+    }
+    free(a);
+    free(c);
+}
+
+double ref_axial_norm(const ref_axial *p, const cplx *psi)
+{
+    double s = 0.0;
+    for (int32_t k = 0; k < p->nz; k++)
+        for (int32_t i = 0; i < p->nr; i++) {
+            cplx v = psi[(size_t)k * p->nr + i];
+            s += ref_axial_rho(p->hr, i) * (creal(v) * creal(v) + cimag(v) * cimag(v));
+        }
+    return 2.0 * kPi * p->hr * p->hz * s;
+}
+
+static void axial_scale(const ref_axial *p, cplx *psi, double f)
+{
+    size_t total = (size_t)p->nr * p->nz;
+    for (size_t at = 0; at < total; at++) psi[at] *= f;
+}
+
+/* n steps from step index step0, g(t) = g + g1 cos(omega t), plain or
+ * symmetric splitting, exactly as ref_step_ext does on the Cartesian grid:
+ * the radial sweep takes the place of x, the axial sweep that of y. */
+void ref_axial_step_ext(const ref_axial *p, cplx *psi, int64_t nsteps, int64_t step0,
+                        int32_t strang, double g1, double omega)
+{
+    for (int64_t s = 0; s < nsteps; s++) {
+        double t0 = (double)(step0 + s) * p->dt;
+        if (strang) {
+            double th = t0 + 0.5 * p->dt, t1 = t0 + p->dt;
+            ref_axial_nonlinear_part(p, psi, 0.5, ref_g_integral(p->g, g1, omega, t0, th));
+            ref_axial_sweep(p, 0, psi);
+            ref_axial_sweep(p, 1, psi);
+            if (p->mode == 0) axial_scale(p, psi, 1.0 / sqrt(ref_axial_norm(p, psi)));
+            ref_axial_nonlinear_part(p, psi, 0.5, ref_g_integral(p->g, g1, omega, th, t1));
+        } else {
+            ref_axial_nonlinear_part(p, psi, 1.0, ref_g_integral(p->g, g1, omega, t0, t0 + p->dt));
+            ref_axial_sweep(p, 0, psi);
+            ref_axial_sweep(p, 1, psi);
+        }
+        if (p->mode == 0) axial_scale(p, psi, 1.0 / sqrt(ref_axial_norm(p, psi)));
+    }
+}
+
+/* exp(-(gamma rho^2 + lambda z^2) / 2), zero at the axial boundary node, N = 1. */
+void ref_axial_seed(const ref_axial *p, cplx *psi)
+{
+    for (int32_t k = 0; k < p->nz; k++) {
+        double z = ref_coord(p->nz, p->hz, k);
+        for (int32_t i = 0; i < p->nr; i++) {
+            double r = ref_axial_rho(p->hr, i);
+            psi[(size_t)k * p->nr + i] =
+                k == 0 ? 0.0 : exp(-0.5 * (p->gamma * r * r + p->lambda * z * z)) + 0.0 * I;
+        }
+    }
+    axial_scale(p, psi, 1.0 / sqrt(ref_axial_norm(p, psi)));
+}
+
+/* out: N, mu, E, rms_x, rms_y, rms_z, rms_r (see the header of this part). */
+void ref_axial_observables(const ref_axial *p, const cplx *psi, double out[7])
+{
+    const int32_t nr = p->nr, nz = p->nz;
+    double s0 = 0, sr2 = 0, sz2 = 0, sv = 0, s4 = 0, kr = 0, kz = 0;
+    for (int32_t k = 0; k < nz; k++) {
+        double z = ref_coord(nz, p->hz, k);
+        for (int32_t i = 0; i < nr; i++) {
+            double r = ref_axial_rho(p->hr, i);
+            size_t at = (size_t)k * nr + i;
+            cplx v = psi[at];
+            double a = creal(v) * creal(v) + cimag(v) * cimag(v);
+            s0 += r * a;
+            sr2 += r * r * r * a;
+            sz2 += r * z * z * a;
+            sv += r * axial_potential(p, r, z) * a;
+            s4 += r * a * a;
+            cplx nxt = i + 1 < nr ? psi[at + 1] : 0.0;
+            kr += (r + 0.5 * p->hr) * creal((nxt - v) * conj(nxt - v));
+            nxt = k + 1 < nz ? psi[at + nr] : 0.0;
+            kz += r * creal((nxt - v) * conj(nxt - v));
+        }
+    }
+    double w = 2.0 * kPi * p->hr * p->hz;
+    double n = w * s0;
+    double kin = 0.5 * (kr / (p->hr * p->hr) + kz / (p->hz * p->hz));
+    out[0] = n;
+    out[1] = w * (kin + sv + p->g * s4) / n;
+    out[2] = w * (kin + sv + 0.5 * p->g * s4) / n;
+    out[3] = sqrt(0.5 * sr2 / s0);
+    out[4] = out[3];
+    out[5] = sqrt(sz2 / s0);
+    out[6] = sqrt((sr2 + sz2) / s0);
 }
