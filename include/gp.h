@@ -256,6 +256,30 @@ int gp_tile_shapes(int precision, int *count);
  * GP_PATH_TMA) into path[0..2] (path[2] = 0 in 2D). */
 int gp_sweep_paths(gp_ctx *ctx, int path[3]);
 
+/*
+ * Axially symmetric form (the paper's program summaries vii, viii, xvi,
+ * xvii): psi(rho, z) in the trap (gamma^2 rho^2 + lambda^2 z^2) / 2, no
+ * angular momentum,
+ *     i dpsi/dt = [ -(1/2)(d2/drho2 + (1/rho) d/drho + d2/dz2) + V + g|psi|^2 ] psi.
+ * Radial points rho_i = (i + 1/2) h_r, i = 0 .. n_r - 1 (all unknowns; zero
+ * beyond the last one, no flux through the axis) with the conservative
+ * 3-point radial operator, which keeps the norm 2 pi h_r h_z sum rho |psi|^2
+ * in real time; axial points as a Cartesian axis (zero node at k = 0).
+ * psi is FP64 (GP_C128 only), laid out psi[k * n_r + i], rho fastest.  The
+ * context then takes every single-grid call: gp_load / gp_store (n_r n_z
+ * values), gp_step, gp_observables (norm, mu, E; rms_x = rms_y =
+ * sqrt(<rho^2> / 2), rms_z, rms_r = sqrt(<rho^2> + <z^2>)), gp_set_params,
+ * GP_OPT_SPLITTING, gp_set_modulation.  The radial sweep runs the exact
+ * two-ended elimination (GP_OPT_SWEEP_PATH has no TMA path here).
+ * GP_EINVAL for n_r or n_z outside 3 .. 8192, h <= 0, dt <= 0, negative
+ * frequencies, non-finite g or precision != GP_C128.
+ */
+int gp_create_axial(int nr, int nz, double hr, double hz, double dt, double gamma, double lambda,
+                    double g, int mode, int precision, void *cuda_stream, gp_ctx **out);
+
+/* Bytes of device memory gp_create_axial allocates. */
+int gp_footprint_axial(int nr, int nz, int precision, size_t *bytes);
+
 /* Bytes of device memory gp_create allocates for this grid and precision. */
 int gp_footprint(const gp_grid *grid, int precision, size_t *bytes);
 

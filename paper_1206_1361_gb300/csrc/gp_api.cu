@@ -38,6 +38,11 @@ struct gp_ctx {
     int split = GP_SPLIT_LIE;
     double g1 = 0, omega = 0;       // g(t) = g + g1 cos(omega t)
     long long *step_dev = nullptr;  // device step counter (modulated g)
+    // axially symmetric psi(rho, z): grid {n_r, n_z, 1}, axis 0 = rho
+    bool axial = false;
+    gp::RadialTables rt[2];         // [mode] radial sweep tables (device)
+    void *rt_mem[2]{};
+    double *rho_w = nullptr;        // rho_i, the norm weights
     double *partials = nullptr;     // norm partials, >= max sweep blocks
     int partial_cap = 0;
     double *obs_partials = nullptr; // observables scratch (rows + finish stage)
@@ -115,7 +120,19 @@ SweepGeom geom(const gp_grid &gr, int axis)
     return g;
 }
 
-double cell_volume(const gp_ctx *c) { return c->h[0] * c->h[1] * (c->grid.nz > 1 ? c->h[2] : 1.0); }
+double cell_volume(const gp_ctx *c)
+{
+    if (c->axial) return 2.0 * 3.14159265358979323846 * c->h[0] * c->h[1];
+    return c->h[0] * c->h[1] * (c->grid.nz > 1 ? c->h[2] : 1.0);
+}
+
+// Coordinate of stored point i on axis k: the Cartesian grid, or on the axial
+// grid's radial axis rho_i = (i + 1/2) h.
+double axis_coord(const gp_ctx *c, int k, int i)
+{
+    if (c->axial && k == 0) return (i + 0.5) * c->h[0];
+    return coord(edge(c->grid, k), c->h[k], i);
+}
 
 // Forward-elimination tables of (I - kappa L), m unknowns:
 // denom_i = 1 + 2 kappa + kappa c'_{i-1} (c'_0 = 0), mult_i = 1/denom_i,
@@ -161,7 +178,7 @@ int upload_tables(gp_ctx *c)
         std::vector<double> x2, v;
         for (int k = 0; k < 3; ++k)
             for (int i = 0; i < edge(c->grid, k); ++i) {
-                const double x = coord(edge(c->grid, k), c->h[k], i);
+                const double x = axis_coord(c, k, i);
                 x2.push_back(x * x);
                 v.push_back(0.5 * c->w[k] * c->w[k] * x * x);
             }
@@ -176,7 +193,7 @@ int upload_tables(gp_ctx *c)
             std::vector<double2> t(n);
             std::vector<float4> t32(n);
             for (int i = 0; i < n; ++i) {
-                const double x = coord(n, c->h[k], i);
+                const double x = axis_coord(c, k, i);
                 const double th = c->dt * 0.5 * c->w[k] * c->w[k] * x * x;
                 t[i] = mode == 0 ? make_double2(std::exp(-th), 0.0)
                                  : make_double2(std::cos(th), -std::sin(th));
@@ -185,7 +202,7 @@ int upload_tables(gp_ctx *c)
             GP_CK(c, cudaMemcpy(c->ph[mode][k], t.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
             GP_CK(c, cudaMemcpy(c->ph32[mode][k], t32.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
             for (int i = 0; i < n; ++i) {
-                const double x = coord(n, c->h[k], i);
+                const double x = axis_coord(c, k, i);
                 const double th = 0.5 * (c->dt * 0.5 * c->w[k] * c->w[k] * x * x);
                 t[i] = mode == 0 ? make_double2(std::exp(-th), 0.0)
                                  : make_double2(std::cos(th), -std::sin(th));
@@ -199,12 +216,37 @@ int upload_tables(gp_ctx *c)
         const int n = edge(c->grid, k);
         std::vector<float> th(n), thh(n);
         for (int i = 0; i < n; ++i) {
-            const double x = coord(n, c->h[k], i);
+            const double x = axis_coord(c, k, i);
             th[i] = (float)(c->dt * 0.5 * c->w[k] * c->w[k] * x * x);
             thh[i] = 0.5f * th[i];
         }
         GP_CK(c, cudaMemcpy(c->th32[k], th.data(), n * sizeof(float), cudaMemcpyHostToDevice));
         GP_CK(c, cudaMemcpy(c->thh32[k], thh.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (c->axial) {
+        const int m = c->grid.nx;
+        const double kap = c->dt / (4.0 * c->h[0] * c->h[0]);
+        for (int mode = 0; mode < 2; ++mode) {
+            std::vector<double2> t4(4 * (size_t)m);
+            std::vector<double> t2(2 * (size_t)m);
+            gp::RadialTables &r = c->rt[mode];
+            gp::radial_tables(m, mode == 0 ? kap : 0.0, mode == 0 ? 0.0 : kap, t4.data(),
+                              t4.data() + m, t4.data() + 2 * m, t4.data() + 3 * m, t2.data(),
+                              t2.data() + m, &r.mid, &r.ka_mid, &r.kc_mid);
+            double2 *d4 = (double2 *)c->rt_mem[mode];
+            double *d2 = (double *)(d4 + 4 * (size_t)m);
+            GP_CK(c, cudaMemcpy(d4, t4.data(), t4.size() * sizeof(double2), cudaMemcpyHostToDevice));
+            GP_CK(c, cudaMemcpy(d2, t2.data(), t2.size() * sizeof(double), cudaMemcpyHostToDevice));
+            r.cp_top = d4;
+            r.mult_top = d4 + m;
+            r.cp_bot = d4 + 2 * m;
+            r.mult_bot = d4 + 3 * m;
+            r.ka_top = d2;
+            r.kc_bot = d2 + m;
+        }
+        std::vector<double> rho(m);
+        for (int i = 0; i < m; ++i) rho[i] = axis_coord(c, 0, i);
+        GP_CK(c, cudaMemcpy(c->rho_w, rho.data(), m * sizeof(double), cudaMemcpyHostToDevice));
     }
     return GP_OK;
 }
@@ -213,6 +255,13 @@ int upload_tables(gp_ctx *c)
 // window truncation bound max|c'|^(C+1) is below the precision's rounding.
 void setup_tma(gp_ctx *c)
 {
+    if (c->axial) {
+        for (int k = 0; k < 3; ++k) {
+            c->map_ok[k] = false;
+            c->tma_ok[0][k] = c->tma_ok[1][k] = false;
+        }
+        return;
+    }
     const int C = gp::tma_chunk(c->prec, c->tile_shape);
     for (int k = 0; k < naxes(c->grid); ++k) {
         c->map_ok[k] = gp::make_sweep_map(c->prec, c->tile_shape, c->psi, c->grid.nx, c->grid.ny,
@@ -272,6 +321,9 @@ void release(gp_ctx *c)
         }
     for (int k = 0; k < 3; ++k) { fr(c->th32[k]); fr(c->thh32[k]); }
     fr(c->step_dev);
+    fr(c->rt_mem[0]);
+    fr(c->rt_mem[1]);
+    fr(c->rho_w);
     fr(c->partials);
     fr(c->obs_partials);
     fr(c->obs_tab);
@@ -299,6 +351,12 @@ int sweep_path(const gp_ctx *c, int axis)
 cudaError_t launch_sweep(gp_ctx *c, int axis, const gp::NonlinArgs *nl, bool nl_at_output,
                          const Partials *norm, int *blocks)
 {
+    if (c->axial && axis == 0) {
+        if (!nl || nl_at_output || norm) return cudaErrorInvalidValue;
+        if (blocks) *blocks = gp::sweep_rho_blocks(c->grid.ny);
+        return gp::launch_sweep_rho(c->mode, c->psi, c->work, c->rt[c->mode], c->grid.nx,
+                                    c->grid.ny, *nl, c->stream);
+    }
     const SweepGeom g = geom(c->grid, axis);
     const gp::AxisTables &ax = c->ax[c->mode][axis];
     if (sweep_path(c, axis) == GP_PATH_TMA) {
@@ -367,7 +425,7 @@ int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
     const bool strang = c->split == GP_SPLIT_STRANG;
     const bool imag = mode == GP_IMAG;
     const int last = three_d ? 2 : 1;
-    Partials part{c->partials, 1};
+    Partials part{c->partials, 1, c->axial ? c->rho_w : nullptr};
     const gp::NonlinArgs nl = pointwise_args(c, 0, strang, 0.0, strang ? 0.5 : 1.0, c->scale);
     const gp::NonlinArgs nl2 =
         pointwise_args(c, imag ? 0 : last, true, 0.5, 1.0, imag ? c->scale : nullptr);
@@ -389,7 +447,8 @@ int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
                                         c->norm_dev, c->err_dev, c->stream));
         if (strang) {
             GP_CK(c, gp::launch_calcnu_pass(c->prec, mode, c->psi, c->grid.nx, c->grid.ny,
-                                            c->grid.nz, nl2, part, gp::kReduceBlocks, c->stream));
+                                            c->grid.nz, nl2, part, gp::kReduceBlocks, c->stream,
+                                            c->axial ? c->rho_w : nullptr));
             GP_CK(c, gp::launch_norm_finish(c->partials, gp::kReduceBlocks, cell_volume(c),
                                             c->scale, c->norm_dev, c->err_dev, c->stream));
         }
@@ -471,8 +530,12 @@ gp::ObsArgs obs_args(const gp_ctx *c)
 // Observables pass and finish, then the 9 sums to pinned host memory.
 int enqueue_observables(gp_ctx *c)
 {
-    GP_CK(c, gp::launch_observables(c->prec, c->psi, obs_args(c), c->obs_partials, c->sums,
-                                    c->stream));
+    if (c->axial)
+        GP_CK(c, gp::launch_observables_axial(c->psi, obs_args(c), c->h[0], c->obs_partials,
+                                              c->sums, c->stream));
+    else
+        GP_CK(c, gp::launch_observables(c->prec, c->psi, obs_args(c), c->obs_partials, c->sums,
+                                        c->stream));
     GP_CK(c, cudaMemcpyAsync(c->host_sums, c->sums, gp::kObsWidth * sizeof(double),
                              cudaMemcpyDeviceToHost, c->stream));
     return GP_OK;
@@ -588,6 +651,12 @@ int gp_footprint(const gp_grid *grid, int precision, size_t *bytes)
     return GP_OK;
 }
 
+namespace {
+int create_ctx(const gp_grid *grid, const double dx[3], double dt, double gamma, double nu,
+               double lambda, double g, int mode, int precision, void *cuda_stream, bool axial,
+               gp_ctx **out);
+}
+
 int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, double nu,
               double lambda, double g, int mode, int precision, void *cuda_stream,
               gp_ctx **out)
@@ -598,6 +667,40 @@ int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, 
     const int nd = grid->nz > 1 ? 3 : 2;
     for (int k = 0; k < nd; ++k)
         if (!(dx[k] > 0) || !std::isfinite(dx[k])) return fail(nullptr, GP_EINVAL, "gp_create: dx must be > 0");
+    return create_ctx(grid, dx, dt, gamma, nu, lambda, g, mode, precision, cuda_stream, false, out);
+}
+
+int gp_create_axial(int nr, int nz, double hr, double hz, double dt, double gamma, double lambda,
+                    double g, int mode, int precision, void *cuda_stream, gp_ctx **out)
+{
+    if (out) *out = nullptr;
+    const gp_grid grid{nr, nz, 1};
+    if (!out || !valid_grid(&grid))
+        return fail(nullptr, GP_EINVAL, "gp_create_axial: need 3 <= n_r, n_z <= 8192");
+    if (!(hr > 0) || !(hz > 0) || !std::isfinite(hr + hz))
+        return fail(nullptr, GP_EINVAL, "gp_create_axial: h_r, h_z must be > 0");
+    if (precision != GP_C128)
+        return fail(nullptr, GP_EINVAL, "gp_create_axial: the axially symmetric form is FP64 (GP_C128)");
+    const double dx[3] = {hr, hz, 1.0};
+    return create_ctx(&grid, dx, dt, gamma, lambda, 0.0, g, mode, precision, cuda_stream, true, out);
+}
+
+int gp_footprint_axial(int nr, int nz, int precision, size_t *bytes)
+{
+    const gp_grid grid{nr, nz, 1};
+    if (!valid_grid(&grid) || precision != GP_C128 || !bytes)
+        return fail(nullptr, GP_EINVAL, "gp_footprint_axial: invalid grid or precision");
+    *bytes = footprint_bytes(grid, precision) + 2 * (size_t)nr * (4 * sizeof(double2) + 2 * sizeof(double)) +
+             (size_t)nr * sizeof(double);
+    return GP_OK;
+}
+
+namespace {
+int create_ctx(const gp_grid *grid, const double dx[3], double dt, double gamma, double nu,
+               double lambda, double g, int mode, int precision, void *cuda_stream, bool axial,
+               gp_ctx **out)
+{
+    const int nd = grid->nz > 1 ? 3 : 2;
     if (!(dt > 0) || !std::isfinite(dt)) return fail(nullptr, GP_EINVAL, "gp_create: dt must be > 0");
     if (!(gamma >= 0) || !(nu >= 0) || !(lambda >= 0) || !std::isfinite(gamma + nu + lambda) ||
         !std::isfinite(g))
@@ -619,6 +722,7 @@ int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, 
     c->g = g;
     c->mode = mode;
     c->prec = precision;
+    c->axial = axial;
 
     auto bail = [&](int rc) {
         g_create_error = c->last_error;
@@ -659,6 +763,13 @@ int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, 
         if ((rc = alloc(c, (void **)&c->thh32[k], edge(c->grid, k) * sizeof(float)))) return bail(rc);
     }
     if ((rc = alloc(c, (void **)&c->step_dev, sizeof(long long)))) return bail(rc);
+    if (axial) {
+        const size_t m = grid->nx;
+        for (int mode_i = 0; mode_i < 2; ++mode_i)
+            if ((rc = alloc(c, &c->rt_mem[mode_i], m * (4 * sizeof(double2) + 2 * sizeof(double)))))
+                return bail(rc);
+        if ((rc = alloc(c, (void **)&c->rho_w, m * sizeof(double)))) return bail(rc);
+    }
     int blocks = gp::kReduceBlocks;
     for (int k = 0; k < naxes(c->grid); ++k)
         for (int sh = 0; sh < gp::tma_shapes(precision); ++sh)
@@ -701,6 +812,7 @@ int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, 
     *out = c;
     return GP_OK;
 }
+}  // namespace
 
 int gp_load(gp_ctx *c, const void *psi, int64_t count, int on_device)
 {
@@ -710,10 +822,18 @@ int gp_load(gp_ctx *c, const void *psi, int64_t count, int on_device)
     c->step = 0;
     GP_CK(c, gp::launch_set_step(c->step_dev, 0, c->stream));
     if (psi == nullptr) {
-        GP_CK(c, gp::launch_seed(c->prec, c->psi, c->grid.nx, c->grid.ny, c->grid.nz, c->h,
-                                 c->w, c->stream));
         Partials part{c->partials, 1};
-        GP_CK(c, gp::launch_norm_partials(c->prec, c->psi, n, part, gp::kReduceBlocks, c->stream));
+        if (c->axial) {
+            GP_CK(c, gp::launch_seed_axial(c->psi, c->grid.nx, c->grid.ny, c->h[0], c->h[1],
+                                           c->w[0], c->w[1], c->stream));
+            GP_CK(c, gp::launch_norm_partials_axial(c->psi, c->grid.nx, c->grid.ny, c->h[0], part,
+                                                    gp::kReduceBlocks, c->stream));
+        } else {
+            GP_CK(c, gp::launch_seed(c->prec, c->psi, c->grid.nx, c->grid.ny, c->grid.nz, c->h,
+                                     c->w, c->stream));
+            GP_CK(c, gp::launch_norm_partials(c->prec, c->psi, n, part, gp::kReduceBlocks,
+                                              c->stream));
+        }
         GP_CK(c, gp::launch_norm_finish(c->partials, gp::kReduceBlocks, cell_volume(c), c->scale,
                                         c->norm_dev, c->err_dev, c->stream));
         c->scale_pending = true;
@@ -723,7 +843,8 @@ int gp_load(gp_ctx *c, const void *psi, int64_t count, int on_device)
     GP_CK(c, cudaMemcpyAsync(c->psi, psi, (size_t)n * elem_bytes(c->prec),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              c->stream));
-    GP_CK(c, gp::launch_zero_boundary(c->prec, c->psi, c->grid.nx, c->grid.ny, c->grid.nz, c->stream));
+    if (c->axial) GP_CK(c, gp::launch_zero_axial(c->psi, c->grid.nx, c->stream));
+    else GP_CK(c, gp::launch_zero_boundary(c->prec, c->psi, c->grid.nx, c->grid.ny, c->grid.nz, c->stream));
     const double one = 1.0;
     GP_CK(c, cudaMemcpyAsync(c->scale, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     GP_CK(c, cudaStreamSynchronize(c->stream));   // `one` and the caller's buffer
@@ -806,10 +927,18 @@ int gp_observables(gp_ctx *c, gp_obs *o)
     o->norm = n;
     o->mu = w * (kin + s[4] + g_now * s[5]) / n;
     o->energy = w * (kin + s[4] + 0.5 * g_now * s[5]) / n;
-    o->rms_x = std::sqrt(s[1] / s[0]);
-    o->rms_y = std::sqrt(s[2] / s[0]);
-    o->rms_z = std::sqrt(s[3] / s[0]);
-    o->rms_r = std::sqrt((s[1] + s[2] + s[3]) / s[0]);
+    if (c->axial) {
+        // s[1] = sum rho^2 (weighted), s[3] = sum z^2: <x^2> = <y^2> = <rho^2> / 2
+        o->rms_x = std::sqrt(0.5 * s[1] / s[0]);
+        o->rms_y = o->rms_x;
+        o->rms_z = std::sqrt(s[3] / s[0]);
+        o->rms_r = std::sqrt((s[1] + s[3]) / s[0]);
+    } else {
+        o->rms_x = std::sqrt(s[1] / s[0]);
+        o->rms_y = std::sqrt(s[2] / s[0]);
+        o->rms_z = std::sqrt(s[3] / s[0]);
+        o->rms_r = std::sqrt((s[1] + s[2] + s[3]) / s[0]);
+    }
     o->step = c->step;
     o->t = c->step * c->dt;
     if (rc) return rc;

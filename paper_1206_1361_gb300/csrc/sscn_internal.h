@@ -99,6 +99,8 @@ struct NonlinArgs {
 struct Partials {
     double *buf = nullptr;   // device, >= blocks * width doubles
     int width = 1;
+    // sweeps: weight of line a's |u|^2 (the rho_i of an axial line); nullptr: 1
+    const double *line_weight = nullptr;
 };
 
 enum Precision { kC128 = 0, kC64 = 1 };
@@ -122,9 +124,10 @@ cudaError_t launch_sweep_yz(int prec, int mode, void *psi, void *work,
 // calcnu as its own pass over every point (x lines; tables in x, y, z order)
 // with the FP64 sums |psi|^2 into `blocks` partials: the imaginary-time
 // symmetric splitting's second half step, after the renormalisation.
+// wx (nullptr: 1) weights |u|^2 by the point's x index (rho_i on the axial grid).
 cudaError_t launch_calcnu_pass(int prec, int mode, void *psi, int nx, int ny, int nz,
                                const NonlinArgs &nl, const Partials &norm_out, int blocks,
-                               cudaStream_t st);
+                               cudaStream_t st, const double *wx = nullptr);
 // Device step counter (modulated g): set it, or add one.
 cudaError_t launch_set_step(long long *step, long long value, cudaStream_t st);
 cudaError_t launch_add_step(long long *step, cudaStream_t st);
@@ -161,6 +164,54 @@ struct ObsArgs {
 long long obs_scratch_doubles(const ObsArgs &a);
 cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
                                double *scratch, double *sums, cudaStream_t st);
+// Fixed-order finish of `lines` partials rows of kObsWidth doubles into sums
+// (two passes through `stage`, ceil(lines / 1024) rows).
+cudaError_t launch_rows_finish(const double *rows, long long lines, double *stage, double *sums,
+                               cudaStream_t st);
+
+// ---- axially symmetric psi(rho, z) (sscn_axial.cu), FP64 ---------------------
+// Radial grid rho_i = (i + 1/2) h_r, i = 0 .. n_r - 1 (all unknowns, a zero
+// node at i = n_r); the radial operator is tridiag(a_i, -2, c_i) / h_r^2 with
+// a_i = 1 - 1/(2i+1), c_i = 1 + 1/(2i+1).  The axial grid is a Cartesian
+// axis; psi[k * n_r + i].
+//
+// Two-ended elimination tables of (I - kappa tridiag(a, -2, c)), m = n_r
+// unknowns j = 1 .. m, 0-based entry t:
+//   top    (j = t + 1):  mult = 1 / (1 + 2 kappa + kappa a_j c'_{j-1}), c' = -kappa c_j mult,
+//                        ka = |kappa| a_j
+//   bottom (j = m - t):  mult = 1 / (1 + 2 kappa + kappa c_j e'_{j+1}), e' = -kappa a_j mult,
+//                        kc = |kappa| c_j
+//   middle row k = ceil(m / 2): 1 / (1 + 2 kappa + kappa (a_k c'_{k-1} + c_k e'_{k+1}))
+struct RadialTables {
+    const double2 *cp_top = nullptr, *mult_top = nullptr, *cp_bot = nullptr, *mult_bot = nullptr;
+    const double *ka_top = nullptr, *kc_bot = nullptr;
+    double2 mid{0, 0};
+    double ka_mid = 0, kc_mid = 0;
+};
+// Host computation of those tables for kappa = kre + i kim (kre or kim zero).
+void radial_tables(int m, double kre, double kim, double2 *cp_top, double2 *mult_top,
+                   double2 *cp_bot, double2 *mult_bot, double *ka_top, double *kc_bot,
+                   double2 *mid, double *ka_mid, double *kc_mid);
+// Radial sweep of every line k (nz lines of nr points) with calcnu fused on
+// the loads: nl.px = radial factor table, nl.py = axial factor table (indexed
+// by the line), nl.pz = a one-entry table (1, 0).
+cudaError_t launch_sweep_rho(int mode, void *psi, void *work, const RadialTables &rt, int nr,
+                             int nz, const NonlinArgs &nl, cudaStream_t st);
+int sweep_rho_blocks(int nz);
+// Gaussian seed exp(-(gamma rho^2 + lambda z^2) / 2), zero at k = 0.
+cudaError_t launch_seed_axial(void *psi, int nr, int nz, double hr, double hz, double gamma,
+                              double lambda, cudaStream_t st);
+// Zero the axial Dirichlet node row k = 0.
+cudaError_t launch_zero_axial(void *psi, int nr, cudaStream_t st);
+// FP64 sums of rho_i |psi|^2 into `blocks` partials.
+cudaError_t launch_norm_partials_axial(const void *psi, int nr, int nz, double hr,
+                                       const Partials &out, int blocks, cudaStream_t st);
+// Observables rows (one per line k): S0 = sum rho |psi|^2, sum rho^3 |psi|^2,
+// 0, z^2 S0, sum rho V |psi|^2, sum rho |psi|^4, sum rho_{i+1/2} |psi_{i+1} - psi_i|^2,
+// sum rho |psi_{k+1} - psi_k|^2, 0 (times the pending scale), then the finish.
+// a.x2 / a.vx: rho^2 and gamma^2 rho^2 / 2; a.y2 / a.vy: z^2 and lambda^2 z^2 / 2.
+cudaError_t launch_observables_axial(const void *psi, const ObsArgs &a, double hr,
+                                     double *scratch, double *sums, cudaStream_t st);
 
 // ---- TMA-pipelined sweeps (sscn_tma.cu) -------------------------------------
 // `shape` indexes a small table of tile shapes (lines per CTA, points per

@@ -123,7 +123,8 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
         T kappa, const typename Coef<T>::t *__restrict__ px,
         const typename Coef<T>::t *__restrict__ py, const typename Coef<T>::t *__restrict__ pz,
         const float *__restrict__ tx, const float *__restrict__ ty, const float *__restrict__ tz,
-        StepG sg, const double *__restrict__ scale, double *__restrict__ partials)
+        StepG sg, const double *__restrict__ scale, double *__restrict__ partials,
+        const double *__restrict__ lw)
 {
     using C = typename CT<T>::c;
     __shared__ double red[32];
@@ -207,7 +208,9 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
         }
     }
     if (NORM) {
-        const double r = block_sum(nacc.get(), red);
+        double part = nacc.get();
+        if (lw && active) part *= lw[a];
+        const double r = block_sum(part, red);
         if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = r;
     }
 }
@@ -240,7 +243,7 @@ cudaError_t sweep_launch(void *psi, void *work, const AxisTables &ax,
     k_sweep<T, MODE, NL, NORM, NLOUT><<<grid, kSweepThreads, 0, st>>>(
         reinterpret_cast<C *>(psi), reinterpret_cast<C *>(work), cp, mult, mid, g, kappa,
         px, py, pz, tx, ty, tz, nl ? nl->g : StepG{}, nl ? nl->scale : nullptr,
-        norm_out ? norm_out->buf : nullptr);
+        norm_out ? norm_out->buf : nullptr, norm_out ? norm_out->line_weight : nullptr);
     return cudaGetLastError();
 }
 
@@ -354,7 +357,8 @@ k_calcnu_pass(typename CT<T>::c *__restrict__ psi, int nx, int ny, int nz,
               const typename Coef<T>::t *__restrict__ px, const typename Coef<T>::t *__restrict__ py,
               const typename Coef<T>::t *__restrict__ pz, const float *__restrict__ tx,
               const float *__restrict__ ty, const float *__restrict__ tz, StepG sg,
-              const double *__restrict__ scale, double *__restrict__ partials)
+              const double *__restrict__ scale, double *__restrict__ partials,
+              const double *__restrict__ wx)
 {
     using C = typename CT<T>::c;
     __shared__ double red[32];
@@ -372,7 +376,7 @@ k_calcnu_pass(typename CT<T>::c *__restrict__ psi, int nx, int ny, int nz,
         for (int i = lane; i < nx; i += 32) {
             const C u = nl.apply(line[i], i);
             line[i] = u;
-            acc += abs2d<T>(u);
+            acc = fma(wx ? wx[i] : 1.0, abs2d<T>(u), acc);
         }
     }
     const double r = block_sum(acc, red);
@@ -566,16 +570,16 @@ cudaError_t launch_norm_partials(int prec, const void *psi, long long count,
 
 cudaError_t launch_calcnu_pass(int prec, int mode, void *psi, int nx, int ny, int nz,
                                const NonlinArgs &nl, const Partials &norm_out, int blocks,
-                               cudaStream_t st)
+                               cudaStream_t st, const double *wx)
 {
     if (prec == kC128) {
         auto k = mode == 0 ? k_calcnu_pass<double, 0> : k_calcnu_pass<double, 1>;
         k<<<blocks, 256, 0, st>>>((double2 *)psi, nx, ny, nz, nl.px, nl.py, nl.pz, nl.tx32, nl.ty32,
-                                  nl.tz32, nl.g, nl.scale, norm_out.buf);
+                                  nl.tz32, nl.g, nl.scale, norm_out.buf, wx);
     } else {
         auto k = mode == 0 ? k_calcnu_pass<float, 0> : k_calcnu_pass<float, 1>;
         k<<<blocks, 256, 0, st>>>((float2 *)psi, nx, ny, nz, nl.px32, nl.py32, nl.pz32, nl.tx32,
-                                  nl.ty32, nl.tz32, nl.g, nl.scale, norm_out.buf);
+                                  nl.ty32, nl.tz32, nl.g, nl.scale, norm_out.buf, wx);
     }
     return cudaGetLastError();
 }
@@ -612,8 +616,16 @@ cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
         k_observables<float><<<(unsigned)blocks, kObsThreads, 0, st>>>((const float2 *)psi, a, rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    return launch_rows_finish(rows, lines, stage, sums, st);
+}
+
+cudaError_t launch_rows_finish(const double *rows, long long lines, double *stage, double *sums,
+                               cudaStream_t st)
+{
+    const long long chunks = (lines + kObsChunk - 1) / kObsChunk;
     k_rows_sum<<<(unsigned)chunks, 256, 0, st>>>(rows, lines, kObsChunk, stage);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     k_rows_sum<<<1, 256, 0, st>>>(stage, chunks, (int)chunks, sums);
     return cudaGetLastError();
 }

@@ -64,6 +64,9 @@ SIGNATURES = {
     "gp_sync": (_int, [_vp]),
     "gp_set_option": (_int, [_vp, _int, _int]),
     "gp_set_modulation": (_int, [_vp, _dbl, _dbl]),
+    "gp_create_axial": (_int, [_int, _int, _dbl, _dbl, _dbl, _dbl, _dbl, _dbl, _int, _int, _vp,
+                               ctypes.POINTER(_vp)]),
+    "gp_footprint_axial": (_int, [_int, _int, _int, ctypes.POINTER(ctypes.c_size_t)]),
     "gp_sweep_paths": (_int, [_vp, ctypes.POINTER(_int)]),
     "gp_get_option": (_int, [_vp, _int, ctypes.POINTER(_int)]),
     "gp_autotune": (_int, [_vp, _int, ctypes.POINTER(_int), ctypes.POINTER(_int),
@@ -162,6 +165,28 @@ def gp_create(grid, dx, dt, gamma, nu, lam, g, mode=GP_IMAG, precision=GP_C128,
         msg = L.gp_last_error(None)
         raise GPError(rc, msg.decode() if msg else "")
     return out.value
+
+
+def gp_create_axial(nr, nz, hr, hz, dt, gamma, lam, g, mode=GP_IMAG, precision=GP_C128,
+                    cuda_stream=None):
+    """Axially symmetric psi(rho, z) on n_r radial x n_z axial points."""
+    L = load_library()
+    out = _vp()
+    rc = L.gp_create_axial(int(nr), int(nz), float(hr), float(hz), float(dt), float(gamma),
+                           float(lam), float(g), int(mode), int(precision),
+                           _stream_handle(cuda_stream), ctypes.byref(out))
+    if rc != GP_OK:
+        msg = L.gp_last_error(None)
+        raise GPError(rc, msg.decode() if msg else "")
+    return out.value
+
+
+def gp_footprint_axial(nr, nz, precision=GP_C128):
+    b = ctypes.c_size_t()
+    rc = load_library().gp_footprint_axial(int(nr), int(nz), int(precision), ctypes.byref(b))
+    if rc != GP_OK:
+        raise GPError(rc, load_library().gp_last_error(None).decode())
+    return b.value
 
 
 def gp_load(ctx, psi=None, count=None, on_device=None):
@@ -303,15 +328,26 @@ class Solver:
     """Owns one context.  ``shape`` is (nx, ny, nz); arrays are (nz, ny, nx)."""
 
     def __init__(self, shape, dx, dt, gamma, nu, lam, g, mode=GP_IMAG,
-                 precision=GP_C128, stream=None):
+                 precision=GP_C128, stream=None, _ctx=None):
         self.shape = tuple(int(v) for v in shape)
         self.precision = precision
-        self.ctx = gp_create(self.shape, dx, dt, gamma, nu, lam, g, mode, precision, stream)
+        self.ctx = _ctx if _ctx is not None else gp_create(self.shape, dx, dt, gamma, nu, lam, g,
+                                                           mode, precision, stream)
+
+    @classmethod
+    def axial(cls, nr, nz, hr, hz, dt, gamma, lam, g, mode=GP_IMAG, stream=None):
+        """Axially symmetric psi(rho, z); arrays are (nz, nr)."""
+        ctx = gp_create_axial(nr, nz, hr, hz, dt, gamma, lam, g, mode, GP_C128, stream)
+        s = cls((nr, nz, 1), None, dt, gamma, lam, 0.0, g, mode, GP_C128, stream, _ctx=ctx)
+        s.is_axial = True
+        return s
+
+    is_axial = False
 
     @property
     def array_shape(self):
         nx, ny, nz = self.shape
-        return (nz, ny, nx)
+        return (ny, nx) if self.is_axial else (nz, ny, nx)
 
     @property
     def dtype(self):
