@@ -404,7 +404,8 @@ def run_ours(args):
         if world == 1 and not args.no_forms:
             forms = {"precision": precision_form(gp, torch, stream, args),
                      "batched": batched_form(gp), "serving": serving_form(gp),
-                     "splitting": splitting_form(gp, torch, stream)}
+                     "splitting": splitting_form(gp, torch, stream),
+                     "axial": axial_form(gp, torch, stream)}
 
         extra = {"prep_imag_steps": prep, "prep_dmu": dmu,
                  "norm_drift": abs(obs_end["norm"] / obs0["norm"] - 1),
@@ -530,6 +531,46 @@ def splitting_form(gp, torch, stream):
     out["accuracy_64cubed_modulated_T0.2"] = err
     out["workload"] = case.name + " (cost); 64^3 real time, g(t) = 10 + 5 cos(20 t) (accuracy)"
     return out
+
+
+def axial_form(gp, torch, stream):
+    """The axially symmetric form psi(rho, z) on 1024 x 2048 points (h =
+    0.0125: rho < 12.8, |z| < 12.8), trap (1, 4), real time from the seed at
+    g = 100, FP64: grid-point-steps/s, the radial sweep against the FP64
+    pipe, and the oracle on the host cores on a bounded sample."""
+    import oracle
+    nr, nz, h, dt, g = 1024, 2048, 0.0125, 1e-4, 100.0
+    steps = 10 * STEPS_PER_BENCH_STEP
+    with gp.Solver.axial(nr, nz, h, h, dt, 1.0, 4.0, g, gp.GP_REAL, stream) as s:
+        s.load(None).step(STEPS_PER_BENCH_STEP)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        s.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        kt = gp.gp_time_kernels(s.ctx, 10)
+    points = nr * nz
+    rho_ms = kt["sweep_x"]
+    ach = FLOPS_PER_POINT[gp.GP_REAL]["sweep_x"] * points / (rho_ms * 1e-3) / 1e12
+    p = oracle.AxialParams.make(nr, nz, h, h, dt, 1.0, 4.0, g, 1)
+    psi = oracle.axial_seed(p)
+    t0 = time.perf_counter()
+    n_cpu = 0
+    while time.perf_counter() - t0 < 5.0:
+        oracle.axial_step(p, psi, 2)
+        n_cpu += 2
+    cpu = n_cpu * points / (time.perf_counter() - t0)
+    return {"workload": "axial %dx%d h=%g, trap (1, 4), g=%g, real time, FP64" % (nr, nz, h, g),
+            "value": points / (ms * 1e-3), "unit": UNIT, "ms_per_sscn_step": ms,
+            "kernel_ms": {"sweep_rho": round(kt["sweep_x"], 5), "sweep_z": round(kt["sweep_y"], 5)},
+            "roofline": {"bound": "alu", "kernel": "sweep_rho", "achieved": ach,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                         "note": "n_z = 2048 radial lines: 4096 threads, latency-bound"},
+            "cpu_baseline": {"value": cpu, "unit": UNIT, "cores": oracle.get_threads(),
+                             "kind": "oracle", "sample": "%d axial SSCN steps" % n_cpu}}
 
 
 def batched_form(gp):
