@@ -589,7 +589,9 @@ def batched_form(gp):
             "value": bs["point_steps_per_s"], "unit": UNIT, "wall_s": bs["wall_s"],
             "points_total": sum(i.points for i in insts),
             "max_steps": max(r.total_steps for r in b.results),
-            "sequential_c64": {"value": ss["point_steps_per_s"], "wall_s": ss["wall_s"]},
+            "converged": bs["converged"], "stalled": bs["stalled"],
+            "sequential_c64": {"value": ss["point_steps_per_s"], "wall_s": ss["wall_s"],
+                               "converged": ss["converged"], "stalled": ss["stalled"]},
             "speedup_vs_sequential": ss["wall_s"] / bs["wall_s"]}
 
 

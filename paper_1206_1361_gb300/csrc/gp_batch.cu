@@ -12,13 +12,15 @@
 // CTAs, so the waits always end; instances at different phases overlap and
 // no grid-wide barrier separates the sweeps.
 //
-// Tile solver: one warp, 32 lines staged in shared memory (coalesced loads:
-// rows for x tiles, one point of 32 neighbouring lines at a time for y / z),
-// each lane runs the exact Thomas elimination of its line in place
-// (right-hand side (1 - 2 kappa) psi_i + kappa (psi_{i-1} + psi_{i+1}),
-// forward elimination overwriting psi with d', back substitution overwriting
-// d' with u), and the tile is written back.  Lines are at most 512 points
-// (complex64) / 384 (complex128).  The per-instance decomposition depends only
+// Tile solver: one warp, 16 lines staged in shared memory (coalesced loads:
+// rows for x tiles, one point of 16 neighbouring lines at a time for y / z),
+// each line eliminated from both ends by a lane pair in place (the right-hand
+// side (1 - 2 kappa) psi_i + kappa (psi_{i-1} + psi_{i+1}) formed on the fly,
+// forward elimination overwriting psi with d', the pair meeting at the middle
+// row, back substitution overwriting d' with u), and the tile is written
+// back.  16-line tiles halve the shared memory a warp holds against 32-line
+// ones, which doubles the warps resident per SM.  Lines are at most 512
+// points (complex64) / 384 (complex128).  The per-instance decomposition depends only
 // on the instance's own shape and its norm is summed in a fixed order, so an
 // instance's result is bit-identical alone and in any mix.
 
@@ -51,7 +53,7 @@ template <typename T> __device__ __forceinline__ typename BC<T>::c mkb(T x, T y)
     return r;
 }
 
-constexpr int kTileLines = 32;
+constexpr int kTileLines = 16;
 constexpr int kObsWidthB = gp::kObsWidth;
 constexpr int kMaxEdge32 = 512, kMaxEdge64 = 384;
 constexpr uint64_t kWaitNs = 2000000000ull;
@@ -68,6 +70,8 @@ struct Inst {
     int conv[3];                    // index from which the table entries are constant
     double2 cinf64[3], minf64[3];   // those constants, FP64 batches
     float4 cinf32[3], minf32[3];    // and complex64 batches (hi + lo)
+    double2 mid64[3];               // middle-row multiplier of the two-ended elimination
+    float4 mid32[3];
     const void *ph[3];              // current-mode potential factors (Coef<T>), n entries
     const float *th[3];             // dt omega^2 x^2 / 2 (FP32) per axis
     const double *x2[3], *v[3];     // x^2, omega^2 x^2 / 2 per axis (observables)
@@ -139,53 +143,81 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
-// The exact line update of one lane, in place on row[0 .. n-1] (shared
-// memory): calcnu first for x tiles (NL), the norm contribution of the
-// result into acc when NORM.
+// The exact line update of a lane pair, in place on row[0 .. n-1] (shared
+// memory; point 0 and the virtual point n are zero).  The top lane eliminates
+// i = 1 .. k-1, the bottom lane i = m .. k+1 with the mirrored tables (the
+// matrix is symmetric Toeplitz), the top lane closes the middle row k =
+// ceil(m / 2), and both back-substitute outward.  calcnu first for x tiles
+// (nl), the norm contribution of the result into acc when norm.  Every lane
+// of the warp calls this (the shuffles need them all); `active` marks lanes
+// with a line.
 template <typename T, int MODE>
-__device__ void solve_line(const Inst &I, int axis, typename BC<T>::c *row, int n, long long line,
-                           bool nl, bool norm, Acc<T> &acc)
+__device__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int n, long long line,
+                            bool top, bool active, bool nl, bool norm, Acc<T> &acc)
 {
     using C = typename BC<T>::c;
     using F = typename Coef<T>::t;
     const int m = n - 1;
+    const int k = (m + 1) >> 1;
     const LineOps<T, MODE> cn{(T)I.kap[axis]};
     const F *cp = static_cast<const F *>(I.cp[axis]);
     const F *mult = static_cast<const F *>(I.mult[axis]);
     const int conv = I.conv[axis];
-    F cinf, minf;
+    F cinf, minf, mid;
     if constexpr (sizeof(T) == 8) {
         cinf = I.cinf64[axis];
         minf = I.minf64[axis];
+        mid = I.mid64[axis];
     } else {
         cinf = I.cinf32[axis];
         minf = I.minf32[axis];
+        mid = I.mid32[axis];
     }
     if (nl) {
-        // x line: j = line % ny, k = line / ny
-        const int j = (int)(line % I.n[1]), k = (int)(line / I.n[1]);
-        Calcnu<T, MODE> cu{};
-        cu.setup(static_cast<const F *>(I.ph[0]), static_cast<const F *>(I.ph[1]),
-                 static_cast<const F *>(I.ph[2]), I.th[0], I.th[1], I.th[2], j, k, I.dtg, I.scale);
-        for (int i = 1; i <= m; ++i) row[i] = cu.apply(row[i], i);
+        if (active) {
+            // x line: j = line % ny, k = line / ny
+            const int j = (int)(line % I.n[1]), kz = (int)(line / I.n[1]);
+            Calcnu<T, MODE> cu{};
+            cu.setup(static_cast<const F *>(I.ph[0]), static_cast<const F *>(I.ph[1]),
+                     static_cast<const F *>(I.ph[2]), I.th[0], I.th[1], I.th[2], j, kz, I.dtg,
+                     I.scale);
+            for (int i = top ? 1 : k + 1; i <= (top ? k : m); ++i) row[i] = cu.apply(row[i], i);
+        }
+        __syncwarp();
     }
     const C zero = mkb<T>((T)0, (T)0);
-    C left = zero, mid = row[1], d = zero;
-    for (int i = 1; i <= m; ++i) {
-        const C right = i < m ? row[i + 1] : zero;
-        const int t = i - 1;
-        d = cn.fwd(cn.rhs(left, mid, right), d, t < conv ? mult[t] : minf);
-        row[i] = d;
-        left = mid;
-        mid = right;
+    const int len = top ? k - 1 : m - k;
+    const int dir = top ? 1 : -1;
+    C prev = zero, cur = zero, d = zero;
+    if (active) {
+        cur = row[top ? 1 : m];
+        for (int t = 0; t < len; ++t) {
+            const int pos = top ? 1 + t : m - t;
+            const C next = row[pos + dir];
+            d = cn.fwd(cn.rhs(prev, cur, next), d, t < conv ? mult[t] : minf);
+            row[pos] = d;
+            prev = cur;
+            cur = next;
+        }
     }
-    C u = d;
-    if (norm) acc.add(fma(u.x, u.x, u.y * u.y));
-    for (int i = m - 1; i >= 1; --i) {
-        const int t = i - 1;
-        u = cn.back(row[i], t < conv ? cp[t] : cinf, u);
-        row[i] = u;
-        if (norm) acc.add(fma(u.x, u.x, u.y * u.y));
+    // top: prev = psi_{k-1}, cur = psi_k; bottom: prev = psi_{k+1}, d = e_{k+1}
+    const C o_prev = mkb<T>(__shfl_xor_sync(0xffffffffu, prev.x, 16), __shfl_xor_sync(0xffffffffu, prev.y, 16));
+    const C o_d = mkb<T>(__shfl_xor_sync(0xffffffffu, d.x, 16), __shfl_xor_sync(0xffffffffu, d.y, 16));
+    C vk = zero;
+    if (active && top) {
+        vk = cn.fwd(cn.rhs(prev, cur, o_prev), mkb<T>(d.x + o_d.x, d.y + o_d.y), mid);
+        row[k] = vk;
+        if (norm) acc.add(fma(vk.x, vk.x, vk.y * vk.y));
+    }
+    const C o_vk = mkb<T>(__shfl_xor_sync(0xffffffffu, vk.x, 16), __shfl_xor_sync(0xffffffffu, vk.y, 16));
+    C u = top ? vk : o_vk;
+    if (active) {
+        for (int t = len - 1; t >= 0; --t) {
+            const int pos = top ? 1 + t : m - t;
+            u = cn.back(row[pos], t < conv ? cp[t] : cinf, u);
+            row[pos] = u;
+            if (norm) acc.add(fma(u.x, u.x, u.y * u.y));
+        }
     }
 }
 
@@ -209,35 +241,36 @@ __device__ void sweep_tile(const Inst &I, int axis, int tile, typename BC<T>::c 
                           : axis == 1 ? (long long)I.n[0] * I.n[2] : (long long)I.n[0] * I.n[1];
     const long long L0 = (long long)tile * kTileLines;
     const int rows = (int)min((long long)kTileLines, lines - L0);
+    const int r = lane & (kTileLines - 1);
+    const bool top = lane < kTileLines, active = r < rows;
     C *psi = static_cast<C *>(I.psi);
-    long long base, stride;
+    long long base = 0, stride = 0;
     constexpr int B = (int)sizeof(C);
+    // y / z tiles: the lane pair of line r moves the two halves of its line
+    const int c_lo = top ? 0 : n / 2, c_hi = top ? n / 2 : n;
     if (axis == 0) {
-        for (int r = 0; r < rows; ++r) {
-            const C *src = psi + (L0 + r) * I.n[0];
-            for (int c = lane; c < n; c += 32) cp_async<B>(&sm[r * P + c], &src[c]);
+        for (int rr = 0; rr < rows; ++rr) {
+            const C *src = psi + (L0 + rr) * I.n[0];
+            for (int c = lane; c < n; c += 32) cp_async<B>(&sm[rr * P + c], &src[c]);
         }
-    } else if (lane < rows) {
-        line_geom(I, axis, L0 + lane, base, stride);
-        for (int c = 0; c < n; ++c) cp_async<B>(&sm[lane * P + c], &psi[base + c * stride]);
+    } else if (active) {
+        line_geom(I, axis, L0 + r, base, stride);
+        for (int c = c_lo; c < c_hi; ++c) cp_async<B>(&sm[r * P + c], &psi[base + c * stride]);
     }
     cp_async_wait_all();
     __syncwarp();
     const bool norm = I.mode == 0 && axis == I.last_axis;
     Acc<T> acc;
-    if (lane < rows) {
-        if (I.mode == 0) solve_line<T, 0>(I, axis, sm + lane * P, n, L0 + lane, axis == 0, norm, acc);
-        else solve_line<T, 1>(I, axis, sm + lane * P, n, L0 + lane, axis == 0, false, acc);
-    }
+    if (I.mode == 0) solve_line2<T, 0>(I, axis, sm + r * P, n, L0 + r, top, active, axis == 0, norm, acc);
+    else solve_line2<T, 1>(I, axis, sm + r * P, n, L0 + r, top, active, axis == 0, false, acc);
     __syncwarp();
     if (axis == 0) {
-        for (int r = 0; r < rows; ++r) {
-            C *dst = psi + (L0 + r) * I.n[0];
-            for (int c = lane; c < n; c += 32) dst[c] = sm[r * P + c];
+        for (int rr = 0; rr < rows; ++rr) {
+            C *dst = psi + (L0 + rr) * I.n[0];
+            for (int c = lane; c < n; c += 32) dst[c] = sm[rr * P + c];
         }
-    } else if (lane < rows) {
-        line_geom(I, axis, L0 + lane, base, stride);
-        for (int c = 0; c < n; ++c) psi[base + c * stride] = sm[lane * P + c];
+    } else if (active) {
+        for (int c = c_lo; c < c_hi; ++c) psi[base + c * stride] = sm[r * P + c];
     }
     if (norm) {
         const double v = warp_sum_d(acc.get());
@@ -636,6 +669,8 @@ Inst make_inst(const gp_batch_slot &s, int prec)
         I.minf64[k] = a.minf64;
         I.cinf32[k] = a.cinf32;
         I.minf32[k] = a.minf32;
+        I.mid64[k] = a.mid64;
+        I.mid32[k] = a.mid32;
         I.ph[k] = s.ph[s.mode][k];
         I.th[k] = s.th[k];
         I.x2[k] = s.x2[k];

@@ -7,6 +7,12 @@ steps apart (complex64: by less than max(1e-6, 2^-22 |mu|), the resolution of
 mu from an FP32 state), optionally followed by a quench: the resident ground
 state continues in real time at a new g for a fixed number of steps.
 
+A solve also ends, unconverged, at the step cap or when |dmu| has not reached
+a new minimum for STALL_CHECKS checks in a row: where dt g max|psi|^2 is large
+the explicit nonlinear step makes the imaginary-time iteration settle into a
+cycle (mu alternating between two values) that no number of steps resolves.
+A converging solve lowers |dmu| at every check and never meets that rule.
+
 The server admits requests that have arrived, first come first served, as
 long as the batch's memory cap can take their footprint; every instance on the
 device advances together, chunk by chunk, in one persistent launch per chunk;
@@ -26,6 +32,7 @@ from . import gp
 from .workloads import convergence_interval
 
 MU_TOL = 1e-6
+STALL_CHECKS = 100
 # complex64 states carry FP32 rounding noise of ~1e-7 |mu| in the chemical
 # potential, so the absolute criterion is floored there at 2^-22 |mu|.
 MU_REL_FLOOR = {gp.GP_C64: 2.0 ** -22, gp.GP_C128: 0.0}
@@ -49,6 +56,9 @@ class Job:
     mu_prev: float = None
     obs: dict = None
     ground_obs: dict = None
+    watch: object = None
+    converged: bool = True
+    stalled: bool = False
 
 
 @dataclass
@@ -61,6 +71,8 @@ class Result:
     total_steps: int
     obs: dict
     ground_obs: dict = None
+    converged: bool = True
+    stalled: bool = False
 
     @property
     def latency(self):
@@ -80,12 +92,28 @@ class ServeStats:
         import numpy as np
         lat = np.array([r.latency for r in self.results]) if self.results else np.zeros(1)
         return {"requests": len(self.results), "wall_s": self.wall,
+                "converged": sum(1 for r in self.results if r.converged),
+                "stalled": sum(1 for r in self.results if r.stalled),
                 "requests_per_s": len(self.results) / self.wall if self.wall else 0.0,
                 "point_steps_per_s": self.point_steps / self.wall if self.wall else 0.0,
                 "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)),
                 "mean_latency_s": float(lat.mean()), "peak_bytes": self.peak_bytes,
                 "chunks": self.chunks}
+
+
+class StallWatch:
+    """Tracks the best |dmu| of a solve and the checks since it last fell."""
+
+    def __init__(self):
+        self.best, self.since = float("inf"), 0
+
+    def update(self, dmu):
+        if dmu < self.best:
+            self.best, self.since = dmu, 0
+        else:
+            self.since += 1
+        return self.since >= STALL_CHECKS
 
 
 def _instance_args(inst):
@@ -115,7 +143,8 @@ class Server:
     def _admit(self, req, now):
         shape, h, dt, g0, g1, g2, g = _instance_args(req.inst)
         slot = self.batch.add(shape, h, dt, g0, g1, g2, g, gp.GP_IMAG, psi=None)
-        return Job(req=req, slot=slot, t_admit=now, next_check=convergence_interval(dt))
+        return Job(req=req, slot=slot, t_admit=now, next_check=convergence_interval(dt),
+                   watch=StallWatch())
 
     def run(self, requests, realtime=True, max_steps=200000, on_chunk=None):
         """Serve `requests` (with .arrival seconds).  realtime: requests become
@@ -180,9 +209,12 @@ class Server:
                 if j.phase == "ground":
                     j.next_check += convergence_interval(j.req.inst.dt)
                     converged = mu_converged(o["mu"], j.mu_prev, self.precision)
+                    stalled = (j.mu_prev is not None and not converged and
+                               j.watch.update(abs(o["mu"] - j.mu_prev)))
                     j.mu_prev = o["mu"]
-                    if converged or j.total_steps >= max_steps:
+                    if converged or stalled or j.total_steps >= max_steps:
                         j.ground_obs = o
+                        j.converged, j.stalled = converged, stalled
                         if j.req.kind == "quench" and converged:
                             self.batch.set_params(j.slot, j.req.quench_g, gp.GP_REAL)
                             j.phase = "real"
@@ -198,7 +230,8 @@ class Server:
                 del active[j.slot]
                 results.append(Result(j.req, j.req.arrival, j.t_admit, now,
                                       j.total_steps - (j.steps if j.phase == "real" else 0),
-                                      j.total_steps, j.obs, j.ground_obs))
+                                      j.total_steps, j.obs, j.ground_obs,
+                                      j.converged, j.stalled))
             if on_chunk:
                 on_chunk(chunks, len(active), len(pending))
         wall = time.perf_counter() - t0
@@ -231,14 +264,16 @@ def solve_sequential(requests, precision=gp.GP_C128, realtime=True, max_steps=20
         k = convergence_interval(dt)
         with gp.Solver(shape, h, dt, g0, g1, g2, g, gp.GP_IMAG, precision, stream) as s:
             s.load(None)
-            steps, mu_prev = 0, None
+            steps, mu_prev, watch = 0, None, StallWatch()
             while True:
                 s.step(k)
                 steps += k
                 o = s.observables()
                 converged = mu_converged(o["mu"], mu_prev, precision)
+                stalled = (mu_prev is not None and not converged and
+                           watch.update(abs(o["mu"] - mu_prev)))
                 mu_prev = o["mu"]
-                if converged or steps >= max_steps:
+                if converged or stalled or steps >= max_steps:
                     break
             ground_obs, ground_steps = o, steps
             if req.kind == "quench" and converged:
@@ -248,7 +283,7 @@ def solve_sequential(requests, precision=gp.GP_C128, realtime=True, max_steps=20
                 o = s.observables()
         point_steps += req.inst.points * steps
         results.append(Result(req, req.arrival, start, time.perf_counter() - t0, ground_steps,
-                              steps, o, ground_obs))
+                              steps, o, ground_obs, converged, stalled))
     wall = time.perf_counter() - t0
     return ServeStats(results, wall, point_steps, 0)
 
