@@ -156,8 +156,8 @@ def measured_peaks():
         return {}
 
 
-KERNEL_SOURCES = ("sscn_kernels.cu", "sscn_tma.cu", "sscn_internal.h", "sscn_line.cuh",
-                  "sscn_coef.cuh", "sscn_accum.cuh")
+KERNEL_SOURCES = ("sscn_kernels.cu", "sscn_tma.cu", "sscn_axial.cu", "gp_batch.cu", "sscn_internal.h",
+                  "sscn_line.cuh", "sscn_coef.cuh", "sscn_accum.cuh")
 
 
 def kernel_source_sha():
@@ -614,12 +614,35 @@ def serving_form(gp, requests=40):
             "throughput_ratio": a["point_steps_per_s"] / b["point_steps_per_s"]}
 
 
+PROBE_BATCH = "batch-60-requests-c64"
+PROBE_AXIAL = "axial-1024x2048-fp64"
+
+
 def run_probe(args):
+    """A short run of one workload for profilers: N steps after setup.
+    --probe-case picks a single-grid case by name, PROBE_BATCH (the first 60
+    instances of the request stream in one batch, complex64, imaginary time)
+    or PROBE_AXIAL (the axial form of the bench)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1206_1361_gb300 import gp
-    from paper_1206_1361_gb300.workloads import CASES
+    from paper_1206_1361_gb300.workloads import CASES, request_stream
+    if args.probe_case == PROBE_BATCH:
+        with gp.Batch(gp.GP_C64, 1 << 36) as b:
+            for r in request_stream(count=60):
+                i = r.inst
+                b.add(i.shape, i.h, i.dt, *i.trap, i.g, gp.GP_IMAG)
+            b.step(args.probe)
+            gp.gp_batch_sync(b.b)
+        torch.cuda.synchronize()
+        return 0
+    if args.probe_case == PROBE_AXIAL:
+        with gp.Solver.axial(1024, 2048, 0.0125, 0.0125, 1e-4, 1.0, 4.0, 100.0, gp.GP_REAL) as s:
+            s.load(None).step(args.probe).sync()
+            s.observables()
+        torch.cuda.synchronize()
+        return 0
     case = CASES[args.probe_case] if args.probe_case else workload()
     with gp.Solver(case.shape, case.h, case.dt, *case.trap, case.g, gp.GP_REAL,
                    case.precision) as s:
