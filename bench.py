@@ -552,6 +552,7 @@ def axial_form(gp, torch, stream):
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / steps
         kt = gp.gp_time_kernels(s.ctx, 10)
+        paths = gp.gp_sweep_paths(s.ctx)[:2]
     points = nr * nz
     rho_ms = kt["sweep_x"]
     ach = FLOPS_PER_POINT[gp.GP_REAL]["sweep_x"] * points / (rho_ms * 1e-3) / 1e12
@@ -568,7 +569,9 @@ def axial_form(gp, torch, stream):
             "kernel_ms": {"sweep_rho": round(kt["sweep_x"], 5), "sweep_z": round(kt["sweep_y"], 5)},
             "roofline": {"bound": "alu", "kernel": "sweep_rho", "achieved": ach,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                         "note": "n_z = 2048 radial lines: 4096 threads, latency-bound"},
+                         "note": "segmented-window sweeps (calcnu pass + radial windows); "
+                                 "algorithmic flops only, the windows add overlap work"},
+            "sweep_paths": list(paths),
             "cpu_baseline": {"value": cpu, "unit": UNIT, "cores": oracle.get_threads(),
                              "kind": "oracle", "sample": "%d axial SSCN steps" % n_cpu}}
 

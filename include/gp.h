@@ -214,7 +214,11 @@ enum {
      * smaller error. */
     GP_OPT_SPLITTING = 3
 };
-enum { GP_PATH_AUTO = 0, GP_PATH_EXACT = 1, GP_PATH_TMA = 2 };
+/* GP_PATH_WINDOW (axial form): each line cut into cores solved in parallel,
+ * each extended by a window of rows wide enough that the cut coupling reaches
+ * the core below 2^-55 (the sweeps then agree with the exact solve to FP64
+ * rounding); GP_PATH_AUTO takes it when a line gets at least two cores. */
+enum { GP_PATH_AUTO = 0, GP_PATH_EXACT = 1, GP_PATH_TMA = 2, GP_PATH_WINDOW = 3 };
 enum { GP_SPLIT_LIE = 0, GP_SPLIT_STRANG = 1 };
 
 /*

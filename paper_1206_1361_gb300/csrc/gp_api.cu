@@ -43,6 +43,10 @@ struct gp_ctx {
     gp::RadialTables rt[2];         // [mode] radial sweep tables (device)
     void *rt_mem[2]{};
     double *rho_w = nullptr;        // rho_i, the norm weights
+    gp::SegWindow segw[2];          // [mode] segmented-window sweeps (few long lines)
+    bool seg_ok[2]{};
+    void *segw_mem[2]{};
+    void *pbuf = nullptr, *wscr = nullptr;
     double *partials = nullptr;     // norm partials, >= max sweep blocks
     int partial_cap = 0;
     double *obs_partials = nullptr; // observables scratch (rows + finish stage)
@@ -251,6 +255,69 @@ int upload_tables(gp_ctx *c)
     return GP_OK;
 }
 
+// Segmented-window sweeps of the axial form: one window W and core length Lc
+// per mode, W the smallest that shields every core below 2^-55 from the
+// truncated coupling on both axes; eligible when some axis gets >= 2 cores.
+int setup_segments(gp_ctx *c)
+{
+    const int nr = c->grid.nx, nz = c->grid.ny, mz = nz - 1;
+    size_t wscr_need = 0;
+    for (int mode = 0; mode < 2; ++mode) {
+        const double kap = c->dt / (4.0 * c->h[0] * c->h[0]);
+        const double kre = mode == 0 ? kap : 0.0, kim = mode == 0 ? 0.0 : kap;
+        const int wz = c->ax[mode][1].win64;
+        int W = 0, Lc = 64;
+        for (int it = 0; it < 4; ++it) {
+            const int wr = gp::radial_window_width(nr, kre, kim, Lc, std::ldexp(1.0, -55), 256);
+            W = (wr > 0 && wz > 0) ? std::max(wr, wz) : 0;
+            if (W == 0 || Lc >= 2 * W) break;
+            Lc = 2 * W;
+        }
+        gp::SegWindow &sw = c->segw[mode];
+        sw = gp::SegWindow{};
+        c->seg_ok[mode] = false;
+        if (W == 0 || Lc < 2 * W) continue;
+        sw.W = W;
+        sw.Lc = Lc;
+        sw.nseg_r = (nr + Lc - 1) / Lc;
+        sw.nseg_z = (mz + Lc - 1) / Lc;
+        sw.tlen = Lc + 2 * W;
+        if (sw.nseg_r < 2 && sw.nseg_z < 2) continue;
+        const size_t n2 = (size_t)sw.nseg_r * sw.tlen;
+        std::vector<double2> cp(n2), mult(n2);
+        std::vector<double> ka(nr);
+        gp::radial_window_tables(nr, kre, kim, Lc, W, cp.data(), mult.data(), ka.data());
+        int rc;
+        if ((rc = alloc(c, &c->segw_mem[mode], 2 * n2 * sizeof(double2) + nr * sizeof(double)))) return rc;
+        double2 *d2 = (double2 *)c->segw_mem[mode];
+        double *dk = (double *)(d2 + 2 * n2);
+        GP_CK(c, cudaMemcpy(d2, cp.data(), n2 * sizeof(double2), cudaMemcpyHostToDevice));
+        GP_CK(c, cudaMemcpy(d2 + n2, mult.data(), n2 * sizeof(double2), cudaMemcpyHostToDevice));
+        GP_CK(c, cudaMemcpy(dk, ka.data(), nr * sizeof(double), cudaMemcpyHostToDevice));
+        sw.cp_r = d2;
+        sw.mult_r = d2 + n2;
+        sw.ka_r = dk;
+        c->seg_ok[mode] = true;
+        wscr_need = std::max(wscr_need, (size_t)W * std::max((size_t)nz * sw.nseg_r,
+                                                              (size_t)nr * sw.nseg_z));
+        // the axial sweep's norm partials: one per block
+        const int zb = (int)(((long long)sw.nseg_z * nr + 127) / 128);
+        if (zb > c->partial_cap) {
+            double *bigger = nullptr;
+            if ((rc = alloc(c, (void **)&bigger, (size_t)zb * sizeof(double)))) return rc;
+            cudaFree(c->partials);
+            c->partials = bigger;
+            c->partial_cap = zb;
+        }
+    }
+    if (c->seg_ok[0] || c->seg_ok[1]) {
+        int rc;
+        if ((rc = alloc(c, &c->pbuf, (size_t)nr * nz * sizeof(double2)))) return rc;
+        if ((rc = alloc(c, &c->wscr, std::max<size_t>(wscr_need, 1) * sizeof(double2)))) return rc;
+    }
+    return GP_OK;
+}
+
 // TMA path eligibility per (mode, axis): the tensor map encodes, and the
 // window truncation bound max|c'|^(C+1) is below the precision's rounding.
 void setup_tma(gp_ctx *c)
@@ -324,6 +391,10 @@ void release(gp_ctx *c)
     fr(c->rt_mem[0]);
     fr(c->rt_mem[1]);
     fr(c->rho_w);
+    fr(c->segw_mem[0]);
+    fr(c->segw_mem[1]);
+    fr(c->pbuf);
+    fr(c->wscr);
     fr(c->partials);
     fr(c->obs_partials);
     fr(c->obs_tab);
@@ -340,6 +411,10 @@ void release(gp_ctx *c)
 // Path of the sweep along `axis` in the current mode.
 int sweep_path(const gp_ctx *c, int axis)
 {
+    if (c->axial) {
+        const bool seg = c->seg_ok[c->mode] && c->path_opt != GP_PATH_EXACT;
+        return seg ? GP_PATH_WINDOW : GP_PATH_EXACT;
+    }
     if (!c->tma_ok[c->mode][axis]) return GP_PATH_EXACT;
     if (c->path_opt == GP_PATH_EXACT) return GP_PATH_EXACT;
     if (c->path_opt == GP_PATH_TMA) return GP_PATH_TMA;
@@ -431,9 +506,23 @@ int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
         pointwise_args(c, imag ? 0 : last, true, 0.5, 1.0, imag ? c->scale : nullptr);
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], c->stream) : cudaSuccess; };
     GP_CK(c, mark(0));
+    int last_blocks = 0;
+    if (c->axial && sweep_path(c, 0) == GP_PATH_WINDOW) {
+        // psi -> work (radial), work -> psi (axial): neighbouring cores read
+        // each other's rows, so each sweep writes another buffer
+        const gp::SegWindow &sw = c->segw[mode];
+        GP_CK(c, gp::launch_sweep_rho_win(mode, c->psi, c->work, c->pbuf, c->wscr, sw, c->grid.nx,
+                                          c->grid.ny, nl, c->stream));
+        GP_CK(c, mark(1));
+        const bool out_nl = strang && !imag;
+        GP_CK(c, gp::launch_sweep_z_win(mode, c->work, c->psi, c->wscr, sw, c->ax[mode][1],
+                                        c->grid.nx, c->grid.ny, out_nl ? &nl2 : nullptr, c->rho_w,
+                                        imag ? &part : nullptr, &last_blocks, c->stream));
+        GP_CK(c, mark(2));
+        GP_CK(c, mark(3));
+    } else {
     GP_CK(c, launch_sweep(c, 0, &nl, false, nullptr, nullptr));
     GP_CK(c, mark(1));
-    int last_blocks = 0;
     for (int axis = 1; axis <= last; ++axis) {
         const bool is_last = axis == last;
         const gp::NonlinArgs *out_nl = (is_last && strang && !imag) ? &nl2 : nullptr;
@@ -442,6 +531,7 @@ int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
         GP_CK(c, mark(axis + 1));
     }
     if (!three_d) GP_CK(c, mark(3));
+    }
     if (imag) {
         GP_CK(c, gp::launch_norm_finish(c->partials, last_blocks, cell_volume(c), c->scale,
                                         c->norm_dev, c->err_dev, c->stream));
@@ -462,7 +552,8 @@ int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
 int kernels_per_step(const gp_ctx *c)
 {
     const bool imag = c->mode == GP_IMAG, strang = c->split == GP_SPLIT_STRANG;
-    return (c->grid.nz > 1 ? 3 : 2) + (imag ? 1 : 0) + (imag && strang ? 2 : 0) +
+    const bool seg = c->axial && sweep_path(c, 0) == GP_PATH_WINDOW;   // + the calcnu pass
+    return (c->grid.nz > 1 ? 3 : 2) + (seg ? 1 : 0) + (imag ? 1 : 0) + (imag && strang ? 2 : 0) +
            (modulated(c) ? 1 : 0);
 }
 
@@ -690,8 +781,14 @@ int gp_footprint_axial(int nr, int nz, int precision, size_t *bytes)
     const gp_grid grid{nr, nz, 1};
     if (!valid_grid(&grid) || precision != GP_C128 || !bytes)
         return fail(nullptr, GP_EINVAL, "gp_footprint_axial: invalid grid or precision");
+    // + radial tables, rho weights, and (segmented windows) the core buffer,
+    // the window scratch (W <= Lc / 2 rows per core: at most one psi), the
+    // restarted tables and the axial sweep's norm partials
+    const size_t psi = (size_t)nr * nz * sizeof(double2);
     *bytes = footprint_bytes(grid, precision) + 2 * (size_t)nr * (4 * sizeof(double2) + 2 * sizeof(double)) +
-             (size_t)nr * sizeof(double);
+             (size_t)nr * sizeof(double) + 2 * psi +
+             2 * (2 * (size_t)(2 * nr + 512) * sizeof(double2) + (size_t)nr * sizeof(double)) +
+             ((size_t)(nz / 32 + 2) * nr / 128 + 1) * sizeof(double);
     return GP_OK;
 }
 
@@ -798,6 +895,7 @@ int create_ctx(const gp_grid *grid, const double dx[3], double dt, double gamma,
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
     }
     if ((rc = upload_tables(c))) return bail(rc);
+    if (axial && (rc = setup_segments(c))) return bail(rc);
     setup_tma(c);
     {
         cudaError_t e = cudaMemsetAsync(c->psi, 0, psi_bytes, c->stream);
@@ -1008,8 +1106,14 @@ int gp_set_option(gp_ctx *c, int option, int value)
         return GP_OK;
     }
     if (option != GP_OPT_SWEEP_PATH) return fail(c, GP_EINVAL, "gp_set_option: unknown option");
-    if (value != GP_PATH_AUTO && value != GP_PATH_EXACT && value != GP_PATH_TMA)
+    if (value != GP_PATH_AUTO && value != GP_PATH_EXACT && value != GP_PATH_TMA &&
+        value != GP_PATH_WINDOW)
         return fail(c, GP_EINVAL, "gp_set_option: unknown sweep path");
+    if (value == GP_PATH_WINDOW && (!c->axial || !c->seg_ok[c->mode]))
+        return fail(c, GP_EINVAL, "gp_set_option: the segmented-window path is for axial grids "
+                                  "with long enough lines");
+    if (value == GP_PATH_TMA && c->axial)
+        return fail(c, GP_EINVAL, "gp_set_option: no TMA sweep path on the axial form");
     if (value == GP_PATH_TMA)
         for (int k = 0; k < naxes(c->grid); ++k)
             if (!c->tma_ok[c->mode][k])
@@ -1047,6 +1151,7 @@ int gp_autotune(gp_ctx *c, int steps, int *path_out, int *shape_out, double *ms_
     }
     struct Cand { int path, shape; };
     std::vector<Cand> cands{{GP_PATH_EXACT, shape0}};
+    if (c->axial && c->seg_ok[c->mode]) cands.push_back({GP_PATH_WINDOW, shape0});
     for (int sh = 0; sh < gp::tma_shapes(c->prec); ++sh) {
         c->tile_shape = sh;
         setup_tma(c);

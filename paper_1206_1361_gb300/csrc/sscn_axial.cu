@@ -141,6 +141,131 @@ k_sweep_rho(double2 *__restrict__ psi, double2 *__restrict__ work, const RadialT
     }
 }
 
+// calcnu of every point into pbuf (the radial windows overlap, so the
+// pointwise step is taken once per point before them).
+template <int MODE>
+__global__ void __launch_bounds__(256)
+k_calcnu_axial(const double2 *__restrict__ in, double2 *__restrict__ pbuf, int nr, int nz,
+               const double2 *__restrict__ pr, const double2 *__restrict__ pz,
+               const double2 *__restrict__ one, StepG sg, const double *__restrict__ scale)
+{
+    const double G = sg.value();
+    const long long count = (long long)nr * nz;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p % nr), k = (int)(p / nr);
+        Calcnu<double, MODE> nl{};
+        nl.setup(pr, pz, one, nullptr, nullptr, nullptr, k, 0, G, scale);
+        pbuf[p] = nl.apply(in[p], i);
+    }
+}
+
+// Segmented-window radial sweep of pbuf (calcnu already applied): thread
+// (q, k) owns core q of radial line k, solves rows a .. f (the core extended
+// by W rows each side, clipped to the line) with the restarted tables of core
+// q, and writes rows s .. e of out.
+template <int MODE>
+__global__ void __launch_bounds__(128)
+k_sweep_rho_win(const double2 *__restrict__ pbuf, double2 *__restrict__ out,
+                double2 *__restrict__ wscr, const SegWindow sw, int nr, int nz)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = (int)(tid % sw.nseg_r);
+    const long long k = tid / sw.nseg_r;
+    if (k >= nz) return;
+    const int s = q * sw.Lc, e = min(nr, s + sw.Lc) - 1;
+    const int a = max(0, s - sw.W), f = min(nr - 1, e + sw.W);
+    const double2 *prow = pbuf + k * nr;
+    double2 *rout = out + k * nr;
+    double2 *w = wscr + (k * sw.nseg_r + q) * (long long)sw.W;
+    const double2 *cpq = sw.cp_r + (long long)q * sw.tlen, *mq = sw.mult_r + (long long)q * sw.tlen;
+    double2 d = make_double2(0.0, 0.0);
+    for (int i0 = a; i0 <= f; i0 += kPrefetchR) {
+        double2 pv[kPrefetchR];
+#pragma unroll
+        for (int u = 0; u < kPrefetchR; ++u)
+            if (i0 + u <= f) pv[u] = prow[i0 + u];
+#pragma unroll
+        for (int u = 0; u < kPrefetchR; ++u) {
+            const int i = i0 + u;
+            if (i <= f) {
+                d = LineOps<double, MODE>{sw.ka_r[i]}.fwd(pv[u], d, mq[i - a]);
+                if (i >= s && i <= e) {
+                    rout[i] = d;
+                } else if (i > e) {
+                    w[i - e - 1] = d;
+                }
+            }
+        }
+    }
+    double2 v = d;
+    for (int i = f; i >= s; --i) {
+        if (i < f) v = LineOps<double, MODE>{0.0}.back(i > e ? w[i - e - 1] : rout[i], cpq[i - a], v);
+        if (i <= e) rout[i] = LineOps<double, MODE>::out(v, prow[i]);
+    }
+}
+
+// Segmented-window axial sweep along z: thread (i, q), rho index i fastest
+// (neighbouring threads on neighbouring addresses), unknowns j = 1 .. nz - 1
+// at stored row j.  Constant coefficients: the restarted tables of any core
+// are the standard ones from its window's first row.
+template <int MODE, bool NORM, bool NLOUT>
+__global__ void __launch_bounds__(128)
+k_sweep_z_win(const double2 *__restrict__ in, double2 *__restrict__ out,
+              double2 *__restrict__ wscr, const SegWindow sw, const double2 *__restrict__ cp,
+              const double2 *__restrict__ mult, double kap, int nr, int nz,
+              const double2 *__restrict__ pz, const double2 *__restrict__ px,
+              const double2 *__restrict__ p1, StepG sg, const double *__restrict__ rho_w,
+              double *__restrict__ partials)
+{
+    __shared__ double red[32];
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(tid % nr);
+    const long long q = tid / nr;
+    const bool active = q < sw.nseg_z;
+    const int m = nz - 1;
+    double acc = 0.0;
+    if (active) {
+        const int s = 1 + (int)q * sw.Lc, e = min(m, s + sw.Lc - 1);
+        const int a = max(1, s - sw.W), f = min(m, e + sw.W);
+        double2 *w = wscr + ((long long)i * sw.nseg_z + q) * sw.W;
+        const LineOps<double, MODE> cn{kap};
+        Calcnu<double, MODE> nl{};
+        if (NLOUT) nl.setup(pz, px, p1, nullptr, nullptr, nullptr, i, 0, sg.value(), nullptr);
+        double2 d = make_double2(0.0, 0.0);
+        for (int j0 = a; j0 <= f; j0 += kPrefetchR) {
+            double2 pv[kPrefetchR];
+#pragma unroll
+            for (int u = 0; u < kPrefetchR; ++u)
+                if (j0 + u <= f) pv[u] = in[(long long)(j0 + u) * nr + i];
+#pragma unroll
+            for (int u = 0; u < kPrefetchR; ++u) {
+                const int j = j0 + u;
+                if (j <= f) {
+                    d = cn.fwd(pv[u], d, mult[j - a]);
+                    if (j >= s && j <= e) out[(long long)j * nr + i] = d;
+                    else if (j > e) w[j - e - 1] = d;
+                }
+            }
+        }
+        double2 v = d;
+        for (int j = f; j >= s; --j) {
+            if (j < f) v = cn.back(j > e ? w[j - e - 1] : out[(long long)j * nr + i], cp[j - a], v);
+            if (j <= e) {
+                double2 u = LineOps<double, MODE>::out(v, in[(long long)j * nr + i]);
+                if (NLOUT) u = nl.apply(u, j);
+                out[(long long)j * nr + i] = u;
+                if (NORM) acc = fma(u.x, u.x, fma(u.y, u.y, acc));
+            }
+        }
+        if (NORM) acc *= rho_w[i];
+    }
+    if (NORM) {
+        const double r = block_sum(acc, red);
+        if (threadIdx.x == 0) partials[blockIdx.x] = r;
+    }
+}
+
 __global__ void k_seed_axial(double2 *__restrict__ psi, int nr, int nz, double hr, double hz,
                              double gamma, double lambda)
 {
@@ -261,6 +386,62 @@ void radial_tables(int m, double kre, double kim, double2 *cp_top, double2 *mult
     *kc_mid = kabs * c(k);
 }
 
+void radial_window_tables(int m, double kre, double kim, int Lc, int W, double2 *cp, double2 *mult,
+                          double *ka)
+{
+    using cd = std::complex<double>;
+    const cd kappa(kre, kim);
+    const double kabs = std::abs(kappa);
+    const int nseg = (m + Lc - 1) / Lc, tlen = Lc + 2 * W;
+    auto a = [](int i) { return 1.0 - 1.0 / (2.0 * i + 1.0); };     // 0-based row i
+    auto c = [](int i) { return 1.0 + 1.0 / (2.0 * i + 1.0); };
+    for (int i = 0; i < m; ++i) ka[i] = kabs * a(i);
+    for (int q = 0; q < nseg; ++q) {
+        const int s = q * Lc, e = std::min(m, s + Lc) - 1;
+        const int lo = std::max(0, s - W), hi = std::min(m - 1, e + W);
+        cd prev = 0.0;
+        for (int i = lo; i <= hi; ++i) {
+            const cd f = 1.0 / (1.0 + 2.0 * kappa + kappa * a(i) * prev);
+            prev = -kappa * c(i) * f;
+            mult[(size_t)q * tlen + (i - lo)] = make_double2(f.real(), f.imag());
+            cp[(size_t)q * tlen + (i - lo)] = make_double2(prev.real(), prev.imag());
+        }
+    }
+}
+
+int radial_window_width(int m, double kre, double kim, int Lc, double tol, int wmax)
+{
+    using cd = std::complex<double>;
+    const cd kappa(kre, kim);
+    std::vector<double> rb(m), rf(m);       // |c'_i|, |kappa a_i mult_i|
+    cd prev = 0.0;
+    for (int i = 0; i < m; ++i) {
+        const double ai = 1.0 - 1.0 / (2.0 * i + 1.0), ci = 1.0 + 1.0 / (2.0 * i + 1.0);
+        const cd f = 1.0 / (1.0 + 2.0 * kappa + kappa * ai * prev);
+        prev = -kappa * ci * f;
+        rb[i] = std::abs(prev);
+        rf[i] = std::abs(kappa * ai * f);
+    }
+    for (int W = 1; W <= wmax; ++W) {
+        bool ok = true;
+        for (int s = 0; s < m && ok; s += Lc) {
+            const int e = std::min(m, s + Lc) - 1;
+            if (s - W > 0) {                  // forward truncation at row s - W
+                double p = 1.0;
+                for (int i = s - W; i < s; ++i) p *= rf[i];
+                ok = p < tol;
+            }
+            if (ok && e + W < m - 1) {        // backward truncation after row e + W
+                double p = 1.0;
+                for (int i = e + 1; i <= e + W; ++i) p *= rb[i];
+                ok = p < tol;
+            }
+        }
+        if (ok) return W;
+    }
+    return 0;
+}
+
 int sweep_rho_blocks(int nz) { return (nz + kLinesPerBlock - 1) / kLinesPerBlock; }
 
 cudaError_t launch_sweep_rho(int mode, void *psi, void *work, const RadialTables &rt, int nr,
@@ -270,6 +451,55 @@ cudaError_t launch_sweep_rho(int mode, void *psi, void *work, const RadialTables
     auto k = mode == 0 ? k_sweep_rho<0> : k_sweep_rho<1>;
     k<<<blocks, kThreads, 0, st>>>((double2 *)psi, (double2 *)work, rt, nr, nz, nl.px, nl.py,
                                    nl.pz, nl.g, nl.scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_rho_win(int mode, const void *in, void *out, void *pbuf, void *wscr,
+                                 const SegWindow &sw, int nr, int nz, const NonlinArgs &nl,
+                                 cudaStream_t st)
+{
+    long long pb = ((long long)nr * nz + 255) / 256;
+    if (pb > 4 * kReduceBlocks) pb = 4 * kReduceBlocks;
+    auto kc = mode == 0 ? k_calcnu_axial<0> : k_calcnu_axial<1>;
+    kc<<<(int)pb, 256, 0, st>>>((const double2 *)in, (double2 *)pbuf, nr, nz, nl.px, nl.py, nl.pz,
+                                nl.g, nl.scale);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const long long threads = (long long)sw.nseg_r * nz;
+    const int blocks = (int)((threads + 127) / 128);
+    auto k = mode == 0 ? k_sweep_rho_win<0> : k_sweep_rho_win<1>;
+    k<<<blocks, 128, 0, st>>>((const double2 *)pbuf, (double2 *)out, (double2 *)wscr, sw, nr, nz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_z_win(int mode, const void *in, void *out, void *wscr,
+                               const SegWindow &sw, const AxisTables &az, int nr, int nz,
+                               const NonlinArgs *nlout, const double *rho_w,
+                               const Partials *norm_out, int *blocks, cudaStream_t st)
+{
+    const long long threads = (long long)sw.nseg_z * nr;
+    const int nb = (int)((threads + 127) / 128);
+    if (blocks) *blocks = nb;
+    const double kap = mode == 0 ? az.kre : az.kim;
+    const StepG sg = nlout ? nlout->g : StepG{};
+    const double2 *pz = nlout ? nlout->px : nullptr, *px = nlout ? nlout->py : nullptr,
+                  *p1 = nlout ? nlout->pz : nullptr;
+    double *part = norm_out ? norm_out->buf : nullptr;
+#define GP_ZW(M, N, O)                                                                        \
+    k_sweep_z_win<M, N, O><<<nb, 128, 0, st>>>((const double2 *)in, (double2 *)out,           \
+                                               (double2 *)wscr, sw, az.cp64, az.mult64, kap,  \
+                                               nr, nz, pz, px, p1, sg, rho_w, part)
+    if (nlout) {
+        if (mode != 1 || norm_out) return cudaErrorInvalidValue;
+        GP_ZW(1, false, true);
+    } else if (mode == 0) {
+        if (norm_out) GP_ZW(0, true, false);
+        else GP_ZW(0, false, false);
+    } else {
+        if (norm_out) GP_ZW(1, true, false);
+        else GP_ZW(1, false, false);
+    }
+#undef GP_ZW
     return cudaGetLastError();
 }
 

@@ -197,6 +197,43 @@ void radial_tables(int m, double kre, double kim, double2 *cp_top, double2 *mult
 // by the line), nl.pz = a one-entry table (1, 0).
 cudaError_t launch_sweep_rho(int mode, void *psi, void *work, const RadialTables &rt, int nr,
                              int nz, const NonlinArgs &nl, cudaStream_t st);
+
+// Segmented-window sweeps of the axial form (few, long lines).  Each line is
+// cut into cores of Lc unknowns; a thread solves its core's rows extended by
+// W rows on either side (zero coupling beyond the extension: the restarted
+// elimination) and keeps the core.  The dropped coupling reaches the core
+// damped by the product of |c'| (or |kappa a m|) over the W rows between, and
+// the host picks W so that product stays below 2^-55 for every core, so the
+// core rows agree with the exact solve to FP64 rounding.  The sweeps read
+// `in` and write `out` (neighbouring cores read each other's rows).
+struct SegWindow {
+    int W = 0, Lc = 0;
+    int nseg_r = 0, nseg_z = 0;         // cores per radial / axial line
+    int tlen = 0;                       // radial table row: Lc + 2 W
+    const double2 *cp_r = nullptr, *mult_r = nullptr;   // [nseg_r][tlen] restarted radial tables
+    const double *ka_r = nullptr;       // |kappa_r| a_i, i = 0 .. nr - 1
+};
+// Host: restarted radial tables for cores of Lc rows and windows of W rows
+// (cp, mult: nseg * (Lc + 2 W) entries each; ka: m entries).
+void radial_window_tables(int m, double kre, double kim, int Lc, int W, double2 *cp, double2 *mult,
+                          double *ka);
+// Host: smallest window W (<= wmax, else 0) such that every core of Lc rows is
+// shielded below tol from both truncations, for the radial tables of kappa.
+int radial_window_width(int m, double kre, double kim, int Lc, double tol, int wmax);
+// Radial: in -> out; calcnu (nl as for launch_sweep_rho) first as its own
+// pass in -> pbuf (nr nz: the windows overlap, so each point's pointwise step
+// is taken once), then the windowed sweep pbuf -> out; wscr (nz nseg_r W)
+// holds the overlap rows.  Two launches.
+cudaError_t launch_sweep_rho_win(int mode, const void *in, void *out, void *pbuf, void *wscr,
+                                 const SegWindow &sw, int nr, int nz, const NonlinArgs &nl,
+                                 cudaStream_t st);
+// Axial: in -> out along z with the constant-coefficient tables (cp, mult of
+// the z axis); nlout (real time) applies calcnu (z order: pz, px, p1) to the
+// results; norm_out adds sum rho_i |u|^2 per block (rho_w).  wscr: nr nseg_z W.
+cudaError_t launch_sweep_z_win(int mode, const void *in, void *out, void *wscr,
+                               const SegWindow &sw, const AxisTables &az, int nr, int nz,
+                               const NonlinArgs *nlout, const double *rho_w,
+                               const Partials *norm_out, int *blocks, cudaStream_t st);
 int sweep_rho_blocks(int nz);
 // Gaussian seed exp(-(gamma rho^2 + lambda z^2) / 2), zero at k = 0.
 cudaError_t launch_seed_axial(void *psi, int nr, int nz, double hr, double hz, double gamma,

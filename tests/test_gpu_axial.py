@@ -114,3 +114,45 @@ def test_arguments():
     with pytest.raises(gp.GPError):
         gp.gp_create_axial(10, 10, -0.1, 0.1, 0.01, 1, 1, 0, 0, gp.GP_C128)
     assert gp.gp_footprint_axial(100, 200) > 100 * 200 * 32
+
+
+# grids long enough for the segmented-window sweeps (>= 2 cores per line)
+WIN_GRIDS = [(300, 420, 0.05, 0.06), (700, 130, 0.02, 0.1)]
+
+
+@pytest.mark.parametrize("nr,nz,hr,hz", WIN_GRIDS)
+@pytest.mark.parametrize("mode", [gp.GP_REAL, gp.GP_IMAG])
+def test_segmented_window_sweeps_match_oracle_and_exact(nr, nz, hr, hz, mode):
+    require_gpu()
+    dt, g = 0.004, 9.0
+    psi0 = rand_state(nr, nz, 31)
+    with solver(nr, nz, hr, hz, dt, g, mode) as s:
+        assert gp.gp_sweep_paths(s.ctx)[:2] == (gp.GP_PATH_WINDOW, gp.GP_PATH_WINDOW)
+        s.load(psi0).step(12)
+        got = s.psi()
+    with solver(nr, nz, hr, hz, dt, g, mode) as s:
+        s.set_path(gp.GP_PATH_EXACT)
+        assert gp.gp_sweep_paths(s.ctx)[:2] == (gp.GP_PATH_EXACT, gp.GP_PATH_EXACT)
+        s.load(psi0).step(12)
+        exact = s.psi()
+    want = oracle.axial_step(params(nr, nz, hr, hz, dt, g, mode), psi0.copy(), 12)
+    assert rel_l2(got, want) <= 1e-12
+    assert rel_l2(got, exact) <= 1e-13
+
+
+@pytest.mark.parametrize("mode", [gp.GP_REAL, gp.GP_IMAG])
+def test_segmented_window_strang_modulation_and_norm(mode):
+    require_gpu()
+    nr, nz, hr, hz, dt = 320, 300, 0.04, 0.05, 0.002
+    psi0 = rand_state(nr, nz, 8)
+    with solver(nr, nz, hr, hz, dt, 20.0, mode) as s:
+        s.set_splitting(gp.GP_SPLIT_STRANG).set_modulation(5.0, 40.0)
+        s.load(psi0)
+        n0 = s.observables()["norm"]
+        s.step(17)
+        got, obs = s.psi(), s.observables()
+    want = oracle.axial_step(params(nr, nz, hr, hz, dt, 20.0, mode), psi0.copy(), 17, 0, True,
+                             5.0, 40.0)
+    assert rel_l2(got, want) <= 1e-12
+    if mode == gp.GP_REAL:
+        assert abs(obs["norm"] / n0 - 1) <= 17 * 2e-15
