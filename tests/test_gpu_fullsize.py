@@ -104,3 +104,63 @@ def test_batched_256_instances_sampled_against_solo_and_oracle():
         assert rel_l2(mix[k].astype(np.complex128), want) <= steps * 4 * 2.0 ** -23, k
         ref = oracle.observables(p, want)
         assert abs(obs_mix[slots[k]]["mu"] - ref["mu"]) <= 1e-6 * max(1.0, abs(ref["mu"])), k
+
+
+def test_real_256_strang_modulated_matches_oracle():
+    """The symmetric splitting with g(t) = 18 + 4 cos(30 t) on the benchmark
+    grid, 100 real-time steps from a short imaginary-time prep, through the
+    graph: psi within 1e-10 of the oracle."""
+    require_gpu()
+    c = REAL_256
+    with gp.Solver(c.shape, c.h, c.dt, *c.trap, c.extra["g_ground"], gp.GP_IMAG) as s:
+        s.load(None).step(20)
+        s.set_params(c.g, gp.GP_REAL).set_splitting(gp.GP_SPLIT_STRANG).set_modulation(4.0, 30.0)
+        s.step(100)
+        got = s.psi()
+    pi = oracle_params(c.shape, c.h, c.dt, c.trap, c.extra["g_ground"], 0)
+    want = oracle.seed(pi)
+    oracle.step(pi, want, 20)
+    pr = oracle_params(c.shape, c.h, c.dt, c.trap, c.g, 1)
+    oracle.step_ext(pr, want, 100, 20, True, 4.0, 30.0)
+    assert rel_l2(got, want) <= 1e-10
+
+
+def test_axial_bench_case_matches_oracle():
+    """The bench's axial case (1024 x 2048, h = 0.0125, trap (1, 4), g = 100,
+    real time from the seed) on the segmented-window path, 30 steps."""
+    require_gpu()
+    nr, nz, h, dt, g = 1024, 2048, 0.0125, 1e-4, 100.0
+    with gp.Solver.axial(nr, nz, h, h, dt, 1.0, 4.0, g, gp.GP_REAL) as s:
+        assert gp.gp_sweep_paths(s.ctx)[:2] == (gp.GP_PATH_WINDOW, gp.GP_PATH_WINDOW)
+        s.load(None).step(30)
+        got, obs = s.psi(), s.observables()
+    p = oracle.AxialParams.make(nr, nz, h, h, dt, 1.0, 4.0, g, 1)
+    want = oracle.axial_seed(p)
+    oracle.axial_step(p, want, 30)
+    assert rel_l2(got, want) <= 1e-11
+    ref = oracle.axial_observables(p, want)
+    for k in ("norm", "mu", "energy", "rms_x", "rms_z"):
+        assert abs(obs[k] - ref[k]) <= 1e-11 * abs(ref[k]), k
+
+
+@pytest.mark.parametrize("shape,h", [((8192, 3, 3), (0.002, 1.0, 1.0)), ((3, 8192, 4), (1.0, 0.002, 0.9)),
+                                     ((3, 4, 8192), (1.0, 0.9, 0.002))])
+def test_longest_lines(shape, h):
+    """Lines of the maximum edge (8192 points) along each axis."""
+    require_gpu()
+    rng = np.random.default_rng(6)
+    nx, ny, nz = shape
+    psi0 = (rng.standard_normal((nz, ny, nx)) + 1j * rng.standard_normal((nz, ny, nx))) * 0.3
+    psi0[:, :, 0] = 0
+    psi0[:, 0, :] = 0
+    psi0[0] = 0
+    for mode in (gp.GP_REAL, gp.GP_IMAG):
+        p = oracle_params(shape, h, 0.001, (1.0, 1.5, 2.0), 3.0, mode)
+        want = psi0.copy()
+        oracle.step(p, want, 5)
+        for prec, dtype, tol in ((gp.GP_C128, np.complex128, 1e-12),
+                                 (gp.GP_C64, np.complex64, 5 * 4 * 2.0 ** -23)):
+            with gp.Solver(shape, h, 0.001, 1.0, 1.5, 2.0, 3.0, mode, prec) as s:
+                s.load(psi0.astype(dtype)).step(5)
+                got = s.psi().astype(np.complex128)
+            assert rel_l2(got, want) <= tol, (mode, prec)
