@@ -212,7 +212,14 @@ enum {
      * extra pass over psi per step; its fixed point stays first order in dt
      * (renormalisation does not commute with the nonlinear step) with a much
      * smaller error. */
-    GP_OPT_SPLITTING = 3
+    GP_OPT_SPLITTING = 3,
+    /* 1 (default): the FP64 real-time x sweep (plain splitting, exact path)
+     * reads the potential factor exp(-i dt V) of each point from a table laid
+     * out like psi, built on the first such step (one more psi-sized buffer;
+     * the sweep is bound by the FP64 pipe, and the table saves it one complex
+     * multiply per point).  0: form it from the per-axis tables and free the
+     * table. */
+    GP_OPT_POTENTIAL_TABLE = 4
 };
 /* GP_PATH_WINDOW (axial form): each line cut into cores solved in parallel,
  * each extended by a window of rows wide enough that the cut coupling reaches

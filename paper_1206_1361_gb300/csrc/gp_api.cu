@@ -47,6 +47,10 @@ struct gp_ctx {
     bool seg_ok[2]{};
     void *segw_mem[2]{};
     void *pbuf = nullptr, *wscr = nullptr;
+    // FP64 real-time potential factor table (one psi-sized buffer, built on
+    // the first real-time step that uses it)
+    int pot_table = 1;
+    double2 *pot3 = nullptr;
     double *partials = nullptr;     // norm partials, >= max sweep blocks
     int partial_cap = 0;
     double *obs_partials = nullptr; // observables scratch (rows + finish stage)
@@ -368,7 +372,8 @@ size_t footprint_bytes(const gp_grid &g, int prec)
                        2 * (size_t)(g.nx + g.ny + g.nz) * sizeof(double) +
                        gp::kObsWidth * sizeof(double) + 2 * sizeof(double) + sizeof(int) +
                        sizeof(long long);
-    return 2 * psi + tables + red;
+    // FP64: the real-time potential factor table (one more psi)
+    return (prec == GP_C128 ? 3 : 2) * psi + tables + red;
 }
 
 void release(gp_ctx *c)
@@ -395,6 +400,7 @@ void release(gp_ctx *c)
     fr(c->segw_mem[1]);
     fr(c->pbuf);
     fr(c->wscr);
+    fr(c->pot3);
     fr(c->partials);
     fr(c->obs_partials);
     fr(c->obs_tab);
@@ -484,6 +490,25 @@ gp::NonlinArgs pointwise_args(const gp_ctx *c, int axis, bool half, double fa, d
     return nl;
 }
 
+// The FP64 real-time plain-splitting x sweep on the exact path reads its
+// potential factors from the precomputed table.
+bool uses_pot3(const gp_ctx *c)
+{
+    return c->pot_table && c->prec == GP_C128 && c->mode == GP_REAL && c->split == GP_SPLIT_LIE &&
+           !c->axial && sweep_path(c, 0) == GP_PATH_EXACT;
+}
+
+// Allocate and fill the table if this step needs it (never under stream capture).
+int prepare_pot3(gp_ctx *c)
+{
+    if (!uses_pot3(c) || c->pot3) return GP_OK;
+    int rc = alloc(c, (void **)&c->pot3, (size_t)points(c->grid) * sizeof(double2));
+    if (rc) return rc;
+    GP_CK(c, gp::launch_build_pot3(c->pot3, c->ph[GP_REAL][0], c->ph[GP_REAL][1], c->ph[GP_REAL][2],
+                                   c->grid.nx, c->grid.ny, c->grid.nz, c->stream));
+    return GP_OK;
+}
+
 // Enqueue one SSCN step.  With ev != nullptr, record ev[0] before the first
 // kernel and ev[1 + k] after kernel slot k (x, y, z sweep, then the norm
 // finish and the rest of the step); slots a step does not launch get their
@@ -501,7 +526,8 @@ int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
     const bool imag = mode == GP_IMAG;
     const int last = three_d ? 2 : 1;
     Partials part{c->partials, 1, c->axial ? c->rho_w : nullptr};
-    const gp::NonlinArgs nl = pointwise_args(c, 0, strang, 0.0, strang ? 0.5 : 1.0, c->scale);
+    gp::NonlinArgs nl = pointwise_args(c, 0, strang, 0.0, strang ? 0.5 : 1.0, c->scale);
+    if (uses_pot3(c) && c->pot3) nl.p3 = c->pot3;
     const gp::NonlinArgs nl2 =
         pointwise_args(c, imag ? 0 : last, true, 0.5, 1.0, imag ? c->scale : nullptr);
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], c->stream) : cudaSuccess; };
@@ -994,6 +1020,7 @@ int gp_step(gp_ctx *c, int64_t n)
     if (!c) return fail(nullptr, GP_EINVAL, "gp_step: null context");
     if (n < 0) return fail(c, GP_EINVAL, "gp_step: n < 0");
     if (n == 0) return GP_OK;
+    if (int rc = prepare_pot3(c)) return rc;
     if (n >= kGraphSteps && !c->graph) build_graph(c);
     int64_t done = 0;
     if (c->graph) {
@@ -1050,6 +1077,7 @@ int gp_time_kernels(gp_ctx *c, int64_t steps, double *ms_out, int n_out)
 {
     if (!c || !ms_out || n_out < 5 || steps < 1)
         return fail(c, GP_EINVAL, "gp_time_kernels: need steps >= 1 and n_out >= 5");
+    if (int rc0 = prepare_pot3(c)) return rc0;
     cudaEvent_t ev[5];
     for (auto &e : ev) GP_CK(c, cudaEventCreate(&e));
     double acc[4] = {0, 0, 0, 0};
@@ -1091,6 +1119,17 @@ int gp_set_option(gp_ctx *c, int option, int value)
         if (value != GP_SPLIT_LIE && value != GP_SPLIT_STRANG)
             return fail(c, GP_EINVAL, "gp_set_option: unknown splitting");
         c->split = value;
+        drop_graph(c);
+        return GP_OK;
+    }
+    if (option == GP_OPT_POTENTIAL_TABLE) {
+        if (value != 0 && value != 1) return fail(c, GP_EINVAL, "gp_set_option: potential table is 0 or 1");
+        c->pot_table = value;
+        if (!value && c->pot3) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->pot3);
+            c->pot3 = nullptr;
+        }
         drop_graph(c);
         return GP_OK;
     }
@@ -1170,6 +1209,7 @@ int gp_autotune(gp_ctx *c, int steps, int *path_out, int *shape_out, double *ms_
         setup_tma(c);
         c->path_opt = cd.path;
         drop_graph(c);
+        if ((rc = prepare_pot3(c))) break;
         if ((rc = enqueue_step(c))) break;             // warm-up
         cudaEventRecord(e0, c->stream);
         for (int s = 0; s < steps && rc == GP_OK; ++s) rc = enqueue_step(c);
@@ -1218,6 +1258,7 @@ int gp_get_option(gp_ctx *c, int option, int *value)
     if (option == GP_OPT_SWEEP_PATH) *value = c->path_opt;
     else if (option == GP_OPT_TILE_SHAPE) *value = c->tile_shape;
     else if (option == GP_OPT_SPLITTING) *value = c->split;
+    else if (option == GP_OPT_POTENTIAL_TABLE) *value = c->pot_table;
     else return fail(c, GP_EINVAL, "gp_get_option: unknown option");
     return GP_OK;
 }

@@ -93,6 +93,9 @@ struct NonlinArgs {
     const float *tx32 = nullptr, *ty32 = nullptr, *tz32 = nullptr;
     StepG g;                         // G of the (sub)step
     const double *scale = nullptr;   // pending imaginary-time scale (device); nullptr: none
+    // FP64 real-time x sweep: P_x[i] P_y[j] P_z[k] per point, laid out like psi
+    // (nullptr: form it from the per-axis tables)
+    const double2 *p3 = nullptr;
 };
 
 // Reduction partials of one sweep / observables pass.
@@ -128,6 +131,9 @@ cudaError_t launch_sweep_yz(int prec, int mode, void *psi, void *work,
 cudaError_t launch_calcnu_pass(int prec, int mode, void *psi, int nx, int ny, int nz,
                                const NonlinArgs &nl, const Partials &norm_out, int blocks,
                                cudaStream_t st, const double *wx = nullptr);
+// Fill the FP64 potential factor table p3 (nx ny nz) from the per-axis tables.
+cudaError_t launch_build_pot3(void *p3, const double2 *px, const double2 *py, const double2 *pz,
+                              int nx, int ny, int nz, cudaStream_t st);
 // Device step counter (modulated g): set it, or add one.
 cudaError_t launch_set_step(long long *step, long long value, cudaStream_t st);
 cudaError_t launch_add_step(long long *step, cudaStream_t st);

@@ -114,8 +114,11 @@ __device__ __forceinline__ typename CT<T>::c shfl_xor16(typename CT<T>::c v)
 
 // NL: calcnu on each point as it is loaded (the x sweep); NLOUT: calcnu on
 // each result before it is stored (the second half step of the symmetric
-// splitting, in the last sweep).
-template <typename T, int MODE, bool NL, bool NORM, bool NLOUT = false>
+// splitting, in the last sweep).  P3 (FP64 real time): the potential factor
+// P_x[i] P_y[j] P_z[k] of each point comes from a precomputed table laid out
+// like psi (one complex multiply per point instead of two; 16 more bytes read
+// per point by a sweep that is bound by the FP64 pipe, not by HBM).
+template <typename T, int MODE, bool NL, bool NORM, bool NLOUT = false, bool P3 = false>
 __global__ void __launch_bounds__(kSweepThreads)
 k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ work,
         const typename Coef<T>::t *__restrict__ cp,
@@ -124,7 +127,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
         const typename Coef<T>::t *__restrict__ py, const typename Coef<T>::t *__restrict__ pz,
         const float *__restrict__ tx, const float *__restrict__ ty, const float *__restrict__ tz,
         StepG sg, const double *__restrict__ scale, double *__restrict__ partials,
-        const double *__restrict__ lw)
+        const double *__restrict__ lw, const double2 *__restrict__ p3)
 {
     using C = typename CT<T>::c;
     __shared__ double red[32];
@@ -142,7 +145,20 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
     C *wl = work + base;
     const LineOps<T, MODE> cn{kappa};
     Calcnu<T, MODE> nl{};
-    if ((NL || NLOUT) && active) nl.setup(px, py, pz, tx, ty, tz, a, b, sg.value(), scale);
+    if ((NL || NLOUT) && active && !P3) nl.setup(px, py, pz, tx, ty, tz, a, b, sg.value(), scale);
+    const double G3 = P3 ? sg.value() : 0.0;
+    const double2 *p3l = p3 + (P3 ? base : 0);
+    // calcnu at stored point i of this line
+    auto calcnu = [&](C v, int i) -> C {
+        if constexpr (P3 && sizeof(T) == 8 && MODE == 1) {
+            double cs, sn;
+            expmi_small(G3 * fma(v.x, v.x, v.y * v.y), cs, sn);
+            const double2 w = make_double2(fma(cs, v.x, sn * v.y), fma(cs, v.y, -sn * v.x));
+            return cmulc(w, p3l[(long long)i * s]);
+        } else {
+            return nl.apply(v, i);
+        }
+    };
     Acc<T> nacc;
     C d = mk<T>((T)0, (T)0);
     if (active) {
@@ -161,7 +177,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
                     const long long at = (long long)i * s;
                     C p = pv[q];
                     if (NL) {
-                        p = nl.apply(p, i);
+                        p = calcnu(p, i);
                         line[at] = p;
                     }
                     d = cn.fwd(p, d, mult[t]);
@@ -174,7 +190,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
     C vk = mk<T>((T)0, (T)0);
     if (active && top) {
         C pk = line[(long long)k * s];
-        if (NL) pk = nl.apply(pk, k);
+        if (NL) pk = calcnu(pk, k);
         vk = cn.fwd(pk, mk<T>(d.x + other.x, d.y + other.y), mid);
         C u = LineOps<T, MODE>::out(vk, pk);
         if (NLOUT) u = nl.apply(u, k);
@@ -217,7 +233,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
 
 constexpr int kLinesPerBlock = kSweepThreads / 2;
 
-template <typename T, int MODE, bool NL, bool NORM, bool NLOUT = false>
+template <typename T, int MODE, bool NL, bool NORM, bool NLOUT = false, bool P3 = false>
 cudaError_t sweep_launch(void *psi, void *work, const AxisTables &ax,
                          const SweepGeom &g, const NonlinArgs *nl,
                          const Partials *norm_out, cudaStream_t st)
@@ -240,10 +256,11 @@ cudaError_t sweep_launch(void *psi, void *work, const AxisTables &ax,
         mid = ax.mid32;
         if (nl) { px = nl->px32; py = nl->py32; pz = nl->pz32; }
     }
-    k_sweep<T, MODE, NL, NORM, NLOUT><<<grid, kSweepThreads, 0, st>>>(
+    k_sweep<T, MODE, NL, NORM, NLOUT, P3><<<grid, kSweepThreads, 0, st>>>(
         reinterpret_cast<C *>(psi), reinterpret_cast<C *>(work), cp, mult, mid, g, kappa,
         px, py, pz, tx, ty, tz, nl ? nl->g : StepG{}, nl ? nl->scale : nullptr,
-        norm_out ? norm_out->buf : nullptr, norm_out ? norm_out->line_weight : nullptr);
+        norm_out ? norm_out->buf : nullptr, norm_out ? norm_out->line_weight : nullptr,
+        nl ? nl->p3 : nullptr);
     return cudaGetLastError();
 }
 
@@ -383,6 +400,19 @@ k_calcnu_pass(typename CT<T>::c *__restrict__ psi, int nx, int ny, int nz,
     if (threadIdx.x == 0) partials[blockIdx.x] = r;
 }
 
+// The potential factor table P[(k ny + j) nx + i] = P_x[i] P_y[j] P_z[k].
+__global__ void k_build_pot3(double2 *__restrict__ p3, const double2 *__restrict__ px,
+                             const double2 *__restrict__ py, const double2 *__restrict__ pz,
+                             int nx, int ny, int nz)
+{
+    const long long count = (long long)nx * ny * nz;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p % nx), j = (int)((p / nx) % ny), k = (int)(p / ((long long)nx * ny));
+        p3[p] = cmulc(cmulc(py[j], pz[k]), px[i]);
+    }
+}
+
 __global__ void k_set_step(long long *step, long long value) { *step = value; }
 __global__ void k_add_step(long long *step) { *step += 1; }
 
@@ -494,6 +524,11 @@ cudaError_t launch_sweep_x(int prec, int mode, void *psi, void *work,
                            const NonlinArgs &nl, int, int, const Partials *norm_out,
                            cudaStream_t st)
 {
+    if (nl.p3) {
+        // the precomputed potential factors: FP64 real time, no norm partials
+        if (prec != kC128 || mode != 1 || norm_out) return cudaErrorInvalidValue;
+        return sweep_launch<double, 1, true, false, false, true>(psi, work, ax, g, &nl, nullptr, st);
+    }
     if (prec == kC128) return sweep_dispatch<double, true>(mode, psi, work, ax, g, &nl, norm_out, st);
     return sweep_dispatch<float, true>(mode, psi, work, ax, g, &nl, norm_out, st);
 }
@@ -581,6 +616,13 @@ cudaError_t launch_calcnu_pass(int prec, int mode, void *psi, int nx, int ny, in
         k<<<blocks, 256, 0, st>>>((float2 *)psi, nx, ny, nz, nl.px32, nl.py32, nl.pz32, nl.tx32,
                                   nl.ty32, nl.tz32, nl.g, nl.scale, norm_out.buf, wx);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_pot3(void *p3, const double2 *px, const double2 *py, const double2 *pz,
+                              int nx, int ny, int nz, cudaStream_t st)
+{
+    k_build_pot3<<<4 * kReduceBlocks, 256, 0, st>>>((double2 *)p3, px, py, pz, nx, ny, nz);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ GP_C128, GP_C64 = 0, 1
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ENONFINITE, GP_ETIMEOUT, GP_EINTERNAL, GP_EFULL = (
     0, -1, -2, -3, -4, -5, -6, -7)
 GP_MAX_EDGE = 8192
-GP_OPT_SWEEP_PATH, GP_OPT_TILE_SHAPE, GP_OPT_SPLITTING = 1, 2, 3
+GP_OPT_SWEEP_PATH, GP_OPT_TILE_SHAPE, GP_OPT_SPLITTING, GP_OPT_POTENTIAL_TABLE = 1, 2, 3, 4
 GP_PATH_AUTO, GP_PATH_EXACT, GP_PATH_TMA, GP_PATH_WINDOW = 0, 1, 2, 3
 GP_SPLIT_LIE, GP_SPLIT_STRANG = 0, 1
 

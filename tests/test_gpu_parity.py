@@ -169,3 +169,23 @@ def test_nonfinite_input_is_reported():
         with pytest.raises(gp.GPError) as e:
             s.observables()
         assert e.value.code == gp.GP_ENONFINITE
+
+
+def test_potential_table_on_and_off_agree():
+    """The FP64 real-time x sweep with the precomputed potential factors and
+    with the per-axis tables: the same step to rounding, both vs the oracle."""
+    require_gpu()
+    shape, h, dt, g = (70, 66, 40), (0.2, 0.25, 0.3), 0.003, 9.0
+    psi0 = rand_state(shape, 12)
+    out = {}
+    for on in (1, 0):
+        with gp.Solver(shape, h, dt, *W3, g, gp.GP_REAL) as s:
+            gp.gp_set_option(s.ctx, gp.GP_OPT_POTENTIAL_TABLE, on)
+            assert gp.gp_get_option(s.ctx, gp.GP_OPT_POTENTIAL_TABLE) == on
+            s.load(psi0).step(25)
+            out[on] = s.psi()
+    p = oracle_params(shape, h, dt, W3, g, 1)
+    want = psi0.copy()
+    oracle.step(p, want, 25)
+    assert rel_l2(out[1], want) <= 1e-12 and rel_l2(out[0], want) <= 1e-12
+    assert rel_l2(out[1], out[0]) <= 1e-13
