@@ -1042,7 +1042,10 @@ int gp_observables(gp_ctx *c, gp_obs *o)
     int rc0 = enqueue_observables(c);
     if (rc0) return rc0;
     int rc = read_errors(c);
-    const double *s = c->host_sums;
+    double s[gp::kObsWidth];
+    std::memcpy(s, c->host_sums, sizeof(s));
+    if (c->prec == GP_C128 && !c->axial)
+        for (int k = 6; k < 9; ++k) s[k] = 2.0 * s[0] - 2.0 * s[k];     // K_k from R_k
     const double w = cell_volume(c);
     const double n = w * s[0];
     double kin = 0.5 * (s[6] / (c->h[0] * c->h[0]) + s[7] / (c->h[1] * c->h[1]));

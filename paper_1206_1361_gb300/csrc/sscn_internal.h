@@ -158,7 +158,8 @@ cudaError_t launch_norm_partials(int prec, const void *psi, long long count,
 
 // Observables: the 9 FP64 sums (S0, Sx, Sy, Sz, SV, S4, Kx, Ky, Kz) of
 // scale * psi, one partials row per x-line, then a fixed-order finish into
-// sums[9].  x2/y2/z2 hold x_i^2 per axis, vx/vy/vz the potential terms
+// sums[9].  FP64 grids return R_k = sum Re(psi_next conj(psi)) in place of K_k
+// (the caller forms K_k = 2 S0 - 2 R_k); complex64 returns K_k.  x2/y2/z2 hold x_i^2 per axis, vx/vy/vz the potential terms
 // omega_k^2 x_i^2 / 2 (device, FP64).
 struct ObsArgs {
     int nx, ny, nz;

@@ -418,69 +418,147 @@ __global__ void k_add_step(long long *step) { *step += 1; }
 
 // ------------------------------------------------------------ observables
 //
-// One warp per x-line (j, k).  Per point: a = |psi|^2 and the forward
-// differences to the next point along x, y and z (zero beyond the last
-// stored point); the y and z coordinate factors are constant on the line, so
-// sum y^2 |psi|^2 = y_j^2 sum |psi|^2 etc. are formed once per line.  Each line
-// writes its 9 sums (times the pending scale s^2, s^4 for |psi|^4) to its own
-// partials row; two fixed-order passes add the rows, so the result does not
-// depend on the launch shape.
+// Per x-line (j, k), FP64 grids: one thread walks the line in order
+// (consecutive threads on consecutive lines; the line's points come through
+// L1).  Per point: a = |psi|^2, its x^2 and V_x weighted sums, |psi|^4, and the
+// neighbour terms along x, y and z (zero beyond the last stored point); the
+// y and z coordinate factors are constant on the line, so sum y^2 |psi|^2 =
+// y_j^2 sum |psi|^2 etc. are formed once per line.  Each line writes its 9
+// sums (times the pending scale s^2, s^4 for |psi|^4) to its own partials
+// row; two fixed-order passes add the rows, so the result does not depend on
+// the launch shape.  A thread per line keeps every sum in one thread: no
+// warp reduction per line, which on GB300 (2 FP64 FMA per clock per SM) cost
+// more than the points themselves.
+//
+// FP64: the neighbour terms are R_k = sum Re(psi_next conj(psi)) (2 FMA),
+// and the finish forms K_k = 2 S0 - 2 R_k (every point is once "next" and
+// once "current", the boundary values are zero): sum |psi_next - psi|^2
+// exactly, with a relative rounding of ~1e-14 after the cancellation.
+//
+// complex64 (FP32 terms, memory-bound) keeps a warp per line for coalesced
+// loads and the differences (the cancellation would amplify FP32 rounding past
+// the 1e-6 the form is held to); its lanes' compensated FP32 partials are
+// combined across the warp in FP32 with an error-free sum (TwoSum), not in
+// FP64, and lane 0 converts the line's totals.
 
 constexpr int kObsThreads = 256;
 constexpr int kObsChunk = 1024;          // lines per first-stage finish block
 
-template <typename T>
-__global__ void __launch_bounds__(kObsThreads)
-k_observables(const typename CT<T>::c *__restrict__ psi, ObsArgs a,
-              double *__restrict__ partials)
+// Warp sum of the values s - c (Kahan pairs) in FP32 with the rounding of
+// every addition carried (TwoSum); the total in FP64, valid in lane 0.
+__device__ __forceinline__ double warp_sum_comp(float s, float c)
 {
-    using C = typename CT<T>::c;
+    float hi = s, lo = -c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o), l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const float t = hi + h2, z = t - hi;
+        const float e = (hi - (t - z)) + (h2 - z);
+        hi = t;
+        lo = lo + l2 + e;
+    }
+    return (double)hi + (double)lo;
+}
+
+__global__ void __launch_bounds__(kObsThreads)
+k_observables_c64(const float2 *__restrict__ psi, ObsArgs a, double *__restrict__ partials)
+{
     const int lane = threadIdx.x & 31;
     const long long line = (long long)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     if (line >= (long long)ny * nz) return;       // whole warp
     const int j = (int)(line % ny), k = (int)(line / ny);
     const long long plane = (long long)nx * ny;
-    const C *row = psi + line * nx;
+    const float2 *row = psi + line * nx;
     const bool has_y = j + 1 < ny, has_z = k + 1 < nz;
-    // per-point terms in T (exact FP64 for complex128, FP32 for complex64),
-    // summed per lane by Acc<T>, then FP64 across lanes and lines
+    const float2 zero = make_float2(0.f, 0.f);
+    Acc<float> acc[7];                            // S0, Sx, SVx, S4, Kx, Ky, Kz
+    for (int i = lane; i < nx; i += 32) {
+        const float2 v = row[i];
+        const float am = fmaf(v.x, v.x, v.y * v.y);
+        acc[0].add(am);
+        acc[1].add_prod(a.x2f[i], am);
+        acc[2].add_prod(a.vxf[i], am);
+        acc[3].add_prod(am, am);
+        const float2 nb = (i + 1 < nx) ? row[i + 1] : zero;
+        acc[4].add_sq2(nb.x - v.x, nb.y - v.y);
+        const float2 ny_ = has_y ? row[i + nx] : zero;
+        acc[5].add_sq2(ny_.x - v.x, ny_.y - v.y);
+        if (nz > 1) {
+            const float2 nz_ = has_z ? row[i + plane] : zero;
+            acc[6].add_sq2(nz_.x - v.x, nz_.y - v.y);
+        }
+    }
+    double r[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) r[q] = warp_sum_comp(acc[q].s, acc[q].c);
+    if (lane == 0) {
+        const double sc = *a.scale, s2 = sc * sc, r0 = r[0];
+        double *out = partials + line * kObsWidth;
+        out[0] = s2 * r0;
+        out[1] = s2 * r[1];
+        out[2] = s2 * a.y2[j] * r0;
+        out[3] = s2 * a.z2[k] * r0;
+        out[4] = s2 * (r[2] + (a.vy[j] + a.vz[k]) * r0);
+        out[5] = s2 * s2 * r[3];
+        out[6] = s2 * r[4];
+        out[7] = s2 * r[5];
+        out[8] = s2 * r[6];
+    }
+}
+
+// Thread per line (FP64 grids).
+template <typename T>
+__global__ void __launch_bounds__(kObsThreads)
+k_observables(const typename CT<T>::c *__restrict__ psi, ObsArgs a,
+              double *__restrict__ partials)
+{
+    using C = typename CT<T>::c;
+    const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    if (line >= (long long)ny * nz) return;
+    const int j = (int)(line % ny), k = (int)(line / ny);
+    const long long plane = (long long)nx * ny;
+    const C *row = psi + line * nx;
+    const bool has_y = j + 1 < ny, has_z = nz > 1 && k + 1 < nz;
     const T *x2 = sizeof(T) == 8 ? (const T *)a.x2 : (const T *)a.x2f;
     const T *vx = sizeof(T) == 8 ? (const T *)a.vx : (const T *)a.vxf;
+    constexpr bool RFORM = sizeof(T) == 8;
     Acc<T> s0, sx, svx, s4, kx, ky, kz;
     const C zero = mk<T>((T)0, (T)0);
-    for (int i = lane; i < nx; i += 32) {
-        const C v = row[i];
+    C v = row[0];
+    for (int i = 0; i < nx; ++i) {
+        const C nb = (i + 1 < nx) ? row[i + 1] : zero;
+        const C ny_ = has_y ? row[i + nx] : zero;
+        const C nz_ = has_z ? row[i + plane] : zero;
         const T am = fma(v.x, v.x, v.y * v.y);
         s0.add(am);
         sx.add_prod(x2[i], am);
         svx.add_prod(vx[i], am);
         s4.add_prod(am, am);
-        const C nb = (i + 1 < nx) ? row[i + 1] : zero;
-        kx.add_sq2(nb.x - v.x, nb.y - v.y);
-        const C ny_ = has_y ? row[i + nx] : zero;
-        ky.add_sq2(ny_.x - v.x, ny_.y - v.y);
-        if (nz > 1) {
-            const C nz_ = has_z ? row[i + plane] : zero;
-            kz.add_sq2(nz_.x - v.x, nz_.y - v.y);
+        if constexpr (RFORM) {
+            kx.s = fma(nb.x, v.x, fma(nb.y, v.y, kx.s));
+            ky.s = fma(ny_.x, v.x, fma(ny_.y, v.y, ky.s));
+            kz.s = fma(nz_.x, v.x, fma(nz_.y, v.y, kz.s));
+        } else {
+            kx.add_sq2(nb.x - v.x, nb.y - v.y);
+            ky.add_sq2(ny_.x - v.x, ny_.y - v.y);
+            if (nz > 1) kz.add_sq2(nz_.x - v.x, nz_.y - v.y);
         }
+        v = nb;
     }
-    const double r0 = warp_sum(s0.get()), rx = warp_sum(sx.get()), rv = warp_sum(svx.get()),
-                 r4 = warp_sum(s4.get()), qx = warp_sum(kx.get()), qy = warp_sum(ky.get()),
-                 qz = warp_sum(kz.get());
-    if (lane == 0) {
-        const double sc = *a.scale, s2 = sc * sc;
-        double *out = partials + line * kObsWidth;
-        out[0] = s2 * r0;
-        out[1] = s2 * rx;
-        out[2] = s2 * a.y2[j] * r0;
-        out[3] = s2 * a.z2[k] * r0;
-        out[4] = s2 * (rv + (a.vy[j] + a.vz[k]) * r0);
-        out[5] = s2 * s2 * r4;
-        out[6] = s2 * qx;
-        out[7] = s2 * qy;
-        out[8] = s2 * qz;
-    }
+    const double sc = *a.scale, s2 = sc * sc;
+    const double r0 = s0.get();
+    double *out = partials + line * kObsWidth;
+    out[0] = s2 * r0;
+    out[1] = s2 * sx.get();
+    out[2] = s2 * a.y2[j] * r0;
+    out[3] = s2 * a.z2[k] * r0;
+    out[4] = s2 * (svx.get() + (a.vy[j] + a.vz[k]) * r0);
+    out[5] = s2 * s2 * s4.get();
+    out[6] = s2 * kx.get();
+    out[7] = s2 * ky.get();
+    out[8] = s2 * kz.get();
 }
 
 // Sum rows [b * chunk, (b + 1) * chunk) of a [rows][9] array into out[b][9].
@@ -649,13 +727,14 @@ cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
                                double *scratch, double *sums, cudaStream_t st)
 {
     const long long lines = (long long)a.ny * a.nz;
-    const long long chunks = (lines + kObsChunk - 1) / kObsChunk;
     double *rows = scratch, *stage = scratch + lines * kObsWidth;
-    const long long blocks = (lines * 32 + kObsThreads - 1) / kObsThreads;
-    if (prec == kC128)
+    if (prec == kC128) {
+        const long long blocks = (lines + kObsThreads - 1) / kObsThreads;
         k_observables<double><<<(unsigned)blocks, kObsThreads, 0, st>>>((const double2 *)psi, a, rows);
-    else
-        k_observables<float><<<(unsigned)blocks, kObsThreads, 0, st>>>((const float2 *)psi, a, rows);
+    } else {
+        const long long blocks = (lines * 32 + kObsThreads - 1) / kObsThreads;
+        k_observables_c64<<<(unsigned)blocks, kObsThreads, 0, st>>>((const float2 *)psi, a, rows);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_rows_finish(rows, lines, stage, sums, st);
