@@ -75,6 +75,7 @@ struct Inst {
     const void *ph[3];              // current-mode potential factors (Coef<T>), n entries
     const float *th[3];             // dt omega^2 x^2 / 2 (FP32) per axis
     const double *x2[3], *v[3];     // x^2, omega^2 x^2 / 2 per axis (observables)
+    const float *x2f, *vf;          // their FP32 roundings along x (complex64 observables)
     double dtg, w;
     double *scale, *norm, *partials, *obs_rows;
 };
@@ -373,12 +374,14 @@ k_batch_obs(const Inst *inst, const long long *line_pref, int N)
     const bool has_y = j + 1 < ny, has_z = k + 1 < nz;
     const C zero = mkb<T>((T)0, (T)0);
     Acc<T> s0, sx, svx, s4, kx, ky, kz;
+    const T *x2 = sizeof(T) == 8 ? (const T *)I.x2[0] : (const T *)I.x2f;
+    const T *vx = sizeof(T) == 8 ? (const T *)I.v[0] : (const T *)I.vf;
     for (int i = lane; i < nx; i += 32) {
         const C v = row[i];
         const T am = fma(v.x, v.x, v.y * v.y);
         s0.add(am);
-        sx.add_prod((T)I.x2[0][i], am);
-        svx.add_prod((T)I.v[0][i], am);
+        sx.add_prod(x2[i], am);
+        svx.add_prod(vx[i], am);
         s4.add_prod(am, am);
         const C nb = (i + 1 < nx) ? row[i + 1] : zero;
         kx.add_sq2(nb.x - v.x, nb.y - v.y);
@@ -389,9 +392,24 @@ k_batch_obs(const Inst *inst, const long long *line_pref, int N)
             kz.add_sq2(nz_.x - v.x, nz_.y - v.y);
         }
     }
-    const double r0 = warp_sum_d(s0.get()), rx = warp_sum_d(sx.get()), rv = warp_sum_d(svx.get()),
-                 r4 = warp_sum_d(s4.get()), qx = warp_sum_d(kx.get()), qy = warp_sum_d(ky.get()),
-                 qz = warp_sum_d(kz.get());
+    double r0, rx, rv, r4, qx, qy, qz;
+    if constexpr (sizeof(T) == 4) {
+        r0 = warp_sum_comp(s0.s, s0.c);
+        rx = warp_sum_comp(sx.s, sx.c);
+        rv = warp_sum_comp(svx.s, svx.c);
+        r4 = warp_sum_comp(s4.s, s4.c);
+        qx = warp_sum_comp(kx.s, kx.c);
+        qy = warp_sum_comp(ky.s, ky.c);
+        qz = warp_sum_comp(kz.s, kz.c);
+    } else {
+        r0 = warp_sum_d(s0.get());
+        rx = warp_sum_d(sx.get());
+        rv = warp_sum_d(svx.get());
+        r4 = warp_sum_d(s4.get());
+        qx = warp_sum_d(kx.get());
+        qy = warp_sum_d(ky.get());
+        qz = warp_sum_d(kz.get());
+    }
     if (lane == 0) {
         const double sc = *I.scale, s2 = sc * sc;
         double *out = I.obs_rows + line * kObsWidthB;
@@ -461,6 +479,7 @@ struct gp_batch_slot {
     void *cp[2][3]{}, *mult[2][3]{}, *ph[2][3]{};
     double *x2[3]{}, *v[3]{};
     float *th[3]{};
+    float *x2f = nullptr, *vf = nullptr;
     double *scale = nullptr, *norm = nullptr, *partials = nullptr, *obs_rows = nullptr;
     gp::AxisTables conv[2][3];      // convergence fields per mode/axis (host)
 };
@@ -534,7 +553,7 @@ int tiles_of(const gp_grid &g, int axis)
 
 // Layout of a slot's aux block (byte offsets), 256-byte aligned pieces.
 struct AuxLayout {
-    size_t cp[2][3], mult[2][3], ph[2][3], th[3], x2[3], v[3], scale, norm, partials, rows, total;
+    size_t cp[2][3], mult[2][3], ph[2][3], th[3], x2[3], v[3], x2f, vf, scale, norm, partials, rows, total;
 };
 
 AuxLayout aux_layout(const gp_grid &g, int prec)
@@ -560,6 +579,8 @@ AuxLayout aux_layout(const gp_grid &g, int prec)
         L.x2[k] = take(edge_of(g, k) * sizeof(double));
         L.v[k] = take(edge_of(g, k) * sizeof(double));
     }
+    L.x2f = take(edge_of(g, 0) * sizeof(float));
+    L.vf = take(edge_of(g, 0) * sizeof(float));
     L.scale = take(sizeof(double));
     L.norm = take(sizeof(double));
     L.partials = take((size_t)std::max(1, tiles_of(g, axes_of(g) - 1)) * sizeof(double));
@@ -626,6 +647,11 @@ int upload_slot(gp_batch *b, gp_batch_slot &s)
         std::vector<float> th(n);
         for (int i = 0; i < n; ++i) th[i] = (float)(s.dt * v[i]);
         put(L.th[k], th.data(), n * sizeof(float));
+        if (k == 0) {
+            std::vector<float> x2f(x2.begin(), x2.end()), vf(v.begin(), v.end());
+            put(L.x2f, x2f.data(), n * sizeof(float));
+            put(L.vf, vf.data(), n * sizeof(float));
+        }
     }
     const double one = 1.0;
     put(L.scale, &one, sizeof(double));
@@ -642,6 +668,8 @@ int upload_slot(gp_batch *b, gp_batch_slot &s)
         s.v[k] = reinterpret_cast<double *>(s.aux + L.v[k]);
         s.th[k] = reinterpret_cast<float *>(s.aux + L.th[k]);
     }
+    s.x2f = reinterpret_cast<float *>(s.aux + L.x2f);
+    s.vf = reinterpret_cast<float *>(s.aux + L.vf);
     s.scale = reinterpret_cast<double *>(s.aux + L.scale);
     s.norm = reinterpret_cast<double *>(s.aux + L.norm);
     s.partials = reinterpret_cast<double *>(s.aux + L.partials);
@@ -676,6 +704,8 @@ Inst make_inst(const gp_batch_slot &s, int prec)
         I.x2[k] = s.x2[k];
         I.v[k] = s.v[k];
     }
+    I.x2f = s.x2f;
+    I.vf = s.vf;
     I.dtg = s.dt * s.g;
     I.w = s.h[0] * s.h[1] * (s.grid.nz > 1 ? s.h[2] : 1.0);
     I.scale = s.scale;

@@ -33,3 +33,21 @@ template <> struct Acc<float> {
     __device__ __forceinline__ void add_sq2(float a, float b) { add(fmaf(a, a, b * b)); }
     __device__ __forceinline__ double get() const { return (double)s - (double)c; }
 };
+
+// Warp sum of the values s - c (Kahan pairs from Acc<float>) in FP32, the
+// rounding of every addition carried along (TwoSum): the total in FP64,
+// valid in lane 0.  FP64 adds across a warp would cost 16 FP64-pipe clocks
+// each on GB300.
+__device__ __forceinline__ double warp_sum_comp(float s, float c)
+{
+    float hi = s, lo = -c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o), l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const float t = hi + h2, z = t - hi;
+        const float e = (hi - (t - z)) + (h2 - z);
+        hi = t;
+        lo = lo + l2 + e;
+    }
+    return (double)hi + (double)lo;
+}

@@ -444,22 +444,6 @@ __global__ void k_add_step(long long *step) { *step += 1; }
 constexpr int kObsThreads = 256;
 constexpr int kObsChunk = 1024;          // lines per first-stage finish block
 
-// Warp sum of the values s - c (Kahan pairs) in FP32 with the rounding of
-// every addition carried (TwoSum); the total in FP64, valid in lane 0.
-__device__ __forceinline__ double warp_sum_comp(float s, float c)
-{
-    float hi = s, lo = -c;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_down_sync(0xffffffffu, hi, o), l2 = __shfl_down_sync(0xffffffffu, lo, o);
-        const float t = hi + h2, z = t - hi;
-        const float e = (hi - (t - z)) + (h2 - z);
-        hi = t;
-        lo = lo + l2 + e;
-    }
-    return (double)hi + (double)lo;
-}
-
 __global__ void __launch_bounds__(kObsThreads)
 k_observables_c64(const float2 *__restrict__ psi, ObsArgs a, double *__restrict__ partials)
 {
