@@ -167,13 +167,16 @@ __device__ __forceinline__ void expmi_small(double a, double &c, double &s)
     }
 }
 
-// cos a - 1 and sin a, each to FP32 relative accuracy
+// cos a - 1 and sin a for the update psi + (cos a - 1) psi - i sin a psi:
+// both to within 2^-25 absolute, below the FP32 rounding of the result.  For
+// |a| <= 1/16 the first dropped terms, a^6 / 720 and a^5 / 120, are below
+// 1e-10 and 8e-9.
 __device__ __forceinline__ void phase_delta(float a, float &cm1, float &s)
 {
     if (fabsf(a) <= 0.0625f) {
         const float t = a * a;
-        cm1 = t * fmaf(t, fmaf(t, -1.0f / 720, 1.0f / 24), -0.5f);
-        s = a * fmaf(t, fmaf(t, 1.0f / 120, -1.0f / 6), 1.0f);
+        cm1 = t * fmaf(t, 1.0f / 24, -0.5f);
+        s = a * fmaf(t, -1.0f / 6, 1.0f);
     } else {
         float sh, ch;
         sincosf(0.5f * a, &sh, &ch);
