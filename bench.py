@@ -62,7 +62,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=30, help="timed benchmark steps")
     ap.add_argument("--warmup", type=int, default=3, help="untimed benchmark steps")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--prep-max-steps", type=int, default=4000,
+    ap.add_argument("--prep-max-steps", type=int, default=20000,
                     help="cap on imaginary-time ground-state steps before the quench")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="budget of the oracle CPU-baseline sample")

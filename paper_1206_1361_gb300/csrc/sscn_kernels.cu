@@ -97,7 +97,10 @@ __device__ double block_sum(double v, double *red /* >= 32 doubles */)
 //   bottom: e_i  = (psi_i + kappa e_{i+1}) mult_{m+1-i}, v_i = e_i - c'_{m+1-i} v_{i-1}
 //   middle: v_k  = (psi_k + kappa (d'_{k-1} + e_{k+1})) mid,
 //           mid  = 1 / (1 + 2 kappa + kappa (c'_{k-1} + c'_{m-k})), c'_0 = 0.
-constexpr int kSweepThreads = 64;
+#ifndef GP_SWEEP_THREADS
+#define GP_SWEEP_THREADS 64
+#endif
+constexpr int kSweepThreads = GP_SWEEP_THREADS;
 #ifndef GP_SWEEP_PREFETCH
 #define GP_SWEEP_PREFETCH 4
 #endif
