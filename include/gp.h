@@ -213,12 +213,13 @@ enum {
      * (renormalisation does not commute with the nonlinear step) with a much
      * smaller error. */
     GP_OPT_SPLITTING = 3,
-    /* 1 (default): the FP64 real-time x sweep (plain splitting, exact path)
-     * reads the potential factor exp(-i dt V) of each point from a table laid
-     * out like psi, built on the first such step (one more psi-sized buffer;
-     * the sweep is bound by the FP64 pipe, and the table saves it one complex
-     * multiply per point).  0: form it from the per-axis tables and free the
-     * table. */
+    /* 1 (default): FP64 real-time steps on the exact path read the potential
+     * factor of each point from a table laid out like psi -- exp(-i dt V) for
+     * the plain splitting's x sweep, exp(-i dt V / 2) for both half steps of
+     * the symmetric one -- built on the first such step (one more psi-sized
+     * buffer per splitting used; the sweeps are bound by the FP64 pipe, and
+     * the table saves one complex multiply per point).  0: form it from the
+     * per-axis tables and free the tables. */
     GP_OPT_POTENTIAL_TABLE = 4
 };
 /* GP_PATH_WINDOW (axial form): each line cut into cores solved in parallel,

@@ -50,7 +50,8 @@ struct gp_ctx {
     // FP64 real-time potential factor table (one psi-sized buffer, built on
     // the first real-time step that uses it)
     int pot_table = 1;
-    double2 *pot3 = nullptr;
+    double2 *pot3 = nullptr;        // exp(-i dt V) per point (plain splitting)
+    double2 *pot3h = nullptr;       // exp(-i dt V / 2) per point (symmetric splitting)
     double *partials = nullptr;     // norm partials, >= max sweep blocks
     int partial_cap = 0;
     double *obs_partials = nullptr; // observables scratch (rows + finish stage)
@@ -401,6 +402,7 @@ void release(gp_ctx *c)
     fr(c->pbuf);
     fr(c->wscr);
     fr(c->pot3);
+    fr(c->pot3h);
     fr(c->partials);
     fr(c->obs_partials);
     fr(c->obs_tab);
@@ -490,22 +492,30 @@ gp::NonlinArgs pointwise_args(const gp_ctx *c, int axis, bool half, double fa, d
     return nl;
 }
 
-// The FP64 real-time plain-splitting x sweep on the exact path reads its
-// potential factors from the precomputed table.
+// FP64 real-time steps on the exact path read their potential factors from a
+// precomputed table: the full-step one for the plain splitting's x sweep, the
+// half-step one for both half steps of the symmetric splitting.
 bool uses_pot3(const gp_ctx *c)
 {
-    return c->pot_table && c->prec == GP_C128 && c->mode == GP_REAL && c->split == GP_SPLIT_LIE &&
-           !c->axial && sweep_path(c, 0) == GP_PATH_EXACT;
+    if (!c->pot_table || c->prec != GP_C128 || c->mode != GP_REAL || c->axial) return false;
+    for (int k = 0; k < naxes(c->grid); ++k)
+        if (sweep_path(c, k) != GP_PATH_EXACT) return false;
+    return true;
 }
 
-// Allocate and fill the table if this step needs it (never under stream capture).
+double2 *pot3_for(const gp_ctx *c) { return c->split == GP_SPLIT_STRANG ? c->pot3h : c->pot3; }
+
+// Allocate and fill the table this step needs (never under stream capture).
 int prepare_pot3(gp_ctx *c)
 {
-    if (!uses_pot3(c) || c->pot3) return GP_OK;
-    int rc = alloc(c, (void **)&c->pot3, (size_t)points(c->grid) * sizeof(double2));
+    if (!uses_pot3(c) || pot3_for(c)) return GP_OK;
+    const bool half = c->split == GP_SPLIT_STRANG;
+    double2 **slot = half ? &c->pot3h : &c->pot3;
+    int rc = alloc(c, (void **)slot, (size_t)points(c->grid) * sizeof(double2));
     if (rc) return rc;
-    GP_CK(c, gp::launch_build_pot3(c->pot3, c->ph[GP_REAL][0], c->ph[GP_REAL][1], c->ph[GP_REAL][2],
-                                   c->grid.nx, c->grid.ny, c->grid.nz, c->stream));
+    double2 *const *P = half ? c->phh[GP_REAL] : c->ph[GP_REAL];
+    GP_CK(c, gp::launch_build_pot3(*slot, P[0], P[1], P[2], c->grid.nx, c->grid.ny, c->grid.nz,
+                                   c->stream));
     return GP_OK;
 }
 
@@ -527,9 +537,12 @@ int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
     const int last = three_d ? 2 : 1;
     Partials part{c->partials, 1, c->axial ? c->rho_w : nullptr};
     gp::NonlinArgs nl = pointwise_args(c, 0, strang, 0.0, strang ? 0.5 : 1.0, c->scale);
-    if (uses_pot3(c) && c->pot3) nl.p3 = c->pot3;
-    const gp::NonlinArgs nl2 =
+    gp::NonlinArgs nl2 =
         pointwise_args(c, imag ? 0 : last, true, 0.5, 1.0, imag ? c->scale : nullptr);
+    if (uses_pot3(c) && pot3_for(c)) {
+        nl.p3 = pot3_for(c);
+        if (!imag) nl2.p3 = pot3_for(c);
+    }
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], c->stream) : cudaSuccess; };
     GP_CK(c, mark(0));
     int last_blocks = 0;
@@ -1128,10 +1141,11 @@ int gp_set_option(gp_ctx *c, int option, int value)
     if (option == GP_OPT_POTENTIAL_TABLE) {
         if (value != 0 && value != 1) return fail(c, GP_EINVAL, "gp_set_option: potential table is 0 or 1");
         c->pot_table = value;
-        if (!value && c->pot3) {
+        if (!value && (c->pot3 || c->pot3h)) {
             cudaStreamSynchronize(c->stream);
             cudaFree(c->pot3);
-            c->pot3 = nullptr;
+            cudaFree(c->pot3h);
+            c->pot3 = c->pot3h = nullptr;
         }
         drop_graph(c);
         return GP_OK;

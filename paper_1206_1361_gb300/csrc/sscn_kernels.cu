@@ -196,7 +196,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
         if (NL) pk = calcnu(pk, k);
         vk = cn.fwd(pk, mk<T>(d.x + other.x, d.y + other.y), mid);
         C u = LineOps<T, MODE>::out(vk, pk);
-        if (NLOUT) u = nl.apply(u, k);
+        if (NLOUT) u = calcnu(u, k);
         line[(long long)k * s] = u;
         if (NORM) nacc.add(abs2<T>(u));
     }
@@ -219,7 +219,7 @@ k_sweep(typename CT<T>::c *__restrict__ psi, typename CT<T>::c *__restrict__ wor
                     const long long at = (long long)(top ? 1 + t : m - t) * s;
                     v = cn.back(wv[q], cp[t], v);
                     C u = LineOps<T, MODE>::out(v, lv[q]);
-                    if (NLOUT) u = nl.apply(u, top ? 1 + t : m - t);
+                    if (NLOUT) u = calcnu(u, top ? 1 + t : m - t);
                     line[at] = u;
                     if (NORM) nacc.add(abs2<T>(u));
                 }
@@ -607,7 +607,10 @@ cudaError_t launch_sweep_yz(int prec, int mode, void *psi, void *work,
         // last sweep stores (imaginary time takes a separate pass after the
         // renormalisation)
         if (mode != 1 || norm_out) return cudaErrorInvalidValue;
-        if (prec == kC128) return sweep_launch<double, 1, false, false, true>(psi, work, ax, g, nlout, nullptr, st);
+        if (prec == kC128) {
+            if (nlout->p3) return sweep_launch<double, 1, false, false, true, true>(psi, work, ax, g, nlout, nullptr, st);
+            return sweep_launch<double, 1, false, false, true>(psi, work, ax, g, nlout, nullptr, st);
+        }
         return sweep_launch<float, 1, false, false, true>(psi, work, ax, g, nlout, nullptr, st);
     }
     if (prec == kC128) return sweep_dispatch<double, false>(mode, psi, work, ax, g, nullptr, norm_out, st);
