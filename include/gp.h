@@ -162,6 +162,11 @@ int gp_sync(gp_ctx *ctx);
  */
 int gp_device_psi(gp_ctx *ctx, void **dev_ptr);
 
+/* Apply the pending imaginary-time scale 1 / sqrt(N) to the device buffer
+ * (enqueued on the context's stream), so gp_device_psi holds normalised
+ * values; a no-op when none is pending. */
+int gp_apply_pending_scale(gp_ctx *ctx);
+
 /*
  * One Crank-Nicolson sweep along `axis` (0 x, 1 y, 2 z; 3D only for z),
  * (I - kappa L) u = (I + kappa L) psi on every line with kappa = dt / (4 h^2)

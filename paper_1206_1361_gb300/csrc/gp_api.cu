@@ -1309,6 +1309,12 @@ int gp_sync(gp_ctx *c)
     return read_errors(c);
 }
 
+int gp_apply_pending_scale(gp_ctx *c)
+{
+    if (!c) return fail(nullptr, GP_EINVAL, "gp_apply_pending_scale: null context");
+    return materialize_scale(c);
+}
+
 int gp_device_psi(gp_ctx *c, void **p)
 {
     if (!c || !p) return fail(c, GP_EINVAL, "gp_device_psi: null argument");

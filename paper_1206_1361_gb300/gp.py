@@ -64,6 +64,7 @@ SIGNATURES = {
     "gp_sync": (_int, [_vp]),
     "gp_set_option": (_int, [_vp, _int, _int]),
     "gp_set_modulation": (_int, [_vp, _dbl, _dbl]),
+    "gp_apply_pending_scale": (_int, [_vp]),
     "gp_create_axial": (_int, [_int, _int, _dbl, _dbl, _dbl, _dbl, _dbl, _dbl, _int, _int, _vp,
                                ctypes.POINTER(_vp)]),
     "gp_footprint_axial": (_int, [_int, _int, _int, ctypes.POINTER(ctypes.c_size_t)]),
@@ -240,6 +241,20 @@ def gp_launches_per_step(ctx):
     return k.value, o.value
 
 
+def gp_apply_pending_scale(ctx):
+    """Apply any pending imaginary-time renormalisation to the device psi."""
+    _err(ctx, load_library().gp_apply_pending_scale(ctx))
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ of a device buffer the context owns."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
 def gp_set_modulation(ctx, g1, omega):
     """g(t) = g + g1 cos(omega t) from the next step on (g1 = 0: off)."""
     _err(ctx, load_library().gp_set_modulation(ctx, float(g1), float(omega)))
@@ -375,6 +390,17 @@ class Solver:
 
     def sync(self):
         gp_sync(self.ctx)
+
+    def device_view(self):
+        """A torch CUDA tensor that borrows the context's psi buffer (no copy;
+        valid until close), normalised: any pending imaginary-time scale is
+        applied first.  Steps taken later update it in place."""
+        import torch
+        gp_apply_pending_scale(self.ctx)
+        gp_sync(self.ctx)
+        typestr = "<c16" if self.precision == GP_C128 else "<c8"
+        return torch.as_tensor(_DeviceArray(gp_device_psi(self.ctx), self.array_shape, typestr),
+                               device="cuda")
 
     def set_path(self, path):
         gp_set_option(self.ctx, GP_OPT_SWEEP_PATH, path)

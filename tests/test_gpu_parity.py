@@ -189,3 +189,17 @@ def test_potential_table_on_and_off_agree():
     oracle.step(p, want, 25)
     assert rel_l2(out[1], want) <= 1e-12 and rel_l2(out[0], want) <= 1e-12
     assert rel_l2(out[1], out[0]) <= 1e-13
+
+
+def test_device_view_borrows_the_context_buffer():
+    require_gpu()
+    import torch
+    shape = (24, 20, 18)
+    with gp.Solver(shape, (0.4, 0.4, 0.4), 0.01, *W3, 3.0, gp.GP_IMAG) as s:
+        s.load(None).step(7)
+        v = s.device_view()
+        assert v.is_cuda and v.dtype == torch.complex128 and tuple(v.shape) == (18, 20, 24)
+        assert np.array_equal(v.cpu().numpy(), s.psi())
+        s.step(3).sync()
+        s.load(None)
+        assert v.data_ptr() == gp.gp_device_psi(s.ctx)
