@@ -396,9 +396,14 @@ def run_ours(args):
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             psi0 = host.numpy().reshape(case.shape[::-1]).copy()
             v, n, cores = oracle_sample(case, psi0, args.cpu_seconds)
+            import oracle
+            oracle.set_threads(1)
+            v1, n1, _ = oracle_sample(case, psi0, min(4.0, args.cpu_seconds))
+            oracle.set_threads(cores)
             cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": "FP64 CPU oracle, %d SSCN steps of the same 256^3 real-time "
-                             "state, observables every 10th" % n}
+                             "state, observables every 10th" % n,
+                   "single_core": {"value": v1, "steps": n1}}
 
         forms = None
         if world == 1 and not args.no_forms:
