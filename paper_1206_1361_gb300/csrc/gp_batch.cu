@@ -4,7 +4,7 @@
 // Work is a queue of items (step s, phase p, instance i, tile t) in that
 // order: phases are the x, y and z Crank-Nicolson sweeps (calclux, calcluy,
 // calcluz; calcnu fused into x) and, in imaginary time, the norm finish
-// (calcnorm).  A tile is 32 lines of one instance along one axis.  Resident
+// (calcnorm).  A tile is 16 lines of one instance along one axis.  Resident
 // CTAs pop items from an atomic counter; before working on an item a CTA
 // waits until every item of the same instance's previous phase has
 // completed (a per-instance completion counter; the wait is bounded by
@@ -13,7 +13,8 @@
 // no grid-wide barrier separates the sweeps.
 //
 // Tile solver: one warp, 16 lines staged in shared memory (coalesced loads:
-// rows for x tiles, one point of 16 neighbouring lines at a time for y / z),
+// rows for x tiles, 16-byte pieces of columns of 16 neighbouring lines for
+// y / z),
 // each line eliminated from both ends by a lane pair in place (the right-hand
 // side (1 - 2 kappa) psi_i + kappa (psi_{i-1} + psi_{i+1}) formed on the fly,
 // forward elimination overwriting psi with d', the pair meeting at the middle
@@ -109,14 +110,21 @@ __device__ __forceinline__ int ld_acquire(const int *p)
     return v;
 }
 
+__device__ __forceinline__ void red_release_add(int *p, int v)
+{
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ bool wait_done(const int *ctr, int need, const int *abort_flag)
 {
     if (ld_acquire(ctr) >= need) return true;
     const uint64_t t0 = gtime();
+    unsigned ns = 32;                      // polling interval, doubled up to 512 ns
     while (ld_acquire(ctr) < need) {
         if (*(volatile const int *)abort_flag) return false;
         if (gtime() - t0 > kWaitNs) return false;
-        __nanosleep(64);
+        __nanosleep(ns);
+        ns = min(2 * ns, 512u);
     }
     return true;
 }
@@ -144,17 +152,20 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
-// The exact line update of a lane pair, in place on row[0 .. n-1] (shared
-// memory; point 0 and the virtual point n are zero).  The top lane eliminates
+// The exact line update of a lane pair, in place on row[0], row[es], ...,
+// row[(n-1) es] (shared memory, element stride es; point 0 and the virtual
+// point n are zero).  The top lane eliminates
 // i = 1 .. k-1, the bottom lane i = m .. k+1 with the mirrored tables (the
 // matrix is symmetric Toeplitz), the top lane closes the middle row k =
-// ceil(m / 2), and both back-substitute outward.  calcnu first for x tiles
-// (nl), the norm contribution of the result into acc when norm.  Every lane
-// of the warp calls this (the shuffles need them all); `active` marks lanes
-// with a line.
-template <typename T, int MODE>
-__device__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int n, long long line,
-                            bool top, bool active, bool nl, bool norm, Acc<T> &acc)
+// ceil(m / 2), and both back-substitute outward.  NL (x tiles): calcnu on
+// each point as the forward elimination reads it (the elimination keeps
+// only d', so the updated point is never stored; the middle point is
+// computed by both lanes).  The norm contribution of the result goes into
+// acc when norm.  Every lane of the warp calls this (the shuffles need them
+// all); `active` marks lanes with a line.
+template <typename T, int MODE, bool NL>
+__device__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int es, int n,
+                            long long line, bool top, bool active, bool norm, Acc<T> &acc)
 {
     using C = typename BC<T>::c;
     using F = typename Coef<T>::t;
@@ -174,29 +185,42 @@ __device__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int
         minf = I.minf32[axis];
         mid = I.mid32[axis];
     }
-    if (nl) {
-        if (active) {
-            // x line: j = line % ny, k = line / ny
-            const int j = (int)(line % I.n[1]), kz = (int)(line / I.n[1]);
-            Calcnu<T, MODE> cu{};
-            cu.setup(static_cast<const F *>(I.ph[0]), static_cast<const F *>(I.ph[1]),
-                     static_cast<const F *>(I.ph[2]), I.th[0], I.th[1], I.th[2], j, kz, I.dtg,
-                     I.scale);
-            for (int i = top ? 1 : k + 1; i <= (top ? k : m); ++i) row[i] = cu.apply(row[i], i);
-        }
-        __syncwarp();
+    Calcnu<T, MODE> cu{};
+    if (NL && active) {
+        // x line: j = line % ny, k = line / ny
+        const int j = (int)(line % I.n[1]), kz = (int)(line / I.n[1]);
+        cu.setup(static_cast<const F *>(I.ph[0]), static_cast<const F *>(I.ph[1]),
+                 static_cast<const F *>(I.ph[2]), I.th[0], I.th[1], I.th[2], j, kz, I.dtg, I.scale);
     }
     const C zero = mkb<T>((T)0, (T)0);
     const int len = top ? k - 1 : m - k;
-    const int dir = top ? 1 : -1;
+    const int dir = top ? es : -es, di = top ? 1 : -1;
+    // entries t >= conv of both tables are the constants minf / cinf: the
+    // recurrences run a table part and a constant part, so most points load
+    // no coefficient (a per-point table load sits on the recurrence's
+    // dependency chain)
+    const int tc = min(conv, len);
     C prev = zero, cur = zero, d = zero;
     if (active) {
-        cur = row[top ? 1 : m];
-        for (int t = 0; t < len; ++t) {
-            const int pos = top ? 1 + t : m - t;
-            const C next = row[pos + dir];
-            d = cn.fwd(cn.rhs(prev, cur, next), d, t < conv ? mult[t] : minf);
-            row[pos] = d;
+        C *p = row + (top ? 1 : m) * es;
+        int i = top ? 1 : m;               // point index of *p
+        cur = *p;
+        if (NL) cur = cu.apply(cur, i);
+        int t = 0;
+        for (; t < tc; ++t, p += dir, i += di) {
+            C next = p[dir];
+            if (NL) next = cu.apply(next, i + di);
+            d = cn.fwd(cn.rhs(prev, cur, next), d, mult[t]);
+            *p = d;
+            prev = cur;
+            cur = next;
+        }
+#pragma unroll 4
+        for (; t < len; ++t, p += dir, i += di) {
+            C next = p[dir];
+            if (NL) next = cu.apply(next, i + di);
+            d = cn.fwd(cn.rhs(prev, cur, next), d, minf);
+            *p = d;
             prev = cur;
             cur = next;
         }
@@ -207,16 +231,23 @@ __device__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int
     C vk = zero;
     if (active && top) {
         vk = cn.fwd(cn.rhs(prev, cur, o_prev), mkb<T>(d.x + o_d.x, d.y + o_d.y), mid);
-        row[k] = vk;
+        row[k * es] = vk;
         if (norm) acc.add(fma(vk.x, vk.x, vk.y * vk.y));
     }
     const C o_vk = mkb<T>(__shfl_xor_sync(0xffffffffu, vk.x, 16), __shfl_xor_sync(0xffffffffu, vk.y, 16));
     C u = top ? vk : o_vk;
     if (active) {
-        for (int t = len - 1; t >= 0; --t) {
-            const int pos = top ? 1 + t : m - t;
-            u = cn.back(row[pos], t < conv ? cp[t] : cinf, u);
-            row[pos] = u;
+        int t = len - 1;
+        C *p = row + (top ? 1 + t : m - t) * es;
+#pragma unroll 4
+        for (; t >= tc; --t, p -= dir) {
+            u = cn.back(*p, cinf, u);
+            *p = u;
+            if (norm) acc.add(fma(u.x, u.x, u.y * u.y));
+        }
+        for (; t >= 0; --t, p -= dir) {
+            u = cn.back(*p, cp[t], u);
+            *p = u;
             if (norm) acc.add(fma(u.x, u.x, u.y * u.y));
         }
     }
@@ -232,6 +263,13 @@ __device__ __forceinline__ void line_geom(const Inst &I, int axis, long long L, 
     else { base = L; stride = nx * ny; }
 }
 
+// A tile in shared memory: x tiles row-major (line r at sm + r P, odd pitch
+// P: lane r's column accesses hit distinct banks), y / z tiles column-major
+// (point c of the 16 lines at sm + 16 c): neighbouring y / z lines are
+// neighbouring in memory, so a full tile of 16 consecutive lines moves as
+// 16 * sizeof(C)-byte columns in 16-byte pieces (32 / sizeof(C) columns per
+// warp instruction); other y / z tiles (a row of lines ending inside the
+// tile, a partial last tile, odd nx) go point by point.
 template <typename T>
 __device__ void sweep_tile(const Inst &I, int axis, int tile, typename BC<T>::c *sm, int lane)
 {
@@ -245,33 +283,60 @@ __device__ void sweep_tile(const Inst &I, int axis, int tile, typename BC<T>::c 
     const int r = lane & (kTileLines - 1);
     const bool top = lane < kTileLines, active = r < rows;
     C *psi = static_cast<C *>(I.psi);
-    long long base = 0, stride = 0;
     constexpr int B = (int)sizeof(C);
+    constexpr int Q = B;                   // 16-byte pieces per column (16 lines)
+    constexpr int E = 16 / B;              // elements per piece
+    long long base = 0, stride = 0, base0 = 0;
     // y / z tiles: the lane pair of line r moves the two halves of its line
     const int c_lo = top ? 0 : n / 2, c_hi = top ? n / 2 : n;
+    bool wide = false;
     if (axis == 0) {
         for (int rr = 0; rr < rows; ++rr) {
             const C *src = psi + (L0 + rr) * I.n[0];
             for (int c = lane; c < n; c += 32) cp_async<B>(&sm[rr * P + c], &src[c]);
         }
-    } else if (active) {
-        line_geom(I, axis, L0 + r, base, stride);
-        for (int c = c_lo; c < c_hi; ++c) cp_async<B>(&sm[r * P + c], &psi[base + c * stride]);
+    } else {
+        line_geom(I, axis, L0, base0, stride);
+        // 16 lines at unit spacing, every column starting on 16 bytes
+        wide = rows == kTileLines && (axis == 2 || (L0 % I.n[0]) + kTileLines <= I.n[0]) &&
+               ((base0 * B) & 15) == 0 && ((stride * B) & 15) == 0;
+        if (wide) {
+            const C *src = psi + base0 + (lane % Q) * E;
+            C *dst = sm + (lane % Q) * E;
+            for (int c = lane / Q; c < n; c += 32 / Q)
+                cp_async<16>(dst + c * kTileLines, src + c * stride);
+        } else if (active) {
+            line_geom(I, axis, L0 + r, base, stride);
+            for (int c = c_lo; c < c_hi; ++c) cp_async<B>(&sm[c * kTileLines + r], &psi[base + c * stride]);
+        }
     }
     cp_async_wait_all();
     __syncwarp();
     const bool norm = I.mode == 0 && axis == I.last_axis;
+    C *row = axis == 0 ? sm + r * P : sm + r;
+    const int es = axis == 0 ? 1 : kTileLines;
     Acc<T> acc;
-    if (I.mode == 0) solve_line2<T, 0>(I, axis, sm + r * P, n, L0 + r, top, active, axis == 0, norm, acc);
-    else solve_line2<T, 1>(I, axis, sm + r * P, n, L0 + r, top, active, axis == 0, false, acc);
+    if (axis == 0) {
+        if (I.mode == 0) solve_line2<T, 0, true>(I, axis, row, es, n, L0 + r, top, active, norm, acc);
+        else solve_line2<T, 1, true>(I, axis, row, es, n, L0 + r, top, active, false, acc);
+    } else {
+        if (I.mode == 0) solve_line2<T, 0, false>(I, axis, row, es, n, L0 + r, top, active, norm, acc);
+        else solve_line2<T, 1, false>(I, axis, row, es, n, L0 + r, top, active, false, acc);
+    }
     __syncwarp();
     if (axis == 0) {
         for (int rr = 0; rr < rows; ++rr) {
             C *dst = psi + (L0 + rr) * I.n[0];
             for (int c = lane; c < n; c += 32) dst[c] = sm[rr * P + c];
         }
+    } else if (wide) {
+        C *dst = psi + base0 + (lane % Q) * E;
+        const C *src = sm + (lane % Q) * E;
+        for (int c = lane / Q; c < n; c += 32 / Q)
+            *reinterpret_cast<float4 *>(dst + c * stride) =
+                *reinterpret_cast<const float4 *>(src + c * kTileLines);
     } else if (active) {
-        for (int c = c_lo; c < c_hi; ++c) psi[base + c * stride] = sm[r * P + c];
+        for (int c = c_lo; c < c_hi; ++c) psi[base + c * stride] = sm[c * kTileLines + r];
     }
     if (norm) {
         const double v = warp_sum_d(acc.get());
@@ -299,6 +364,27 @@ __device__ void norm_item(const Inst &I, int lane, int *err)
     }
 }
 
+// The instance owning item r of a phase: the largest a with pr[a] <= r
+// (pr non-decreasing, pr[0] = 0 <= r < pr[N]).  The warp samples up to 32
+// entries per round and a ballot picks the last one <= r (a prefix, pr being
+// sorted), so a search over N instances takes ceil(log32(N + 1)) dependent
+// loads instead of log2(N).
+__device__ __forceinline__ int find_instance(const int *pr, int N, int r, int lane)
+{
+    int lo = 0, span = N + 1;              // the answer lies in [lo, lo + span)
+    for (;;) {
+        const int S = span > 32 ? (span + 31) >> 5 : 1;
+        const int idx = lo + lane * S;
+        const bool ok = idx < lo + span && pr[idx] <= r;
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        const int j = 31 - __clz(bal);     // lane 0 always votes yes: pr[lo] <= r
+        const int nlo = lo + j * S;
+        if (S == 1) return nlo;
+        span = min(S, lo + span - nlo);
+        lo = nlo;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(32) k_batch_steps(const LaunchArgs A)
 {
@@ -318,13 +404,7 @@ __global__ void __launch_bounds__(32) k_batch_steps(const LaunchArgs A)
         int p = 0;
         while (r >= A.phase_total[p]) r -= A.phase_total[p++];
         const int *pr = A.pref + p * (A.N + 1);
-        int lo = 0, hi = A.N;                  // pr[lo] <= r < pr[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (pr[mid] <= r) lo = mid;
-            else hi = mid;
-        }
-        const int i = lo, tile = (int)(r - pr[lo]);
+        const int i = find_instance(pr, A.N, (int)r, lane), tile = (int)(r - pr[i]);
         const Inst &I = A.inst[i];
         const int need = s * A.tot[i] + A.cum[i * 4 + p];
         int ok = 1;
@@ -337,13 +417,15 @@ __global__ void __launch_bounds__(32) k_batch_steps(const LaunchArgs A)
             }
             break;
         }
+        // lane 0's acquire, then the warp barrier (which orders memory among
+        // its lanes), make the previous phase's stores visible to every lane
         __syncwarp();
-        __threadfence();
         if (p < 3) sweep_tile<T>(I, p, tile, sm, lane);
         else norm_item(I, lane, A.err);
+        // the barrier orders every lane's stores before lane 0's release,
+        // which carries them (cumulatively) to the waiting warps
         __syncwarp();
-        __threadfence();
-        if (lane == 0) atomicAdd(&A.done[i], 1);
+        if (lane == 0) red_release_add(&A.done[i], 1);
     }
 }
 
@@ -800,7 +882,6 @@ int prepare(gp_batch *b)
     A.head = b->d_head;
     b->smem = (size_t)kTileLines * maxP * elem(b->prec);
     b->obs_lines = lpref[N];
-    // persistent grid: as many warps as stay resident
     int per_sm = 0, sms = 0, dev = 0;
     GP_BCK(b, cudaGetDevice(&dev));
     GP_BCK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -811,7 +892,15 @@ int prepare(gp_batch *b)
         GP_BCK(b, cudaFuncSetAttribute(k_batch_steps<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
         GP_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_steps<float>, 32, b->smem));
     }
-    b->grid = std::max(1, per_sm) * sms;
+    // persistent grid: every resident warp, but no more than twice the
+    // widest phase.  Warps beyond that would only hold later items and poll
+    // their dependency counters, which with a few small instances left (the
+    // tail of a batch of solves) crowds the L2 around the counters that the
+    // working warps update.
+    long long widest = 1;
+    for (int p = 0; p < 3; ++p) widest = std::max(widest, ptot[p]);
+    b->grid = (int)std::min<long long>((long long)std::max(1, per_sm) * sms,
+                                       std::max<long long>(sms, 2 * widest));
     b->dirty = false;
     return GP_OK;
 }

@@ -497,10 +497,13 @@ def gp_batch_step(b, n):
     _berr(b, load_library().gp_batch_step(b, int(n)))
 
 
-def gp_batch_observables(b, capacity):
-    """List of capacity dicts, one per slot id (step == -1: unused slot)."""
+def gp_batch_observables(b, capacity, slots=None):
+    """List of capacity dicts, one per slot id (step == -1: unused slot); with
+    `slots`, a dict of those slots' entries only (no conversion of the rest)."""
     arr = (gp_obs * max(1, capacity))()
     _berr(b, load_library().gp_batch_observables(b, arr, int(capacity)))
+    if slots is not None:
+        return {s: arr[s].as_dict() for s in slots}
     return [arr[i].as_dict() for i in range(capacity)]
 
 
@@ -548,8 +551,7 @@ class Batch:
 
     def observables(self):
         cap = max(self.shapes) + 1 if self.shapes else 0
-        obs = gp_batch_observables(self.b, cap)
-        return {s: obs[s] for s in self.shapes}
+        return gp_batch_observables(self.b, cap, list(self.shapes))
 
     def psi(self, slot):
         nx, ny, nz = self.shapes[slot]

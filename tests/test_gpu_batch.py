@@ -18,6 +18,8 @@ INSTANCES = [
     ((40, 24, 56), (0.25, 0.35, 0.2), 0.002, (2.0, 0.8, 1.5), 3.0, 1),
     ((96, 64, 1), (0.15, 0.2, 1.0), 0.002, (1.0, 2.0, 0.0), 40.0, 0),
     ((48, 48, 48), (0.25, 0.25, 0.25), 0.003, (1.0, 1.0, 1.0), 0.0, 0),
+    # odd nx: y tiles move point by point, z tiles as 16-byte column pieces
+    ((33, 20, 18), (0.3, 0.3, 0.35), 0.004, (1.2, 1.0, 1.4), 6.0, 1),
 ]
 
 
