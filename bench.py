@@ -160,12 +160,13 @@ KERNEL_SOURCES = ("sscn_kernels.cu", "sscn_tma.cu", "sscn_axial.cu", "gp_batch.c
                   "sscn_line.cuh", "sscn_coef.cuh", "sscn_accum.cuh")
 
 
-def kernel_source_sha():
-    """Hash of the sources that define the sweep and observables kernels; a
-    committed ncu traffic figure is used only while it matches."""
+def kernel_source_sha(files=KERNEL_SOURCES):
+    """Hash of kernel sources under csrc/.  An ncu summary names the files its
+    kernels are compiled from (`kernel_sources:`) and their hash at capture
+    (`kernel_source_sha:`); its traffic figure is used only while they match."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1206_1361_gb300", "csrc")
-    for fn in KERNEL_SOURCES:
+    for fn in files:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -173,21 +174,23 @@ def kernel_source_sha():
 
 def profiled_traffic(kernel, workload_name):
     """DRAM bytes per launch of `kernel` from a committed ncu summary under
-    profiles/, if it was taken on the current kernel sources; else None."""
+    profiles/, if it was taken on the current sources of that kernel; else
+    None."""
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None
-    sha = kernel_source_sha()
     for fn in sorted(os.listdir(pdir)):
         if not fn.endswith((".md", ".txt")):
             continue
         text = open(os.path.join(pdir, fn)).read()
-        m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-        if not m_sha or m_sha.group(1) != sha:
-            continue
         m = re.search(r"traffic\[%s@%s\]:\s*([0-9.eE+]+)" % (re.escape(kernel),
                                                            re.escape(workload_name)), text)
-        if m:
+        if not m:
+            continue
+        m_src = re.search(r"kernel_sources:\s*(.+)", text)
+        files = tuple(m_src.group(1).split()) if m_src else KERNEL_SOURCES
+        m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+        if m_sha and m_sha.group(1) == kernel_source_sha(files):
             return float(m.group(1))
     return None
 

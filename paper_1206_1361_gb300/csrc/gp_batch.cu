@@ -58,6 +58,7 @@ constexpr int kTileLines = 16;
 constexpr int kObsWidthB = gp::kObsWidth;
 constexpr int kMaxEdge32 = 512, kMaxEdge64 = 384;
 constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr unsigned kPollMaxNs = 512;
 
 // Device descriptor of one active instance.
 struct Inst {
@@ -119,12 +120,12 @@ __device__ bool wait_done(const int *ctr, int need, const int *abort_flag)
 {
     if (ld_acquire(ctr) >= need) return true;
     const uint64_t t0 = gtime();
-    unsigned ns = 32;                      // polling interval, doubled up to 512 ns
+    unsigned ns = 32;                      // polling interval, doubled up to kPollMaxNs
     while (ld_acquire(ctr) < need) {
         if (*(volatile const int *)abort_flag) return false;
         if (gtime() - t0 > kWaitNs) return false;
         __nanosleep(ns);
-        ns = min(2 * ns, 512u);
+        ns = min(2 * ns, kPollMaxNs);
     }
     return true;
 }
@@ -164,7 +165,7 @@ __device__ __forceinline__ double warp_sum_d(double v)
 // acc when norm.  Every lane of the warp calls this (the shuffles need them
 // all); `active` marks lanes with a line.
 template <typename T, int MODE, bool NL>
-__device__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int es, int n,
+__device__ __forceinline__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int es, int n,
                             long long line, bool top, bool active, bool norm, Acc<T> &acc)
 {
     using C = typename BC<T>::c;
@@ -215,7 +216,25 @@ __device__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int
             prev = cur;
             cur = next;
         }
-#pragma unroll 4
+        // constant part in groups of 4: a group's points (and their calcnu)
+        // are read before any of its results is stored, so the loads and the
+        // calcnu arithmetic overlap the recurrence
+        for (; t + 4 <= len; t += 4, p += 4 * dir, i += 4 * di) {
+            C nx[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nx[q] = p[(q + 1) * dir];
+            if (NL) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) nx[q] = cu.apply(nx[q], i + (q + 1) * di);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                d = cn.fwd(cn.rhs(prev, cur, nx[q]), d, minf);
+                p[q * dir] = d;
+                prev = cur;
+                cur = nx[q];
+            }
+        }
         for (; t < len; ++t, p += dir, i += di) {
             C next = p[dir];
             if (NL) next = cu.apply(next, i + di);
@@ -239,7 +258,18 @@ __device__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int
     if (active) {
         int t = len - 1;
         C *p = row + (top ? 1 + t : m - t) * es;
-#pragma unroll 4
+        // likewise in groups of 4 (each d' is read before its u is stored)
+        for (; t - 3 >= tc; t -= 4, p -= 4 * dir) {
+            C dv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dv[q] = p[-q * dir];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                u = cn.back(dv[q], cinf, u);
+                p[-q * dir] = u;
+                if (norm) acc.add(fma(u.x, u.x, u.y * u.y));
+            }
+        }
         for (; t >= tc; --t, p -= dir) {
             u = cn.back(*p, cinf, u);
             *p = u;
@@ -271,7 +301,7 @@ __device__ __forceinline__ void line_geom(const Inst &I, int axis, long long L, 
 // warp instruction); other y / z tiles (a row of lines ending inside the
 // tile, a partial last tile, odd nx) go point by point.
 template <typename T>
-__device__ void sweep_tile(const Inst &I, int axis, int tile, typename BC<T>::c *sm, int lane)
+__device__ __forceinline__ void sweep_tile(const Inst &I, int axis, int tile, typename BC<T>::c *sm, int lane)
 {
     using C = typename BC<T>::c;
     const int n = I.n[axis];
@@ -349,9 +379,18 @@ __device__ void sweep_tile(const Inst &I, int axis, int tile, typename BC<T>::c 
 __device__ void norm_item(const Inst &I, int lane, int *err)
 {
     const int tiles = I.tiles[I.last_axis];
-    double v = 0.0;
-    for (int t = lane; t < tiles; t += 32) v += I.partials[t];
-    v = warp_sum_d(v);
+    // four interleaved FP64 chains per lane (a dependent FP64 add is slow on
+    // GB300), combined in a fixed order
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int t = lane;
+    for (; t + 96 < tiles; t += 128) {
+        v0 += I.partials[t];
+        v1 += I.partials[t + 32];
+        v2 += I.partials[t + 64];
+        v3 += I.partials[t + 96];
+    }
+    for (; t < tiles; t += 32) v0 += I.partials[t];
+    const double v = warp_sum_d((v0 + v1) + (v2 + v3));
     if (lane == 0) {
         const double nrm = I.w * v;
         *I.norm = nrm;
@@ -402,10 +441,26 @@ __global__ void __launch_bounds__(32) k_batch_steps(const LaunchArgs A)
         const int s = (int)((long long)it / A.ips);
         long long r = (long long)it - (long long)s * A.ips;
         int p = 0;
-        while (r >= A.phase_total[p]) r -= A.phase_total[p++];
+        // (constant indices: a dynamically indexed kernel-parameter array
+        // would be copied to local memory)
+        if (r >= A.phase_total[0]) {
+            r -= A.phase_total[0];
+            ++p;
+            if (r >= A.phase_total[1]) {
+                r -= A.phase_total[1];
+                ++p;
+                if (r >= A.phase_total[2]) {
+                    r -= A.phase_total[2];
+                    ++p;
+                }
+            }
+        }
         const int *pr = A.pref + p * (A.N + 1);
         const int i = find_instance(pr, A.N, (int)r, lane), tile = (int)(r - pr[i]);
         const Inst &I = A.inst[i];
+        // its descriptor into L1 while the dependency wait runs
+        if (lane * 128 < (int)sizeof(Inst))
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char *>(&I) + lane * 128));
         const int need = s * A.tot[i] + A.cum[i * 4 + p];
         int ok = 1;
         if (lane == 0) ok = wait_done(&A.done[i], need, A.abort_flag);
