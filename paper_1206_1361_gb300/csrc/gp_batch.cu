@@ -154,8 +154,8 @@ __device__ __forceinline__ double warp_sum_d(double v)
 }
 
 // The exact line update of a lane pair, in place on row[0], row[es], ...,
-// row[(n-1) es] (shared memory, element stride es; point 0 and the virtual
-// point n are zero).  The top lane eliminates
+// row[(n-1) es] (shared memory, element stride es: 1 for x tiles, 16 for
+// y / z tiles; point 0 and the virtual point n are zero).  The top lane eliminates
 // i = 1 .. k-1, the bottom lane i = m .. k+1 with the mirrored tables (the
 // matrix is symmetric Toeplitz), the top lane closes the middle row k =
 // ceil(m / 2), and both back-substitute outward.  NL (x tiles): calcnu on
@@ -165,9 +165,11 @@ __device__ __forceinline__ double warp_sum_d(double v)
 // acc when norm.  Every lane of the warp calls this (the shuffles need them
 // all); `active` marks lanes with a line.
 template <typename T, int MODE, bool NL>
-__device__ __forceinline__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int es, int n,
-                            long long line, bool top, bool active, bool norm, Acc<T> &acc)
+__device__ __forceinline__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int n,
+                                            long long line, bool top, bool active, bool norm, Acc<T> &acc)
 {
+    // x tiles are row-major, y / z tiles column-major
+    constexpr int es = NL ? 1 : kTileLines;
     using C = typename BC<T>::c;
     using F = typename Coef<T>::t;
     const int m = n - 1;
@@ -313,6 +315,7 @@ __device__ __forceinline__ void sweep_tile(const Inst &I, int axis, int tile, ty
     const int r = lane & (kTileLines - 1);
     const bool top = lane < kTileLines, active = r < rows;
     C *psi = static_cast<C *>(I.psi);
+    const int nx = I.n[0];                 // (kept in a register across the cp.async clobbers)
     constexpr int B = (int)sizeof(C);
     constexpr int Q = B;                   // 16-byte pieces per column (16 lines)
     constexpr int E = 16 / B;              // elements per piece
@@ -322,13 +325,13 @@ __device__ __forceinline__ void sweep_tile(const Inst &I, int axis, int tile, ty
     bool wide = false;
     if (axis == 0) {
         for (int rr = 0; rr < rows; ++rr) {
-            const C *src = psi + (L0 + rr) * I.n[0];
+            const C *src = psi + (L0 + rr) * nx;
             for (int c = lane; c < n; c += 32) cp_async<B>(&sm[rr * P + c], &src[c]);
         }
     } else {
         line_geom(I, axis, L0, base0, stride);
         // 16 lines at unit spacing, every column starting on 16 bytes
-        wide = rows == kTileLines && (axis == 2 || (L0 % I.n[0]) + kTileLines <= I.n[0]) &&
+        wide = rows == kTileLines && (axis == 2 || (L0 % nx) + kTileLines <= nx) &&
                ((base0 * B) & 15) == 0 && ((stride * B) & 15) == 0;
         if (wide) {
             const C *src = psi + base0 + (lane % Q) * E;
@@ -344,19 +347,18 @@ __device__ __forceinline__ void sweep_tile(const Inst &I, int axis, int tile, ty
     __syncwarp();
     const bool norm = I.mode == 0 && axis == I.last_axis;
     C *row = axis == 0 ? sm + r * P : sm + r;
-    const int es = axis == 0 ? 1 : kTileLines;
     Acc<T> acc;
     if (axis == 0) {
-        if (I.mode == 0) solve_line2<T, 0, true>(I, axis, row, es, n, L0 + r, top, active, norm, acc);
-        else solve_line2<T, 1, true>(I, axis, row, es, n, L0 + r, top, active, false, acc);
+        if (I.mode == 0) solve_line2<T, 0, true>(I, axis, row, n, L0 + r, top, active, norm, acc);
+        else solve_line2<T, 1, true>(I, axis, row, n, L0 + r, top, active, false, acc);
     } else {
-        if (I.mode == 0) solve_line2<T, 0, false>(I, axis, row, es, n, L0 + r, top, active, norm, acc);
-        else solve_line2<T, 1, false>(I, axis, row, es, n, L0 + r, top, active, false, acc);
+        if (I.mode == 0) solve_line2<T, 0, false>(I, axis, row, n, L0 + r, top, active, norm, acc);
+        else solve_line2<T, 1, false>(I, axis, row, n, L0 + r, top, active, false, acc);
     }
     __syncwarp();
     if (axis == 0) {
         for (int rr = 0; rr < rows; ++rr) {
-            C *dst = psi + (L0 + rr) * I.n[0];
+            C *dst = psi + (L0 + rr) * nx;
             for (int c = lane; c < n; c += 32) dst[c] = sm[rr * P + c];
         }
     } else if (wide) {
