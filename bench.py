@@ -75,6 +75,7 @@ def parse_args():
     ap.add_argument("--probe-case", default=None,
                     help="workload name for --probe (default: the benchmark workload)")
     ap.add_argument("--probe-shape", type=int, default=None, help="TMA tile shape for --probe")
+    ap.add_argument("--probe-path", type=int, default=None, help="sweep path (GP_PATH_*) for --probe")
     return ap.parse_args()
 
 
@@ -156,8 +157,8 @@ def measured_peaks():
         return {}
 
 
-KERNEL_SOURCES = ("sscn_kernels.cu", "sscn_tma.cu", "sscn_axial.cu", "gp_batch.cu", "sscn_internal.h",
-                  "sscn_line.cuh", "sscn_coef.cuh", "sscn_accum.cuh")
+KERNEL_SOURCES = ("sscn_kernels.cu", "sscn_tma.cu", "sscn_axial.cu", "gp_batch.cu", "sscn_slab.cu",
+                  "sscn_internal.h", "sscn_line.cuh", "sscn_coef.cuh", "sscn_accum.cuh", "sscn_pair.cuh")
 
 
 def kernel_source_sha(files=KERNEL_SOURCES):
@@ -413,7 +414,8 @@ def run_ours(args):
             forms = {"precision": precision_form(gp, torch, stream, args),
                      "batched": batched_form(gp), "serving": serving_form(gp),
                      "splitting": splitting_form(gp, torch, stream),
-                     "axial": axial_form(gp, torch, stream)}
+                     "axial": axial_form(gp, torch, stream),
+                     "slab": slab_form(gp, torch, stream)}
 
         extra = {"prep_imag_steps": prep, "prep_dmu": dmu,
                  "norm_drift": abs(obs_end["norm"] / obs0["norm"] - 1),
@@ -584,6 +586,53 @@ def axial_form(gp, torch, stream):
                              "kind": "oracle", "sample": "%d axial SSCN steps" % n_cpu}}
 
 
+def slab_form(gp, torch, stream):
+    """The fused x+y slab sweep (one CTA per z-plane held in shared memory)
+    against the separate sweeps, on grids whose xy-plane fits one CTA: per
+    SSCN step time of each, and the fused kernel's HBM roofline (psi read and
+    written once for both sweeps: 16 B per point in complex64, 32 in
+    complex128)."""
+    from paper_1206_1361_gb300.workloads import SLAB_C64, SLAB_FP64
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs") or FALLBACK_HBM_GBS
+    out = {}
+    for case in (SLAB_C64, SLAB_FP64):
+        entry = {"grid": list(case.shape), "steps": case.steps}
+        for name, path in (("separate", gp.GP_PATH_AUTO), ("slab", gp.GP_PATH_SLAB)):
+            ctx = gp.gp_create(case.shape, case.h, case.dt, *case.trap, case.g, case.mode,
+                               case.precision, stream)
+            try:
+                gp.gp_set_option(ctx, gp.GP_OPT_SWEEP_PATH, path)
+                gp.gp_load(ctx, None)
+                gp.gp_step(ctx, 10)
+                kt = gp.gp_time_kernels(ctx, 10)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                gp.gp_step(ctx, case.steps)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                ms = ev0.elapsed_time(ev1) / case.steps
+                e = {"ms_per_sscn_step": ms, "value": case.points / (ms * 1e-3), "unit": UNIT,
+                     "paths": list(gp.gp_sweep_paths(ctx)),
+                     "kernel_ms": {k: round(v, 5) for k, v in kt.items() if v > 0}}
+                if path == gp.GP_PATH_SLAB:
+                    bpp = SWEEP_BYTES_PER_POINT[case.precision]
+                    ach = bpp * case.points / (kt["sweep_x"] * 1e-3) / 1e9
+                    e["roofline"] = {"bound": "hbm", "kernel": "sweep_xy", "achieved": ach,
+                                     "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                     "bytes_per_point": bpp,
+                                     "traffic": profiled_traffic("sweep_xy", case.name),
+                                     "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"}
+                entry[name] = e
+            finally:
+                gp.gp_destroy(ctx)
+        entry["speedup_slab"] = entry["separate"]["ms_per_sscn_step"] / entry["slab"]["ms_per_sscn_step"]
+        out[case.name] = entry
+    return out
+
+
 def batched_form(gp):
     """256 uneven imaginary-time problems (seed 3) solved to convergence in
     one batch, against the same problems solved one at a time on complex64
@@ -660,6 +709,8 @@ def run_probe(args):
                    case.precision) as s:
         if args.probe_shape is not None:
             gp.gp_set_option(s.ctx, gp.GP_OPT_TILE_SHAPE, args.probe_shape)
+        if args.probe_path is not None:
+            s.set_path(args.probe_path)
         s.load(None).step(args.probe).sync()
         s.observables()
     torch.cuda.synchronize()

@@ -231,7 +231,14 @@ enum {
  * each extended by a window of rows wide enough that the cut coupling reaches
  * the core below 2^-55 (the sweeps then agree with the exact solve to FP64
  * rounding); GP_PATH_AUTO takes it when a line gets at least two cores. */
-enum { GP_PATH_AUTO = 0, GP_PATH_EXACT = 1, GP_PATH_TMA = 2, GP_PATH_WINDOW = 3 };
+/* GP_PATH_SLAB (3D Cartesian grids whose xy-plane fits one CTA's shared
+ * memory: ny (nx | 1) points of 16 (complex128) / 8 (complex64) bytes at most
+ * 232448 bytes, nx, ny <= 256): the x and y sweeps of a step run as one pass,
+ * a CTA holding a whole z-plane (calcnu and the x sweep on its rows, the y
+ * sweep on its columns, right-hand-side form, exact elimination); the z sweep
+ * takes the path GP_PATH_AUTO would.  psi crosses HBM twice per step instead
+ * of three times.  Only on request (gp_set_option or gp_autotune). */
+enum { GP_PATH_AUTO = 0, GP_PATH_EXACT = 1, GP_PATH_TMA = 2, GP_PATH_WINDOW = 3, GP_PATH_SLAB = 4 };
 enum { GP_SPLIT_LIE = 0, GP_SPLIT_STRANG = 1 };
 
 /*
@@ -269,8 +276,9 @@ int gp_get_option(gp_ctx *ctx, int option, int *value);
 /* Number of tile shapes GP_OPT_TILE_SHAPE accepts for a precision. */
 int gp_tile_shapes(int precision, int *count);
 
-/* The sweep path each axis uses now in the current mode (GP_PATH_EXACT or
- * GP_PATH_TMA) into path[0..2] (path[2] = 0 in 2D). */
+/* The sweep path each axis uses now in the current mode (GP_PATH_EXACT,
+ * GP_PATH_TMA, GP_PATH_WINDOW or GP_PATH_SLAB -- the last for x and y
+ * together) into path[0..2] (path[2] = 0 in 2D). */
 int gp_sweep_paths(gp_ctx *ctx, int path[3]);
 
 /*

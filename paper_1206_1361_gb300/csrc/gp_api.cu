@@ -417,12 +417,20 @@ void release(gp_ctx *c)
 }
 
 // Path of the sweep along `axis` in the current mode.
+// x and y fused over z-planes in shared memory (3D Cartesian grids whose
+// plane fits one CTA)
+bool slab_ok(const gp_ctx *c)
+{
+    return !c->axial && c->grid.nz > 1 && gp::slab_fits(c->prec, c->grid.nx, c->grid.ny);
+}
+
 int sweep_path(const gp_ctx *c, int axis)
 {
     if (c->axial) {
         const bool seg = c->seg_ok[c->mode] && c->path_opt != GP_PATH_EXACT;
         return seg ? GP_PATH_WINDOW : GP_PATH_EXACT;
     }
+    if (c->path_opt == GP_PATH_SLAB && axis < 2 && slab_ok(c)) return GP_PATH_SLAB;
     if (!c->tma_ok[c->mode][axis]) return GP_PATH_EXACT;
     if (c->path_opt == GP_PATH_EXACT) return GP_PATH_EXACT;
     if (c->path_opt == GP_PATH_TMA) return GP_PATH_TMA;
@@ -560,9 +568,17 @@ int enqueue_step(gp_ctx *c, cudaEvent_t *ev = nullptr)
         GP_CK(c, mark(2));
         GP_CK(c, mark(3));
     } else {
-    GP_CK(c, launch_sweep(c, 0, &nl, false, nullptr, nullptr));
-    GP_CK(c, mark(1));
-    for (int axis = 1; axis <= last; ++axis) {
+    const bool slab = sweep_path(c, 0) == GP_PATH_SLAB;
+    if (slab) {
+        GP_CK(c, gp::launch_sweep_xy(c->prec, mode, c->psi, c->grid.nx, c->grid.ny, c->grid.nz,
+                                     c->ax[mode][0], c->ax[mode][1], nl, c->stream));
+        GP_CK(c, mark(1));
+        GP_CK(c, mark(2));
+    } else {
+        GP_CK(c, launch_sweep(c, 0, &nl, false, nullptr, nullptr));
+        GP_CK(c, mark(1));
+    }
+    for (int axis = slab ? 2 : 1; axis <= last; ++axis) {
         const bool is_last = axis == last;
         const gp::NonlinArgs *out_nl = (is_last && strang && !imag) ? &nl2 : nullptr;
         GP_CK(c, launch_sweep(c, axis, out_nl, out_nl != nullptr,
@@ -592,8 +608,9 @@ int kernels_per_step(const gp_ctx *c)
 {
     const bool imag = c->mode == GP_IMAG, strang = c->split == GP_SPLIT_STRANG;
     const bool seg = c->axial && sweep_path(c, 0) == GP_PATH_WINDOW;   // + the calcnu pass
-    return (c->grid.nz > 1 ? 3 : 2) + (seg ? 1 : 0) + (imag ? 1 : 0) + (imag && strang ? 2 : 0) +
-           (modulated(c) ? 1 : 0);
+    const bool slab = sweep_path(c, 0) == GP_PATH_SLAB;      // x and y in one launch
+    return (c->grid.nz > 1 ? 3 : 2) - (slab ? 1 : 0) + (seg ? 1 : 0) + (imag ? 1 : 0) +
+           (imag && strang ? 2 : 0) + (modulated(c) ? 1 : 0);
 }
 
 void drop_graph(gp_ctx *c)
@@ -1163,8 +1180,11 @@ int gp_set_option(gp_ctx *c, int option, int value)
     }
     if (option != GP_OPT_SWEEP_PATH) return fail(c, GP_EINVAL, "gp_set_option: unknown option");
     if (value != GP_PATH_AUTO && value != GP_PATH_EXACT && value != GP_PATH_TMA &&
-        value != GP_PATH_WINDOW)
+        value != GP_PATH_WINDOW && value != GP_PATH_SLAB)
         return fail(c, GP_EINVAL, "gp_set_option: unknown sweep path");
+    if (value == GP_PATH_SLAB && !slab_ok(c))
+        return fail(c, GP_EINVAL, "gp_set_option: the slab path needs a 3D Cartesian grid whose "
+                                  "xy-plane fits one CTA's shared memory");
     if (value == GP_PATH_WINDOW && (!c->axial || !c->seg_ok[c->mode]))
         return fail(c, GP_EINVAL, "gp_set_option: the segmented-window path is for axial grids "
                                   "with long enough lines");
@@ -1208,6 +1228,7 @@ int gp_autotune(gp_ctx *c, int steps, int *path_out, int *shape_out, double *ms_
     struct Cand { int path, shape; };
     std::vector<Cand> cands{{GP_PATH_EXACT, shape0}};
     if (c->axial && c->seg_ok[c->mode]) cands.push_back({GP_PATH_WINDOW, shape0});
+    if (slab_ok(c)) cands.push_back({GP_PATH_SLAB, shape0});
     for (int sh = 0; sh < gp::tma_shapes(c->prec); ++sh) {
         c->tile_shape = sh;
         setup_tma(c);

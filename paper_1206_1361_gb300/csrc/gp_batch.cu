@@ -39,6 +39,7 @@
 #include "sscn_accum.cuh"
 #include "sscn_internal.h"
 #include "sscn_line.cuh"
+#include "sscn_pair.cuh"
 
 namespace {
 
@@ -153,40 +154,27 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
-// The exact line update of a lane pair, in place on row[0], row[es], ...,
-// row[(n-1) es] (shared memory, element stride es: 1 for x tiles, 16 for
-// y / z tiles; point 0 and the virtual point n are zero).  The top lane eliminates
-// i = 1 .. k-1, the bottom lane i = m .. k+1 with the mirrored tables (the
-// matrix is symmetric Toeplitz), the top lane closes the middle row k =
-// ceil(m / 2), and both back-substitute outward.  NL (x tiles): calcnu on
-// each point as the forward elimination reads it (the elimination keeps
-// only d', so the updated point is never stored; the middle point is
-// computed by both lanes).  The norm contribution of the result goes into
-// acc when norm.  Every lane of the warp calls this (the shuffles need them
-// all); `active` marks lanes with a line.
+// The exact line update of a lane pair (gp::solve_pair) on a tile row:
+// x tiles row-major (element stride 1, calcnu fused into the elimination),
+// y / z tiles column-major (stride 16).
 template <typename T, int MODE, bool NL>
 __device__ __forceinline__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int n,
                                             long long line, bool top, bool active, bool norm, Acc<T> &acc)
 {
-    // x tiles are row-major, y / z tiles column-major
-    constexpr int es = NL ? 1 : kTileLines;
-    using C = typename BC<T>::c;
     using F = typename Coef<T>::t;
-    const int m = n - 1;
-    const int k = (m + 1) >> 1;
-    const LineOps<T, MODE> cn{(T)I.kap[axis]};
-    const F *cp = static_cast<const F *>(I.cp[axis]);
-    const F *mult = static_cast<const F *>(I.mult[axis]);
-    const int conv = I.conv[axis];
-    F cinf, minf, mid;
+    gp::PairTabs<T> tb;
+    tb.mult = static_cast<const F *>(I.mult[axis]);
+    tb.cp = static_cast<const F *>(I.cp[axis]);
+    tb.conv = I.conv[axis];
+    tb.kappa = (T)I.kap[axis];
     if constexpr (sizeof(T) == 8) {
-        cinf = I.cinf64[axis];
-        minf = I.minf64[axis];
-        mid = I.mid64[axis];
+        tb.cinf = I.cinf64[axis];
+        tb.minf = I.minf64[axis];
+        tb.mid = I.mid64[axis];
     } else {
-        cinf = I.cinf32[axis];
-        minf = I.minf32[axis];
-        mid = I.mid32[axis];
+        tb.cinf = I.cinf32[axis];
+        tb.minf = I.minf32[axis];
+        tb.mid = I.mid32[axis];
     }
     Calcnu<T, MODE> cu{};
     if (NL && active) {
@@ -195,94 +183,7 @@ __device__ __forceinline__ void solve_line2(const Inst &I, int axis, typename BC
         cu.setup(static_cast<const F *>(I.ph[0]), static_cast<const F *>(I.ph[1]),
                  static_cast<const F *>(I.ph[2]), I.th[0], I.th[1], I.th[2], j, kz, I.dtg, I.scale);
     }
-    const C zero = mkb<T>((T)0, (T)0);
-    const int len = top ? k - 1 : m - k;
-    const int dir = top ? es : -es, di = top ? 1 : -1;
-    // entries t >= conv of both tables are the constants minf / cinf: the
-    // recurrences run a table part and a constant part, so most points load
-    // no coefficient (a per-point table load sits on the recurrence's
-    // dependency chain)
-    const int tc = min(conv, len);
-    C prev = zero, cur = zero, d = zero;
-    if (active) {
-        C *p = row + (top ? 1 : m) * es;
-        int i = top ? 1 : m;               // point index of *p
-        cur = *p;
-        if (NL) cur = cu.apply(cur, i);
-        int t = 0;
-        for (; t < tc; ++t, p += dir, i += di) {
-            C next = p[dir];
-            if (NL) next = cu.apply(next, i + di);
-            d = cn.fwd(cn.rhs(prev, cur, next), d, mult[t]);
-            *p = d;
-            prev = cur;
-            cur = next;
-        }
-        // constant part in groups of 4: a group's points (and their calcnu)
-        // are read before any of its results is stored, so the loads and the
-        // calcnu arithmetic overlap the recurrence
-        for (; t + 4 <= len; t += 4, p += 4 * dir, i += 4 * di) {
-            C nx[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) nx[q] = p[(q + 1) * dir];
-            if (NL) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) nx[q] = cu.apply(nx[q], i + (q + 1) * di);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                d = cn.fwd(cn.rhs(prev, cur, nx[q]), d, minf);
-                p[q * dir] = d;
-                prev = cur;
-                cur = nx[q];
-            }
-        }
-        for (; t < len; ++t, p += dir, i += di) {
-            C next = p[dir];
-            if (NL) next = cu.apply(next, i + di);
-            d = cn.fwd(cn.rhs(prev, cur, next), d, minf);
-            *p = d;
-            prev = cur;
-            cur = next;
-        }
-    }
-    // top: prev = psi_{k-1}, cur = psi_k; bottom: prev = psi_{k+1}, d = e_{k+1}
-    const C o_prev = mkb<T>(__shfl_xor_sync(0xffffffffu, prev.x, 16), __shfl_xor_sync(0xffffffffu, prev.y, 16));
-    const C o_d = mkb<T>(__shfl_xor_sync(0xffffffffu, d.x, 16), __shfl_xor_sync(0xffffffffu, d.y, 16));
-    C vk = zero;
-    if (active && top) {
-        vk = cn.fwd(cn.rhs(prev, cur, o_prev), mkb<T>(d.x + o_d.x, d.y + o_d.y), mid);
-        row[k * es] = vk;
-        if (norm) acc.add(fma(vk.x, vk.x, vk.y * vk.y));
-    }
-    const C o_vk = mkb<T>(__shfl_xor_sync(0xffffffffu, vk.x, 16), __shfl_xor_sync(0xffffffffu, vk.y, 16));
-    C u = top ? vk : o_vk;
-    if (active) {
-        int t = len - 1;
-        C *p = row + (top ? 1 + t : m - t) * es;
-        // likewise in groups of 4 (each d' is read before its u is stored)
-        for (; t - 3 >= tc; t -= 4, p -= 4 * dir) {
-            C dv[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) dv[q] = p[-q * dir];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                u = cn.back(dv[q], cinf, u);
-                p[-q * dir] = u;
-                if (norm) acc.add(fma(u.x, u.x, u.y * u.y));
-            }
-        }
-        for (; t >= tc; --t, p -= dir) {
-            u = cn.back(*p, cinf, u);
-            *p = u;
-            if (norm) acc.add(fma(u.x, u.x, u.y * u.y));
-        }
-        for (; t >= 0; --t, p -= dir) {
-            u = cn.back(*p, cp[t], u);
-            *p = u;
-            if (norm) acc.add(fma(u.x, u.x, u.y * u.y));
-        }
-    }
+    gp::solve_pair<T, MODE, NL, NL ? 1 : kTileLines>(row, 0, n, top, active, norm, acc, tb, cu);
 }
 
 // Line index -> offset of its point 0 and the stride between its points.

@@ -21,7 +21,7 @@ GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ENONFINITE, GP_ETIMEOUT, GP_EINTERNAL,
     0, -1, -2, -3, -4, -5, -6, -7)
 GP_MAX_EDGE = 8192
 GP_OPT_SWEEP_PATH, GP_OPT_TILE_SHAPE, GP_OPT_SPLITTING, GP_OPT_POTENTIAL_TABLE = 1, 2, 3, 4
-GP_PATH_AUTO, GP_PATH_EXACT, GP_PATH_TMA, GP_PATH_WINDOW = 0, 1, 2, 3
+GP_PATH_AUTO, GP_PATH_EXACT, GP_PATH_TMA, GP_PATH_WINDOW, GP_PATH_SLAB = 0, 1, 2, 3, 4
 GP_SPLIT_LIE, GP_SPLIT_STRANG = 0, 1
 
 ERROR_NAMES = {GP_EINVAL: "GP_EINVAL", GP_ENOMEM: "GP_ENOMEM", GP_ECUDA: "GP_ECUDA",
@@ -287,7 +287,8 @@ def gp_tile_shapes(precision):
 
 
 def gp_sweep_paths(ctx):
-    """Sweep path per axis now in use: GP_PATH_EXACT or GP_PATH_TMA (0 if none)."""
+    """Sweep path per axis now in use: GP_PATH_EXACT, GP_PATH_TMA, GP_PATH_WINDOW or
+    GP_PATH_SLAB (0 if none)."""
     p = (ctypes.c_int * 3)()
     _err(ctx, load_library().gp_sweep_paths(ctx, p))
     return tuple(p)

@@ -52,7 +52,18 @@ PRECISION_512 = Case(
     trap=(1.0, 2.0, 4.0), g=50.0, mode=1, steps=1000, precision=1,
     note="real time from the Gaussian seed, complex64 psi, FP64 reductions")
 
-CASES = {c.name: c for c in (SMALL_IMAG_64, REAL_256, PRECISION_512)}
+# Grids whose xy-plane fits one CTA's shared memory (the fused x+y slab
+# sweep): many small planes, psi larger than L2 (129 MB).
+SLAB_C64 = Case(
+    name="real3d-128x128x1024-c64", shape=(128, 128, 1024), h=(0.1, 0.1, 0.0125), dt=1e-4,
+    trap=(1.0, 1.5, 2.0), g=10.0, mode=1, steps=200, precision=1,
+    note="real time from the Gaussian seed, complex64, 128 x 128 planes")
+SLAB_FP64 = Case(
+    name="real3d-96x96x1024-fp64", shape=(96, 96, 1024), h=(0.1, 0.1, 0.0125), dt=1e-4,
+    trap=(1.0, 1.5, 2.0), g=10.0, mode=1, steps=200,
+    note="real time from the Gaussian seed, complex128, 96 x 96 planes")
+
+CASES = {c.name: c for c in (SMALL_IMAG_64, REAL_256, PRECISION_512, SLAB_C64, SLAB_FP64)}
 
 
 def convergence_interval(dt):

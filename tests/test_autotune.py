@@ -30,7 +30,7 @@ def test_autotune_keeps_state_and_caches(tmp_path):
             s.load(psi0.astype(dtype)).step(3)
             before = s.psi()
             first = autotune.tune(s, h, dt, gp.GP_REAL, steps=3, path=cache)
-            assert not first["cached"] and first["path"] in (gp.GP_PATH_EXACT, gp.GP_PATH_TMA)
+            assert not first["cached"] and first["path"] in (gp.GP_PATH_EXACT, gp.GP_PATH_TMA, gp.GP_PATH_SLAB)
             assert np.array_equal(s.psi(), before)
             assert s.observables()["step"] == 3
             s.step(4)
