@@ -74,15 +74,13 @@ k_sweep_xy(typename Cx<T>::t *__restrict__ psi, int nx, int ny, PairTabs<T> tx, 
     const int P = nx | 1;
     const int kz = blockIdx.x;
     C *plane = psi + (long long)kz * nx * ny;
-    const int np = nx * ny;
-    for (int idx = threadIdx.x; idx < np; idx += blockDim.x) {
-        const int y = idx / nx, x = idx - y * nx;
-        cp_async<(int)sizeof(C)>(&sm[y * P + x], &plane[idx]);
-    }
+    // rows to warps, points of a row to lanes (coalesced, no index division)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int y = warp; y < ny; y += nwarps)
+        for (int x = lane; x < nx; x += 32) cp_async<(int)sizeof(C)>(&sm[y * P + x], &plane[y * nx + x]);
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int r = (threadIdx.x >> 5) * 16 + (lane & 15);   // this lane pair's line
+    const int r = warp * 16 + (lane & 15);                 // this lane pair's line
     const bool top = lane < 16;
     Acc<T> acc;                                            // (no norm here)
     {
@@ -100,10 +98,8 @@ k_sweep_xy(typename Cx<T>::t *__restrict__ psi, int nx, int ny, PairTabs<T> tx, 
         solve_pair<T, MODE, false, 0>(sm + r, P, ny, top, active, false, acc, ty, none);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < np; idx += blockDim.x) {
-        const int y = idx / nx, x = idx - y * nx;
-        plane[idx] = sm[y * P + x];
-    }
+    for (int y = warp; y < ny; y += nwarps)
+        for (int x = lane; x < nx; x += 32) plane[y * nx + x] = sm[y * P + x];
 }
 
 template <typename T, int MODE>
