@@ -158,7 +158,8 @@ def measured_peaks():
 
 
 KERNEL_SOURCES = ("sscn_kernels.cu", "sscn_tma.cu", "sscn_axial.cu", "gp_batch.cu", "sscn_slab.cu",
-                  "sscn_internal.h", "sscn_line.cuh", "sscn_coef.cuh", "sscn_accum.cuh", "sscn_pair.cuh")
+                  "sscn_internal.h", "sscn_slab.h", "sscn_line.cuh", "sscn_coef.cuh", "sscn_accum.cuh",
+                  "sscn_pair.cuh")
 
 
 def kernel_source_sha(files=KERNEL_SOURCES):

@@ -15,6 +15,7 @@
 
 #include "../../include/gp.h"
 #include "sscn_internal.h"
+#include "sscn_slab.h"
 
 using gp::AxisTables;
 using gp::Partials;

@@ -108,16 +108,6 @@ struct Partials {
 
 enum Precision { kC128 = 0, kC64 = 1 };
 
-// ---- fused x + y sweep over z-planes in shared memory (sscn_slab.cu) -------
-// Shared memory one plane takes (ny rows of nx | 1 points), whether a plane
-// fits one CTA, and the launch: calcnu (tables in x, y, z order) with the x
-// sweep, then the y sweep, one CTA per plane, no norm partials.
-size_t slab_bytes(int prec, int nx, int ny);
-bool slab_fits(int prec, int nx, int ny);
-cudaError_t launch_sweep_xy(int prec, int mode, void *psi, int nx, int ny, int nz,
-                            const AxisTables &ax, const AxisTables &ay, const NonlinArgs &nl,
-                            cudaStream_t st);
-
 // ---- launchers (sscn_kernels.cu) -------------------------------------------
 // All launchers enqueue on `st` and return the launch error (cudaSuccess if
 // the launch was accepted).

@@ -14,8 +14,8 @@
 
 #include <cuda_runtime.h>
 
-#include "sscn_internal.h"
 #include "sscn_pair.cuh"
+#include "sscn_slab.h"
 
 namespace gp {
 namespace {
