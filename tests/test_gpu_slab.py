@@ -1,9 +1,11 @@
-"""GPU parity of the fused x+y slab sweep (GP_PATH_SLAB: one CTA per z-plane
-held in shared memory, calcnu and the x sweep on its rows, the y sweep on its
-columns) against the oracle and against the separate sweeps.  Shapes cover
-odd and even edges, nx != ny, planes that fill several warps with a ragged
-last warp, the largest complex128 plane that fits, and both modes; the
-symmetric splitting and a modulated g ride on the slab's x sweep."""
+"""GPU parity of the fused x+y slab sweep (GP_PATH_SLAB: a z-plane held in
+shared memory -- by one CTA, or split at the middle row over a 2-CTA cluster
+when one CTA cannot hold it -- calcnu and the x sweep
+on its rows, the y sweep on its columns) against the oracle and against the
+separate sweeps.  Shapes cover odd and even edges, nx != ny, planes that fill
+several warps with a ragged last warp, both plane placements, the largest
+planes that fit, and both modes; the symmetric splitting and a modulated g
+ride on the slab's x sweep."""
 import numpy as np
 import pytest
 
@@ -75,6 +77,29 @@ def test_slab_complex64_matches_oracle(shape, h, mode):
     assert rel_l2(got, want) <= 3e-6
 
 
+# planes larger than one CTA's shared memory: split over a 2-CTA cluster
+SPLIT = [
+    ((130, 120, 4), (0.1, 0.12, 0.3), gp.GP_C128),    # 120 x 131 x 16 B = 251 KB: fits only split
+    ((131, 125, 3), (0.12, 0.1, 0.4), gp.GP_C128),    # odd nx and ny
+    ((172, 171, 4), (0.08, 0.08, 0.4), gp.GP_C64),    # 171 x 173 x 8 B = 237 KB: odd ny
+    ((180, 176, 3), (0.08, 0.08, 0.5), gp.GP_C64),    # 253 KB: fits only split
+]
+
+
+@pytest.mark.parametrize("shape,h,prec", SPLIT)
+@pytest.mark.parametrize("mode", [gp.GP_IMAG, gp.GP_REAL])
+def test_split_plane_matches_oracle(shape, h, prec, mode):
+    require_gpu()
+    dt, g = 0.002, 6.0
+    dtype = np.complex128 if prec == gp.GP_C128 else np.complex64
+    psi0 = rand_state(shape, 43)
+    got, _, paths = run(shape, h, dt, g, mode, [5, 4], psi0.astype(dtype), prec, gp.GP_PATH_SLAB)
+    assert paths[:2] == (gp.GP_PATH_SLAB, gp.GP_PATH_SLAB)
+    want = psi0.copy()
+    oracle.step(oracle_params(shape, h, dt, W3, g, mode), want, 9)
+    assert rel_l2(got, want) <= (1e-12 if prec == gp.GP_C128 else 3e-6)
+
+
 @pytest.mark.parametrize("mode", [gp.GP_IMAG, gp.GP_REAL])
 def test_slab_agrees_with_separate_sweeps_over_many_steps(mode):
     require_gpu()
@@ -98,7 +123,7 @@ def test_slab_with_strang_and_modulated_g(mode):
     assert rel_l2(got, want) <= 1e-12
 
 
-def test_largest_fp64_plane_and_eligibility():
+def test_largest_one_cta_fp64_plane_and_eligibility():
     require_gpu()
     # 120 x 120 complex128: 120 rows of 121 points x 16 B = 232320 B, just under 227 KB
     shape, h, dt, g = (120, 120, 4), (0.1, 0.1, 0.4), 5e-4, 3.0
@@ -108,7 +133,7 @@ def test_largest_fp64_plane_and_eligibility():
     want = psi0.copy()
     oracle.step(oracle_params(shape, h, dt, W3, g, gp.GP_REAL), want, 4)
     assert rel_l2(got, want) <= 1e-12
-    for shape in ((122, 120, 4), (64, 64, 1), (300, 8, 4)):   # too large, 2D, edge > 256
+    for shape in ((256, 256, 4), (64, 64, 1), (300, 8, 4)):   # too large, 2D, edge > 256
         with gp.Solver(shape, (0.1, 0.1, 0.1), 1e-3, *W3, 1.0, gp.GP_REAL, gp.GP_C128) as s:
             with pytest.raises(gp.GPError) as e:
                 s.set_path(gp.GP_PATH_SLAB)
