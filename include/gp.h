@@ -231,13 +231,15 @@ enum {
  * each extended by a window of rows wide enough that the cut coupling reaches
  * the core below 2^-55 (the sweeps then agree with the exact solve to FP64
  * rounding); GP_PATH_AUTO takes it when a line gets at least two cores. */
-/* GP_PATH_SLAB (3D Cartesian grids whose xy-plane fits one CTA's shared
- * memory: ny (nx | 1) points of 16 (complex128) / 8 (complex64) bytes at most
- * 232448 bytes, nx, ny <= 256): the x and y sweeps of a step run as one pass,
- * a CTA holding a whole z-plane (calcnu and the x sweep on its rows, the y
- * sweep on its columns, right-hand-side form, exact elimination); the z sweep
- * takes the path GP_PATH_AUTO would.  psi crosses HBM twice per step instead
- * of three times.  Only on request (gp_set_option or gp_autotune). */
+/* GP_PATH_SLAB (3D Cartesian grids, nx, ny <= 256, whose xy-plane fits the
+ * shared memory of one CTA -- ny (nx | 1) points of 16 (complex128) / 8
+ * (complex64) bytes at most 232448 bytes -- or of a 2-CTA cluster, half the
+ * rows plus a halo row each): the x and y sweeps of a step run as one pass,
+ * the CTA (or cluster) holding a whole z-plane (calcnu and the x sweep on its
+ * rows, the y sweep on its columns, right-hand-side form, exact elimination);
+ * the z sweep takes the path GP_PATH_AUTO would.  psi crosses HBM twice per
+ * step instead of three times.  Only on request (gp_set_option or
+ * gp_autotune); GP_EINVAL for grids it does not fit. */
 enum { GP_PATH_AUTO = 0, GP_PATH_EXACT = 1, GP_PATH_TMA = 2, GP_PATH_WINDOW = 3, GP_PATH_SLAB = 4 };
 enum { GP_SPLIT_LIE = 0, GP_SPLIT_STRANG = 1 };
 
