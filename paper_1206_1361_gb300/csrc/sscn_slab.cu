@@ -75,14 +75,16 @@ k_sweep_xy(typename Cx<T>::t *__restrict__ psi, int nx, int ny, PairTabs<T> tx, 
     const int P = nx | 1;
     const int kz = blockIdx.x;
     C *plane = psi + (long long)kz * nx * ny;
-    // rows to warps, points of a row to lanes (coalesced, no index division)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int y = warp; y < ny; y += nwarps)
-        for (int x = lane; x < nx; x += 32) cp_async<(int)sizeof(C)>(&sm[y * P + x], &plane[y * nx + x]);
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
+    // Each warp loads the 16 rows it sweeps along x and starts on them as soon
+    // as its own copies land; one CTA barrier before the columns; each warp
+    // then stores the 16 columns it swept along y.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = warp * 16 + (lane & 15);                 // this lane pair's line
     const bool top = lane < 16;
+    for (int y = warp * 16; y < min(warp * 16 + 16, ny); ++y)
+        for (int x = lane; x < nx; x += 32) cp_async<(int)sizeof(C)>(&sm[y * P + x], &plane[y * nx + x]);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
     Acc<T> acc;                                            // (no norm here)
     {
         // x sweep on row r (calcnu fused into its elimination)
@@ -98,9 +100,9 @@ k_sweep_xy(typename Cx<T>::t *__restrict__ psi, int nx, int ny, PairTabs<T> tx, 
         const Calcnu<T, MODE> none{};
         solve_pair<T, MODE, false, 0>(sm + r, P, ny, top, active, false, acc, ty, none);
     }
-    __syncthreads();
-    for (int y = warp; y < ny; y += nwarps)
-        for (int x = lane; x < nx; x += 32) plane[y * nx + x] = sm[y * P + x];
+    __syncwarp();
+    if (r < nx)                                            // lanes 0-15 even rows, 16-31 odd
+        for (int y = lane >> 4; y < ny; y += 2) plane[y * nx + r] = sm[y * P + r];
 }
 
 // ---- one plane over a 2-CTA cluster ---------------------------------------
