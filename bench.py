@@ -76,6 +76,9 @@ def parse_args():
                     help="workload name for --probe (default: the benchmark workload)")
     ap.add_argument("--probe-shape", type=int, default=None, help="TMA tile shape for --probe")
     ap.add_argument("--probe-path", type=int, default=None, help="sweep path (GP_PATH_*) for --probe")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP64, FP32 and packed FP32x2 multiply-add rates of "
+                         "this GPU (the alu roofline denominators), print one JSON line, exit")
     return ap.parse_args()
 
 
@@ -718,8 +721,44 @@ def run_probe(args):
     return 0
 
 
+PEAK_ITERS = {"fp64_fma": 20000, "fp32_fma": 400000, "fp32x2_fma": 200000}
+
+
+def alu_peaks(gp):
+    """Measured TFLOP/s of the FP64, FP32 and packed FP32x2 multiply-add pipes
+    (gp_measure_peak: best of three launches over every CTA slot)."""
+    kinds = {"fp64_fma": gp.GP_PEAK_FP64_FMA, "fp32_fma": gp.GP_PEAK_FP32_FMA,
+             "fp32x2_fma": gp.GP_PEAK_FP32X2_FMA}
+    out = {}
+    for name, kind in kinds.items():
+        tf, ms = gp.gp_measure_peak(kind, PEAK_ITERS[name])
+        out[name] = {"tflops": tf, "ms": ms, "iters": PEAK_ITERS[name]}
+    return out
+
+
+def run_peaks(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1206_1361_gb300 import gp
+    dev_id = None
+    try:
+        dev_id = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(dev_id)
+    clocks.start()
+    peaks = alu_peaks(gp)
+    clk = clocks.stop()
+    print(json.dumps({"peaks": peaks, "clocks": clk,
+                      "device": torch.cuda.get_device_name(0)}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.peaks:
+        return run_peaks(args)
     if args.probe:
         return run_probe(args)
     if args.impl == "reference":

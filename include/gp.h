@@ -30,7 +30,9 @@
  *
  * Memory layout of psi: psi[(k * ny + j) * nx + i], x fastest, complex numbers
  * stored as interleaved (re, im): complex128 (2 x double) for GP_C128,
- * complex64 (2 x float) for GP_C64.  Reductions always accumulate in FP64.
+ * complex64 (2 x float) for GP_C64; GP_CFF exchanges complex128 through
+ * gp_load / gp_store (see GP_CFF below).  Reductions always accumulate in
+ * FP64.
  *
  * Conventions: every int-returning call returns GP_OK (0) or a negative GP_E*
  * code and never throws; gp_last_error() gives a message for the last failure
@@ -63,7 +65,22 @@ typedef struct {
 #define GP_MAX_EDGE 8192
 
 enum { GP_IMAG = 0, GP_REAL = 1 };           /* propagation mode            */
-enum { GP_C128 = 0, GP_C64 = 1 };            /* psi / sweep precision       */
+/*
+ * psi / sweep precision.  GP_C128: complex128 psi, FP64 arithmetic.
+ * GP_C64: complex64 psi and sweeps, FP64 tables and reductions.
+ * GP_CFF: the FP64-class float-float form -- psi is kept on the device as
+ * float-float pairs (per point four floats: re_hi, im_hi, re_lo, im_lo,
+ * re = re_hi + re_lo, about 48 significant bits) and every sweep and calcnu
+ * runs in FP32 error-free arithmetic (TwoSum, FMA TwoProduct) on the FP32
+ * pipe, which GB300 executes 64 times faster than FP64; tables and
+ * reductions are FP64.  gp_load and gp_store exchange complex128 values;
+ * gp_device_psi exposes the float-float buffer.  Cartesian grids only, the
+ * TMA sweep path only (GP_OPT_SWEEP_PATH accepts GP_PATH_AUTO and
+ * GP_PATH_TMA), the plain splitting only; gp_create returns GP_EINVAL when
+ * an axis's back-substitution window does not fit one 8-point chunk
+ * (max|c'|^9 >= 2^-50, roughly dt / (4 h^2) >= 0.02).
+ */
+enum { GP_C128 = 0, GP_C64 = 1, GP_CFF = 2 };
 
 enum {
     GP_OK = 0,
@@ -309,6 +326,22 @@ int gp_footprint_axial(int nr, int nz, int precision, size_t *bytes);
 
 /* Bytes of device memory gp_create allocates for this grid and precision. */
 int gp_footprint(const gp_grid *grid, int precision, size_t *bytes);
+
+/*
+ * Arithmetic-rate microbenchmark of the current device.  The paper has no
+ * counterpart: the sweeps of the complex128 form are bound by the FP64 pipe,
+ * and those of the float-float form by the FP32 pipe, so their rooflines are
+ * taken against these measured rates.  kind GP_PEAK_FP64_FMA (DFMA),
+ * GP_PEAK_FP32_FMA (FFMA) or GP_PEAK_FP32X2_FMA (packed two-lane FFMA2);
+ * every CTA slot of the device runs `iters` >= 1 rounds of 8 independent
+ * multiply-add chains per thread.  *tflops receives the best of 3 timed
+ * launches (CUDA events, 2 flops per multiply-add) and *ms (may be NULL)
+ * that launch's milliseconds.  Allocates 8 bytes of device memory and a
+ * stream for the call; synchronises.  GP_EINVAL for a bad kind or count,
+ * GP_ECUDA / GP_ENOMEM on CUDA failures (message in gp_last_error(NULL)).
+ */
+enum { GP_PEAK_FP64_FMA = 0, GP_PEAK_FP32_FMA = 1, GP_PEAK_FP32X2_FMA = 2 };
+int gp_measure_peak(int kind, int64_t iters, double *tflops, double *ms);
 
 /* Message for the last failure on ctx ("" if none); ctx may be NULL for the
  * last failure of a gp_create in this thread. */

@@ -65,6 +65,11 @@ struct gp_ctx {
     double *host_sums = nullptr;    // pinned
     int *host_err = nullptr;        // pinned
 
+    // float-float form (GP_CFF): expanded Crank-Nicolson and x-factor tables
+    gp::FfAxis ffax[2][3];          // [mode][axis]
+    gp::FfCoef *ffpx[2][3]{};       // [mode][axis] exp(-tau w_k^2 x^2 / 2), expanded
+    void *ffmem = nullptr;          // one allocation for all of them
+
     CUtensorMap maps[3];            // 64-byte aligned type
     bool map_ok[3]{};
     bool tma_ok[2][3]{};            // [mode][axis] TMA path eligible
@@ -112,7 +117,21 @@ bool valid_grid(const gp_grid *g)
 
 long long points(const gp_grid &g) { return (long long)g.nx * g.ny * g.nz; }
 
-size_t elem_bytes(int prec) { return prec == GP_C128 ? 16 : 8; }
+size_t elem_bytes(int prec) { return prec == GP_C64 ? 8 : 16; }
+
+bool is_ff(const gp_ctx *c) { return c->prec == GP_CFF; }
+
+// Number of float-float coefficients the context keeps: per mode and axis,
+// c' and mult (m each) and the factor table (n).
+size_t ff_coefs(const gp_grid &g)
+{
+    size_t n = 0;
+    for (int k = 0; k < 3; ++k) {
+        const size_t e = k == 0 ? g.nx : (k == 1 ? g.ny : g.nz);
+        n += 2 * (2 * (e - 1 + (e == 1 ? 1 : 0)) + e);
+    }
+    return n;
+}
 
 double coord(int n, double h, int i) { return n == 1 ? 0.0 : -0.5 * n * h + i * h; }
 
@@ -182,6 +201,19 @@ int upload_tables(gp_ctx *c)
             GP_CK(c, cudaMemcpy(d_mult64, mult.data(), m * sizeof(double2), cudaMemcpyHostToDevice));
             GP_CK(c, cudaMemcpy(d_cp32, cp32.data(), m * sizeof(float4), cudaMemcpyHostToDevice));
             GP_CK(c, cudaMemcpy(d_mult32, mult32.data(), m * sizeof(float4), cudaMemcpyHostToDevice));
+            if (is_ff(c)) {
+                gp::FfAxis &f = c->ffax[mode][k];
+                gp::FfCoef *d_cp = f.cp, *d_mult = f.mult;
+                std::vector<gp::FfCoef> fcp(m), fmult(m);
+                double cmax = 0.0;
+                for (int i = 0; i < m; ++i) cmax = std::max(cmax, std::hypot(cp[i].x, cp[i].y));
+                gp::ff_tables(m, cp.data(), mult.data(), a.conv64, cmax, kap, gp::ff_chunk(0), f,
+                              fcp.data(), fmult.data());
+                f.cp = d_cp;
+                f.mult = d_mult;
+                GP_CK(c, cudaMemcpy(d_cp, fcp.data(), m * sizeof(gp::FfCoef), cudaMemcpyHostToDevice));
+                GP_CK(c, cudaMemcpy(d_mult, fmult.data(), m * sizeof(gp::FfCoef), cudaMemcpyHostToDevice));
+            }
         }
     }
     {
@@ -211,6 +243,11 @@ int upload_tables(gp_ctx *c)
             }
             GP_CK(c, cudaMemcpy(c->ph[mode][k], t.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
             GP_CK(c, cudaMemcpy(c->ph32[mode][k], t32.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+            if (is_ff(c)) {
+                std::vector<gp::FfCoef> tf(n);
+                for (int i = 0; i < n; ++i) tf[i] = gp::ff_expand(t[i]);
+                GP_CK(c, cudaMemcpy(c->ffpx[mode][k], tf.data(), n * sizeof(gp::FfCoef), cudaMemcpyHostToDevice));
+            }
             for (int i = 0; i < n; ++i) {
                 const double x = axis_coord(c, k, i);
                 const double th = 0.5 * (c->dt * 0.5 * c->w[k] * c->w[k] * x * x);
@@ -335,6 +372,18 @@ void setup_tma(gp_ctx *c)
         }
         return;
     }
+    if (is_ff(c)) {
+        for (int k = 0; k < naxes(c->grid); ++k) {
+            c->map_ok[k] = gp::make_ff_map(c->tile_shape, c->psi, c->grid.nx, c->grid.ny,
+                                           c->grid.nz, k, &c->maps[k]) == cudaSuccess;
+            cudaGetLastError();
+            for (int mode = 0; mode < 2; ++mode) {
+                const int w = c->ffax[mode][k].win;
+                c->tma_ok[mode][k] = c->map_ok[k] && w >= 1 && w <= gp::ff_chunk(c->tile_shape);
+            }
+        }
+        return;
+    }
     const int C = gp::tma_chunk(c->prec, c->tile_shape);
     for (int k = 0; k < naxes(c->grid); ++k) {
         c->map_ok[k] = gp::make_sweep_map(c->prec, c->tile_shape, c->psi, c->grid.nx, c->grid.ny,
@@ -361,9 +410,13 @@ size_t footprint_bytes(const gp_grid &g, int prec)
                   2 * n * sizeof(float);
     }
     int blocks = 0;
-    for (int k = 0; k < naxes(g); ++k)
+    for (int k = 0; k < naxes(g); ++k) {
         for (int sh = 0; sh < gp::tma_shapes(prec); ++sh)
             blocks = std::max({blocks, gp::sweep_blocks(geom(g, k)), gp::tma_blocks(prec, sh, geom(g, k))});
+        if (prec == GP_CFF)
+            for (int sh = 0; sh < gp::ff_shapes(); ++sh) blocks = std::max(blocks, gp::ff_blocks(sh, geom(g, k)));
+    }
+    if (prec == GP_CFF) tables += ff_coefs(g) * sizeof(gp::FfCoef);
     blocks = std::max(blocks, gp::kReduceBlocks);
     gp::ObsArgs oa{};
     oa.nx = g.nx;
@@ -378,12 +431,24 @@ size_t footprint_bytes(const gp_grid &g, int prec)
     return (prec == GP_C128 ? 3 : 2) * psi + tables + red;
 }
 
+// ---- float-float form: conversions at the boundary ------------------------
+
+// psi <- scale * psi (float-float), scale <- 1, through the complex128 work buffer
+cudaError_t ff_rescale(gp_ctx *c)
+{
+    const long long n = points(c->grid);
+    cudaError_t e = gp::launch_ff_to_c128(c->work, c->psi, n, c->scale, c->stream);
+    if (e == cudaSuccess) e = gp::launch_ff_from_c128(c->psi, c->work, n, nullptr, c->scale, c->stream);
+    return e;
+}
+
 void release(gp_ctx *c)
 {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     auto fr = [](void *p) { if (p) cudaFree(p); };
     fr(c->psi);
     fr(c->work);
+    fr(c->ffmem);
     for (auto &row : c->ax)
         for (auto &a : row) { fr(a.cp64); fr(a.mult64); fr(a.cp32); fr(a.mult32); }
     for (int mode = 0; mode < 2; ++mode)
@@ -422,7 +487,7 @@ void release(gp_ctx *c)
 // plane fits one CTA)
 bool slab_ok(const gp_ctx *c)
 {
-    return !c->axial && c->grid.nz > 1 && gp::slab_fits(c->prec, c->grid.nx, c->grid.ny);
+    return !c->axial && !is_ff(c) && c->grid.nz > 1 && gp::slab_fits(c->prec, c->grid.nx, c->grid.ny);
 }
 
 int sweep_path(const gp_ctx *c, int axis)
@@ -431,6 +496,7 @@ int sweep_path(const gp_ctx *c, int axis)
         const bool seg = c->seg_ok[c->mode] && c->path_opt != GP_PATH_EXACT;
         return seg ? GP_PATH_WINDOW : GP_PATH_EXACT;
     }
+    if (is_ff(c)) return GP_PATH_TMA;      // the float-float form has one sweep path
     if (c->path_opt == GP_PATH_SLAB && axis < 2 && slab_ok(c)) return GP_PATH_SLAB;
     if (!c->tma_ok[c->mode][axis]) return GP_PATH_EXACT;
     if (c->path_opt == GP_PATH_EXACT) return GP_PATH_EXACT;
@@ -451,6 +517,20 @@ cudaError_t launch_sweep(gp_ctx *c, int axis, const gp::NonlinArgs *nl, bool nl_
     }
     const SweepGeom g = geom(c->grid, axis);
     const gp::AxisTables &ax = c->ax[c->mode][axis];
+    if (is_ff(c)) {
+        if (nl_at_output) return cudaErrorInvalidValue;
+        gp::FfNonlin fn;
+        if (nl) {
+            fn.px = c->ffpx[c->mode][0];
+            fn.py = nl->py;
+            fn.pz = nl->pz;
+            fn.g = nl->g;
+            fn.scale = nl->scale;
+        }
+        if (blocks) *blocks = gp::ff_blocks(c->tile_shape, g);
+        return gp::launch_sweep_ff(c->tile_shape, c->mode, axis, c->maps[axis], c->ffax[c->mode][axis],
+                                   g, nl ? &fn : nullptr, norm, c->err_dev, c->stream);
+    }
     if (sweep_path(c, axis) == GP_PATH_TMA) {
         if (blocks) *blocks = gp::tma_blocks(c->prec, c->tile_shape, g);
         return gp::launch_sweep_tma(c->prec, c->tile_shape, c->mode, axis, c->maps[axis], ax, g,
@@ -652,7 +732,8 @@ void build_graph(gp_ctx *c)
 int materialize_scale(gp_ctx *c)
 {
     if (!c->scale_pending) return GP_OK;
-    GP_CK(c, gp::launch_apply_scale(c->prec, c->psi, points(c->grid), c->scale, c->stream));
+    if (is_ff(c)) GP_CK(c, ff_rescale(c));
+    else GP_CK(c, gp::launch_apply_scale(c->prec, c->psi, points(c->grid), c->scale, c->stream));
     c->scale_pending = false;
     return GP_OK;
 }
@@ -681,7 +762,12 @@ int enqueue_observables(gp_ctx *c)
     if (c->axial)
         GP_CK(c, gp::launch_observables_axial(c->psi, obs_args(c), c->h[0], c->obs_partials,
                                               c->sums, c->stream));
-    else
+    else if (is_ff(c)) {
+        // FP64 observables of the float-float state (hi + lo) through the work buffer
+        GP_CK(c, gp::launch_ff_to_c128(c->work, c->psi, points(c->grid), nullptr, c->stream));
+        GP_CK(c, gp::launch_observables(GP_C128, c->work, obs_args(c), c->obs_partials, c->sums,
+                                        c->stream));
+    } else
         GP_CK(c, gp::launch_observables(c->prec, c->psi, obs_args(c), c->obs_partials, c->sums,
                                         c->stream));
     GP_CK(c, cudaMemcpyAsync(c->host_sums, c->sums, gp::kObsWidth * sizeof(double),
@@ -793,7 +879,8 @@ extern "C" {
 
 int gp_footprint(const gp_grid *grid, int precision, size_t *bytes)
 {
-    if (!valid_grid(grid) || (precision != GP_C128 && precision != GP_C64) || !bytes)
+    if (!valid_grid(grid) || (precision != GP_C128 && precision != GP_C64 && precision != GP_CFF) ||
+        !bytes)
         return fail(nullptr, GP_EINVAL, "gp_footprint: invalid grid or precision");
     *bytes = footprint_bytes(*grid, precision);
     return GP_OK;
@@ -860,7 +947,7 @@ int create_ctx(const gp_grid *grid, const double dx[3], double dt, double gamma,
         !std::isfinite(g))
         return fail(nullptr, GP_EINVAL, "gp_create: trap frequencies must be >= 0 and g finite");
     if (mode != GP_IMAG && mode != GP_REAL) return fail(nullptr, GP_EINVAL, "gp_create: bad mode");
-    if (precision != GP_C128 && precision != GP_C64)
+    if (precision != GP_C128 && precision != GP_C64 && (precision != GP_CFF || axial))
         return fail(nullptr, GP_EINVAL, "gp_create: bad precision");
 
     gp_ctx *c = new (std::nothrow) gp_ctx;
@@ -916,6 +1003,22 @@ int create_ctx(const gp_grid *grid, const double dx[3], double dt, double gamma,
         if ((rc = alloc(c, (void **)&c->th32[k], edge(c->grid, k) * sizeof(float)))) return bail(rc);
         if ((rc = alloc(c, (void **)&c->thh32[k], edge(c->grid, k) * sizeof(float)))) return bail(rc);
     }
+    if (precision == GP_CFF) {
+        if ((rc = alloc(c, &c->ffmem, ff_coefs(c->grid) * sizeof(gp::FfCoef)))) return bail(rc);
+        gp::FfCoef *q = static_cast<gp::FfCoef *>(c->ffmem);
+        for (int mode_i = 0; mode_i < 2; ++mode_i)
+            for (int k = 0; k < 3; ++k) {
+                const int n = edge(c->grid, k);
+                if (k < naxes(c->grid)) {
+                    c->ffax[mode_i][k].cp = q;
+                    q += n - 1;
+                    c->ffax[mode_i][k].mult = q;
+                    q += n - 1;
+                }
+                c->ffpx[mode_i][k] = q;
+                q += n;
+            }
+    }
     if ((rc = alloc(c, (void **)&c->step_dev, sizeof(long long)))) return bail(rc);
     if (axial) {
         const size_t m = grid->nx;
@@ -925,10 +1028,14 @@ int create_ctx(const gp_grid *grid, const double dx[3], double dt, double gamma,
         if ((rc = alloc(c, (void **)&c->rho_w, m * sizeof(double)))) return bail(rc);
     }
     int blocks = gp::kReduceBlocks;
-    for (int k = 0; k < naxes(c->grid); ++k)
+    for (int k = 0; k < naxes(c->grid); ++k) {
         for (int sh = 0; sh < gp::tma_shapes(precision); ++sh)
             blocks = std::max({blocks, gp::sweep_blocks(geom(c->grid, k)),
                                gp::tma_blocks(precision, sh, geom(c->grid, k))});
+        if (precision == GP_CFF)
+            for (int sh = 0; sh < gp::ff_shapes(); ++sh)
+                blocks = std::max(blocks, gp::ff_blocks(sh, geom(c->grid, k)));
+    }
     c->partial_cap = blocks;
     if ((rc = alloc(c, (void **)&c->partials, blocks * sizeof(double)))) return bail(rc);
     {
@@ -954,6 +1061,15 @@ int create_ctx(const gp_grid *grid, const double dx[3], double dt, double gamma,
     if ((rc = upload_tables(c))) return bail(rc);
     if (axial && (rc = setup_segments(c))) return bail(rc);
     setup_tma(c);
+    if (precision == GP_CFF)
+        for (int mode_i = 0; mode_i < 2; ++mode_i)
+            for (int k = 0; k < naxes(c->grid); ++k)
+                if (!c->tma_ok[mode_i][k]) {
+                    fail(c, GP_EINVAL, "gp_create: the float-float form needs every axis's "
+                                       "back-substitution window within one chunk "
+                                       "(max|c'|^9 < 2^-50, about dt / (4 h^2) < 0.02)");
+                    return bail(GP_EINVAL);
+                }
     {
         cudaError_t e = cudaMemsetAsync(c->psi, 0, psi_bytes, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
@@ -983,6 +1099,16 @@ int gp_load(gp_ctx *c, const void *psi, int64_t count, int on_device)
                                            c->w[0], c->w[1], c->stream));
             GP_CK(c, gp::launch_norm_partials_axial(c->psi, c->grid.nx, c->grid.ny, c->h[0], part,
                                                     gp::kReduceBlocks, c->stream));
+        } else if (is_ff(c)) {
+            // the seed in FP64 in the work buffer, normalised into psi
+            GP_CK(c, gp::launch_seed(GP_C128, c->work, c->grid.nx, c->grid.ny, c->grid.nz, c->h,
+                                     c->w, c->stream));
+            GP_CK(c, gp::launch_norm_partials(GP_C128, c->work, n, part, gp::kReduceBlocks,
+                                              c->stream));
+            GP_CK(c, gp::launch_norm_finish(c->partials, gp::kReduceBlocks, cell_volume(c), c->scale,
+                                            c->norm_dev, c->err_dev, c->stream));
+            GP_CK(c, gp::launch_ff_from_c128(c->psi, c->work, n, c->scale, c->scale, c->stream));
+            return GP_OK;
         } else {
             GP_CK(c, gp::launch_seed(c->prec, c->psi, c->grid.nx, c->grid.ny, c->grid.nz, c->h,
                                      c->w, c->stream));
@@ -995,6 +1121,17 @@ int gp_load(gp_ctx *c, const void *psi, int64_t count, int on_device)
         return materialize_scale(c);
     }
     if (count != n) return fail(c, GP_EINVAL, "gp_load: count != nx*ny*nz");
+    if (is_ff(c)) {
+        // complex128 in, split into float-float pairs
+        GP_CK(c, cudaMemcpyAsync(c->work, psi, (size_t)n * sizeof(double2),
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                 c->stream));
+        GP_CK(c, gp::launch_zero_boundary(GP_C128, c->work, c->grid.nx, c->grid.ny, c->grid.nz,
+                                          c->stream));
+        GP_CK(c, gp::launch_ff_from_c128(c->psi, c->work, n, nullptr, c->scale, c->stream));
+        GP_CK(c, cudaStreamSynchronize(c->stream));   // the caller's buffer
+        return GP_OK;
+    }
     GP_CK(c, cudaMemcpyAsync(c->psi, psi, (size_t)n * elem_bytes(c->prec),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              c->stream));
@@ -1011,6 +1148,15 @@ int gp_store(gp_ctx *c, void *out, int64_t count, int on_device)
     if (!c || !out) return fail(c, GP_EINVAL, "gp_store: null argument");
     const long long n = points(c->grid);
     if (count != n) return fail(c, GP_EINVAL, "gp_store: count != nx*ny*nz");
+    if (is_ff(c)) {
+        // hi + lo in FP64, times the pending scale
+        void *dst = on_device ? out : c->work;
+        GP_CK(c, gp::launch_ff_to_c128(dst, c->psi, n, c->scale, c->stream));
+        if (!on_device)
+            GP_CK(c, cudaMemcpyAsync(out, c->work, (size_t)n * sizeof(double2), cudaMemcpyDeviceToHost,
+                                     c->stream));
+        return read_errors(c);
+    }
     int rc = materialize_scale(c);
     if (rc) return rc;
     GP_CK(c, cudaMemcpyAsync(out, c->psi, (size_t)n * elem_bytes(c->prec),
@@ -1075,7 +1221,7 @@ int gp_observables(gp_ctx *c, gp_obs *o)
     int rc = read_errors(c);
     double s[gp::kObsWidth];
     std::memcpy(s, c->host_sums, sizeof(s));
-    if (c->prec == GP_C128 && !c->axial)
+    if (c->prec != GP_C64 && !c->axial)
         for (int k = 6; k < 9; ++k) s[k] = 2.0 * s[0] - 2.0 * s[k];     // K_k from R_k
     const double w = cell_volume(c);
     const double n = w * s[0];
@@ -1152,6 +1298,8 @@ int gp_set_option(gp_ctx *c, int option, int value)
     if (option == GP_OPT_SPLITTING) {
         if (value != GP_SPLIT_LIE && value != GP_SPLIT_STRANG)
             return fail(c, GP_EINVAL, "gp_set_option: unknown splitting");
+        if (value == GP_SPLIT_STRANG && is_ff(c))
+            return fail(c, GP_EINVAL, "gp_set_option: the float-float form runs the plain splitting");
         c->split = value;
         drop_graph(c);
         return GP_OK;
@@ -1169,10 +1317,16 @@ int gp_set_option(gp_ctx *c, int option, int value)
         return GP_OK;
     }
     if (option == GP_OPT_TILE_SHAPE) {
-        if (value < 0 || value >= gp::tma_shapes(c->prec))
+        if (value < 0 || value >= (is_ff(c) ? gp::ff_shapes() : gp::tma_shapes(c->prec)))
             return fail(c, GP_EINVAL, "gp_set_option: tile shape out of range");
+        const int old = c->tile_shape;
         c->tile_shape = value;
         setup_tma(c);
+        if (is_ff(c) && !c->tma_ok[c->mode][0]) {
+            c->tile_shape = old;
+            setup_tma(c);
+            return fail(c, GP_EINVAL, "gp_set_option: tile shape does not apply to this grid");
+        }
         if (c->path_opt == GP_PATH_TMA)
             for (int k = 0; k < naxes(c->grid); ++k)
                 if (!c->tma_ok[c->mode][k]) c->path_opt = GP_PATH_AUTO;
@@ -1191,6 +1345,8 @@ int gp_set_option(gp_ctx *c, int option, int value)
                                   "with long enough lines");
     if (value == GP_PATH_TMA && c->axial)
         return fail(c, GP_EINVAL, "gp_set_option: no TMA sweep path on the axial form");
+    if (is_ff(c) && value != GP_PATH_AUTO && value != GP_PATH_TMA)
+        return fail(c, GP_EINVAL, "gp_set_option: the float-float form has the TMA sweep path only");
     if (value == GP_PATH_TMA)
         for (int k = 0; k < naxes(c->grid); ++k)
             if (!c->tma_ok[c->mode][k])
@@ -1227,15 +1383,20 @@ int gp_autotune(gp_ctx *c, int steps, int *path_out, int *shape_out, double *ms_
         return cuda_fail(c, e, "gp_autotune: save state");
     }
     struct Cand { int path, shape; };
-    std::vector<Cand> cands{{GP_PATH_EXACT, shape0}};
+    std::vector<Cand> cands;
+    if (!is_ff(c)) cands.push_back({GP_PATH_EXACT, shape0});
     if (c->axial && c->seg_ok[c->mode]) cands.push_back({GP_PATH_WINDOW, shape0});
     if (slab_ok(c)) cands.push_back({GP_PATH_SLAB, shape0});
-    for (int sh = 0; sh < gp::tma_shapes(c->prec); ++sh) {
+    for (int sh = 0; sh < (is_ff(c) ? gp::ff_shapes() : gp::tma_shapes(c->prec)); ++sh) {
         c->tile_shape = sh;
         setup_tma(c);
         bool ok = true;
         for (int k = 0; k < naxes(c->grid); ++k) ok = ok && c->tma_ok[c->mode][k];
         if (ok) cands.push_back({GP_PATH_TMA, sh});
+    }
+    if (cands.empty()) {
+        cleanup();
+        return fail(c, GP_EINTERNAL, "gp_autotune: no eligible sweep path");
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1304,9 +1465,9 @@ int gp_get_option(gp_ctx *c, int option, int *value)
 
 int gp_tile_shapes(int precision, int *count)
 {
-    if ((precision != GP_C128 && precision != GP_C64) || !count)
+    if ((precision != GP_C128 && precision != GP_C64 && precision != GP_CFF) || !count)
         return fail(nullptr, GP_EINVAL, "gp_tile_shapes: bad precision");
-    *count = gp::tma_shapes(precision);
+    *count = precision == GP_CFF ? gp::ff_shapes() : gp::tma_shapes(precision);
     return GP_OK;
 }
 

@@ -1,0 +1,606 @@
+// sscn_ff.cu -- the FP64-class form of the Crank-Nicolson sweeps (calclux,
+// calcluy, calcluz, with calcnu fused into the x sweep) in float-float
+// arithmetic on the FP32 pipe, sm_103a.
+//
+// GB300 executes FP64 at 2 multiply-adds per clock per SM against 128 for
+// FP32, so FP64 sweeps are bound by the FP64 pipe at a small fraction of the
+// HBM bandwidth.  This form carries psi and every recurrence as float-float
+// values (hi + lo, ~48 significant bits; sscn_ff.cuh), which keeps the
+// result within the FP64 tolerances while the sweeps run on the FP32 pipe.
+//
+// The pipeline is the TMA-staged one of the complex64 sweeps: one CTA owns a
+// tile of L = 32 K lines (one consumer thread per line), a producer warp
+// streams chunks of C = 8 points of all L lines through an S-stage
+// shared-memory ring (cp.async.bulk.tensor, one mbarrier per stage) and
+// stores finished chunks back with TMA stores.  Each consumer runs the
+// forward elimination of its line, (I - kappa L) v = psi,
+//     d'_i = (psi_i + kappa d'_{i-1}) mult_i,
+// keeps d' for the last two chunks in shared memory, and back-substitutes
+// over a window: the values of chunk q-1 are produced after the forward pass
+// of chunk q, from v ~ d' at W points into chunk q,
+//     v_i = d'_i - c'_i v_{i+1},   u_i = 2 v_i - psi_i,
+// which is the Crank-Nicolson update (I + kappa L) = 2 I - (I - kappa L).
+// The dropped term decays as |c'|^(W+1); the host picks W <= C with
+// max|c'|^(W+1) < 2^-50, below the float-float rounding.  The last chunks
+// are back-substituted exactly from v_m = d'_m.
+//
+// calcnu (real time): psi <- P_x[i] P_y[j] P_z[k] (1 + delta) psi with the
+// unit-modulus factor tables P_k = exp(-i dt omega_k^2 x^2 / 2) and
+// delta = exp(-i a) - 1, a = G |psi|^2 (G the integral of g over the step),
+// from its Taylor series for |a| < 2^-8 (first dropped terms below 2^-57)
+// and through FP64 sincos beyond.  Imaginary time: the real factor
+// s P_x P_y P_z (1 + eps), eps = exp(-a) - 1, a = G s^2 |psi|^2, s the
+// pending renormalisation scale.
+
+#include <cstdint>
+#include <cstring>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include "sscn_ff.cuh"
+#include "sscn_internal.h"
+#include "sscn_tma.cuh"
+
+namespace gp {
+namespace {
+
+using namespace gp::tma;
+using namespace gp::ff;
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per chunk wait
+constexpr int kErrTimeout = 2;
+constexpr int kC = 8;                              // points per chunk (128-byte x rows)
+
+struct FfArgs {
+    int n;                  // stored points per line (m = n - 1 unknowns)
+    int lines_a;            // extent of the in-tile line index
+    int win, conv;          // window W (1 .. C), first constant table index
+    FfCoef cinf, minf;      // the constants past conv
+    const FfCoef *cp, *mult;
+    float2 kk_hi, kk_lo;    // kappa per lane: (k, k) imaginary, (-k, k) real time
+    const FfCoef *px;       // calcnu (x sweep)
+    const double2 *py, *pz;
+    StepG g;
+    const double *scale;
+    double *partials;       // norm partials (NORM)
+    int *err;
+};
+
+__device__ __forceinline__ C ld(const unsigned char *p)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return C{f2(v.x, v.y), f2(v.z, v.w)};
+}
+__device__ __forceinline__ void st(unsigned char *p, C z)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(z.hi.x, z.hi.y, z.lo.x, z.lo.y);
+}
+
+// Crank-Nicolson line steps.  MODE 0: kappa = k, real tables.  MODE 1:
+// kappa = i k, complex tables.
+template <int MODE> struct FfLine {
+    float2 kh, kl;
+    // (p + kappa d) mult
+    __device__ __forceinline__ C fwd(C p, C d, const FfCoef &f) const
+    {
+        if (MODE == 0) return rmul(add(p, lmul(d, kh, kl)), f);
+        return cmul(add(p, imul(d, kh, kl)), f);
+    }
+    // d - c' v
+    __device__ __forceinline__ C back(C d, const FfCoef &c, C v) const
+    {
+        if (MODE == 0) return sub(d, rmul(v, c));
+        return sub(d, cmul(v, c));
+    }
+};
+
+// calcnu at one point of an x line (see the file comment).
+template <int MODE> struct FfCalcnu {
+    const FfCoef *px;
+    FfCoef pyz;          // P_y[j] P_z[k] (times s in imaginary time), expanded
+    float2 acoef;        // G (times s^2 in imaginary time)
+    float2 fyz;          // imaginary time: s P_y[j] P_z[k] as a scalar pair
+
+    __device__ __forceinline__ void setup(const FfArgs &a, int j, int k)
+    {
+        px = a.px;
+        const double2 y = a.py[j], z = a.pz[k];
+        const double G = a.g.value();
+        if (MODE == 0) {
+            const double s = a.scale ? *a.scale : 1.0;
+            const double f = s * y.x * z.x;
+            fyz = split(f);
+            acoef = split(G * s * s);
+            pyz = expand(f, 0.0);
+        } else {
+            pyz = expand(y.x * z.x - y.y * z.y, y.x * z.y + y.y * z.x);
+            acoef = split(G);
+            fyz = f2(0.f, 0.f);
+        }
+    }
+
+    __device__ __forceinline__ C apply(C p, int i) const
+    {
+        const float2 a = s_mul(acoef, abs2(p));
+        if (MODE == 0) {
+            // eps = exp(-a) - 1 = -a + a^2/2 - a^3/6 + a^4/24 - a^5/120 + ...
+            float2 eps;
+            if (fabsf(a.x) < 0x1p-8f) {
+                const float q = __fmul_rn(a.x, a.x);
+                float qe = fmaf(a.x, a.x, -q);
+                qe = fmaf(2.f * a.x, a.y, qe);
+                eps = s_two_sum(-a.x, 0.5f * q);
+                const float tail = fmaf(q, fmaf(a.x, -1.f / 120, 1.f / 24) * q, -a.x * q * (1.f / 6));
+                eps = s_norm(f2(eps.x, eps.y + ((0.5f * qe - a.y) + tail)));
+            } else {
+                eps = split(expm1(-join(a)));
+            }
+            const FfCoef &x = px[i];
+            const float2 f = s_mul(fyz, f2(x.rh.x, x.rl.x));
+            const float2 F = s_norm(s_add(f, s_mul(f, eps)));
+            return norm(lmul(p, f2(F.x, F.x), f2(F.y, F.y)));
+        }
+        // delta = exp(-i a) - 1 = (cos a - 1) - i sin a
+        float2 dr, di;
+        if (fabsf(a.x) < 0x1p-8f) {
+            const float q = __fmul_rn(a.x, a.x);
+            float qe = fmaf(a.x, a.x, -q);
+            qe = fmaf(2.f * a.x, a.y, qe);
+            // cos a - 1 = -a^2/2 + a^4/24 - ...   (a^6/720 < 2^-57)
+            dr = f2(-0.5f * q, fmaf(q * q, 1.f / 24, -0.5f * qe));
+            // -sin a = -a + a^3/6 - a^5/120 + ...  (a^7/5040 < 2^-68)
+            di = f2(-a.x, fmaf(a.x * q, fmaf(q, -1.f / 120, 1.f / 6), -a.y));
+        } else {
+            double sh, ch;
+            sincos(0.5 * join(a), &sh, &ch);
+            dr = split(-2.0 * sh * sh);
+            di = split(-2.0 * sh * ch);
+        }
+        const FfCoef D{f2(dr.x, dr.x), f2(dr.y, dr.y), f2(-di.x, di.x), f2(-di.y, di.y)};
+        const C q2 = cmul(cmul(p, px[i]), pyz);
+        return norm(add(q2, cmul(q2, D)));
+    }
+};
+
+template <int L, int AXIS> struct FfTile {
+    static constexpr int E = 16;
+    static constexpr int kStageBytes = L * kC * E;
+    static __device__ __forceinline__ int off(int l, int c)
+    {
+        if (AXIS == 0) return l * (kC * E) + ((c ^ (l & 7)) << 4);   // 128-byte swizzle
+        return (c * L + l) * E;
+    }
+};
+
+// Warp-specialised CTA: K consumer warps own L = 32 K lines; warp K is the
+// producer, whose lane 0 issues every TMA load and store.  full[s] completes
+// when a chunk has landed, ready[s] when all K consumer warps have written
+// the chunk's final values; the producer stores a ready chunk and reuses its
+// stage once the store has read shared memory.
+template <int MODE, int AXIS, bool NL, bool NORM, int K, int S>
+__global__ void __launch_bounds__(32 * (K + 1))
+k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
+{
+    constexpr int L = 32 * K;
+    constexpr int Cc = kC;
+    using G = FfTile<L, AXIS>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *stages = smem;
+    float4 *ring = reinterpret_cast<float4 *>(stages + S * G::kStageBytes);   // [2][C][L]
+    uint64_t *full = reinterpret_cast<uint64_t *>(ring + 2 * Cc * L);
+    uint64_t *ready = full + S;
+    double *red = reinterpret_cast<double *>(ready + S);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool producer = warp == K;
+    const int l = producer ? 0 : threadIdx.x;
+    const int tile0 = blockIdx.x * L;
+    const int a = tile0 + l;
+    const bool active = !producer && a < args.lines_a;
+    const int m = args.n - 1;
+    const int Q = (args.n + Cc - 1) / Cc;
+    const int conv = args.conv, win = args.win;
+
+    auto coords = [&](int q, int &c0, int &c1, int &c2) {
+        if (AXIS == 0) { c0 = q * Cc * 2; c1 = tile0; c2 = blockIdx.y; }
+        else if (AXIS == 1) { c0 = tile0 * 2; c1 = q * Cc; c2 = blockIdx.y; }
+        else { c0 = tile0 * 2; c1 = blockIdx.y; c2 = q * Cc; }
+    };
+    auto stage_ptr = [&](int q) { return stages + (q % S) * G::kStageBytes; };
+    auto at = [&](int q, int c) { return stage_ptr(q) + G::off(l, c); };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&ready[s], K);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    bool failed = false;
+    float2 nacc = f2(0.f, 0.f);        // float-float sum of |u|^2 (NORM)
+    if (producer) {
+        if (lane == 0) {
+            auto store = [&](int q) {
+                int c0, c1, c2;
+                coords(q, c0, c1, c2);
+                tma_store_3d(&map, stage_ptr(q), c0, c1, c2);
+                bulk_commit();
+            };
+            for (int q = 0; q < Q && !failed; ++q) {
+                if (q >= S) {
+                    const int o = q - S;
+                    if (!mbar_wait_bounded(&ready[o % S], (uint32_t)((o / S) & 1), kWaitLimitNs)) {
+                        failed = true;
+                        break;
+                    }
+                    store(o);
+                    bulk_wait_read<0>();
+                }
+                int c0, c1, c2;
+                coords(q, c0, c1, c2);
+                mbar_arrive_expect_tx(&full[q % S], G::kStageBytes);
+                tma_load_3d(stage_ptr(q), &map, &full[q % S], c0, c1, c2);
+            }
+            for (int o = Q > S ? Q - S : 0; o < Q && !failed; ++o) {
+                if (!mbar_wait_bounded(&ready[o % S], (uint32_t)((o / S) & 1), kWaitLimitNs)) {
+                    failed = true;
+                    break;
+                }
+                store(o);
+            }
+            bulk_wait_all();
+        }
+    } else {
+        const FfLine<MODE> cn{args.kk_hi, args.kk_lo};
+        FfCalcnu<MODE> nl;
+        if (NL && active) nl.setup(args, a, blockIdx.y);
+        auto cp = [&](int t) -> FfCoef { return t < conv ? args.cp[t] : args.cinf; };
+        auto mult = [&](int t) -> FfCoef { return t < conv ? args.mult[t] : args.minf; };
+        auto slot = [&](int i) -> float4 * {
+            return ring + ((i / Cc) & 1) * Cc * L + (i % Cc) * L + l;
+        };
+        auto put = [&](int i, C d) { *slot(i) = make_float4(d.hi.x, d.hi.y, d.lo.x, d.lo.y); };
+        auto get = [&](int i) -> C {
+            const float4 v = *slot(i);
+            return C{f2(v.x, v.y), f2(v.z, v.w)};
+        };
+        auto acc_norm = [&](C u) {
+            if (NORM) nacc = s_norm(s_add(nacc, abs2(u)));
+        };
+        auto output = [&](C v, unsigned char *tile_slot) {
+            const C u = twice_minus(v, ld(tile_slot));
+            st(tile_slot, u);
+            acc_norm(u);
+        };
+        C d = cz();
+        for (int q = 0; q < Q; ++q) {
+            if (!mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs)) {
+                failed = true;
+                break;
+            }
+            const bool last = q == Q - 1;
+            const bool fast = active && q >= 2 && !last && (q - 1) * Cc - 1 >= conv &&
+                              (q + 1) * Cc - 1 <= m;
+            if (fast) {
+                // interior chunk: every point an unknown, constant tables
+                const FfCoef minf = args.minf, cinf = args.cinf;
+#pragma unroll
+                for (int c = 0; c < Cc; ++c) {
+                    unsigned char *tc = at(q, c);
+                    C p = ld(tc);
+                    if (NL) {
+                        p = nl.apply(p, q * Cc + c);
+                        st(tc, p);
+                    }
+                    d = cn.fwd(p, d, minf);
+                    put(q * Cc + c, d);
+                }
+                C v = get(q * Cc + win - 1);
+                for (int c = win - 2; c >= 0; --c) v = cn.back(get(q * Cc + c), cinf, v);
+#pragma unroll
+                for (int c = Cc - 1; c >= 0; --c) {
+                    v = cn.back(get((q - 1) * Cc + c), cinf, v);
+                    output(v, at(q - 1, c));
+                }
+            } else {
+                if (active) {
+#pragma unroll 2
+                    for (int c = 0; c < Cc; ++c) {
+                        const int j = q * Cc + c;
+                        if (j >= 1 && j <= m) {
+                            C p = ld(at(q, c));
+                            if (NL) {
+                                p = nl.apply(p, j);
+                                st(at(q, c), p);
+                            }
+                            d = cn.fwd(p, d, mult(j - 1));
+                            put(j, d);
+                        }
+                    }
+                }
+                if (active) {
+                    if (!last && q >= 1) {
+                        C v = get(q * Cc + win - 1);
+                        for (int c = win - 2; c >= 0; --c) v = cn.back(get(q * Cc + c), cp(q * Cc + c - 1), v);
+                        for (int c = Cc - 1; c >= 0; --c) {
+                            const int i = (q - 1) * Cc + c;
+                            if (i < 1) break;
+                            v = cn.back(get(i), cp(i - 1), v);
+                            output(v, at(q - 1, c));
+                        }
+                    } else if (last) {
+                        C v = d;
+                        const int lo = q >= 1 ? (q - 1) * Cc : 0;
+                        for (int i = m; i >= lo && i >= 1; --i) {
+                            if (i < m) v = cn.back(get(i), cp(i - 1), v);
+                            output(v, at(i / Cc, i % Cc));
+                        }
+                    }
+                }
+            }
+            if (q >= 1 || last) {
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    if (q >= 1) mbar_arrive(&ready[(q - 1) % S]);
+                    if (last) mbar_arrive(&ready[q % S]);
+                }
+            }
+        }
+    }
+    if (failed) atomicOr(args.err, kErrTimeout);
+    if (NORM) {
+        double v = join(nacc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double r = lane < K ? red[lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+            if (lane == 0) args.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = r;
+        }
+    }
+}
+
+template <int K, int S>
+constexpr size_t ff_smem_bytes()
+{
+    constexpr size_t L = 32 * K;
+    return 1024 + (size_t)S * L * kC * 16 + 2 * (size_t)kC * L * 16 + 2 * S * sizeof(uint64_t) +
+           32 * sizeof(double);
+}
+
+template <int MODE, int AXIS, bool NL, bool NORM, int K, int S>
+cudaError_t launch_inst(const CUtensorMap &map, const FfArgs &args, int tiles, int lines_b,
+                        cudaStream_t st)
+{
+    auto kern = k_sweep_ff<MODE, AXIS, NL, NORM, K, S>;
+    constexpr size_t smem = ff_smem_bytes<K, S>();
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!configured[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    kern<<<dim3(tiles, lines_b), 32 * (K + 1), smem, st>>>(map, args);
+    return cudaGetLastError();
+}
+
+template <int AXIS, int K, int S>
+cudaError_t launch_axis(int mode, bool nl, bool norm, const CUtensorMap &map, const FfArgs &args,
+                        int tiles, int lines_b, cudaStream_t st)
+{
+    // calcnu rides on the x sweep only
+    if (nl && AXIS != 0) return cudaErrorInvalidValue;
+#define GP_FF(MODE, NLV, NORMV) \
+    return launch_inst<MODE, AXIS, (NLV && AXIS == 0), NORMV, K, S>(map, args, tiles, lines_b, st)
+    if (mode == 0) {
+        if (nl) { if (norm) GP_FF(0, true, true); GP_FF(0, true, false); }
+        if (norm) GP_FF(0, false, true);
+        GP_FF(0, false, false);
+    }
+    if (nl) { if (norm) GP_FF(1, true, true); GP_FF(1, true, false); }
+    if (norm) GP_FF(1, false, true);
+    GP_FF(1, false, false);
+#undef GP_FF
+}
+
+// Tile shapes (consumer warps K, stages S); a CTA owns 32 K lines.
+struct Shape { int K, S; };
+constexpr Shape kShapes[] = {{2, 3}, {1, 4}, {2, 4}, {4, 3}};
+constexpr int kNumShapes = 4;
+
+template <int K, int S>
+cudaError_t launch_shape(int mode, int axis, bool nl, bool norm, const CUtensorMap &map,
+                         const FfArgs &args, int tiles, int lines_b, cudaStream_t st)
+{
+    if (axis == 0) return launch_axis<0, K, S>(mode, nl, norm, map, args, tiles, lines_b, st);
+    if (axis == 1) return launch_axis<1, K, S>(mode, nl, norm, map, args, tiles, lines_b, st);
+    return launch_axis<2, K, S>(mode, nl, norm, map, args, tiles, lines_b, st);
+}
+
+Shape shape_of(int s) { return kShapes[s < 0 || s >= kNumShapes ? 0 : s]; }
+
+// --------------------------------------------------------------- conversions
+
+__global__ void k_ff_from_c128(float4 *__restrict__ dst, const double2 *__restrict__ src,
+                               long long count, const double *scale)
+{
+    const double s = scale ? *scale : 1.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double2 v = src[i];
+        const float2 r = split(s * v.x), im = split(s * v.y);
+        dst[i] = make_float4(r.x, im.x, r.y, im.y);
+    }
+}
+
+__global__ void k_ff_set_one(double *x) { *x = 1.0; }
+
+__global__ void k_ff_to_c128(double2 *__restrict__ dst, const float4 *__restrict__ src,
+                             long long count, const double *scale)
+{
+    const double s = scale ? *scale : 1.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 v = src[i];
+        dst[i] = make_double2(s * ((double)v.x + (double)v.z), s * ((double)v.y + (double)v.w));
+    }
+}
+
+int point_blocks(long long count)
+{
+    const long long b = (count + 255) / 256;
+    return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+}  // namespace
+
+FfCoef ff_expand(double2 v)
+{
+    const float rh = (float)v.x, ih = (float)v.y;
+    const float rl = (float)(v.x - (double)rh), il = (float)(v.y - (double)ih);
+    return FfCoef{make_float2(rh, rh), make_float2(rl, rl), make_float2(-ih, ih), make_float2(-il, il)};
+}
+
+void ff_tables(int m, const double2 *cp64, const double2 *mult64, int conv64, double cmax,
+               double k, int chunk, FfAxis &out, FfCoef *cp, FfCoef *mult)
+{
+    for (int i = 0; i < m; ++i) {
+        cp[i] = ff_expand(cp64[i]);
+        mult[i] = ff_expand(mult64[i]);
+    }
+    out.n = m + 1;
+    out.conv = conv64;
+    out.cinf = cp[m - 1];
+    out.minf = mult[m - 1];
+    out.k = k;
+    // window: smallest W <= chunk with cmax^(W+1) < 2^-50
+    out.win = 0;
+    double p = cmax;
+    for (int w = 1; w <= chunk; ++w) {
+        p *= cmax;
+        if (p < 0x1p-50) {
+            out.win = w;
+            break;
+        }
+    }
+}
+
+int ff_shapes() { return kNumShapes; }
+int ff_chunk(int) { return kC; }
+
+int ff_blocks(int shape, const SweepGeom &g)
+{
+    const int L = 32 * shape_of(shape).K;
+    return ((g.lines_a + L - 1) / L) * g.lines_b;
+}
+
+cudaError_t make_ff_map(int shape, void *psi, int nx, int ny, int nz, int axis, CUtensorMap *out)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const Shape sh = shape_of(shape);
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)2 * nx * 8, (cuuint64_t)2 * nx * ny * 8};
+    cuuint32_t box[3];
+    CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_NONE;
+    const int L = 32 * sh.K;
+    if (axis == 0) { box[0] = 2 * kC; box[1] = L; box[2] = 1; sw = CU_TENSOR_MAP_SWIZZLE_128B; }
+    else if (axis == 1) { box[0] = 2 * L; box[1] = kC; box[2] = 1; }
+    else { box[0] = 2 * L; box[1] = 1; box[2] = kC; }
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, psi, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sweep_ff(int shape, int mode, int axis, const CUtensorMap &map,
+                            const FfAxis &ax, const SweepGeom &g, const FfNonlin *nl,
+                            const Partials *norm_out, int *err, cudaStream_t st)
+{
+    if (ax.win < 1 || ax.win > kC) return cudaErrorInvalidValue;
+    FfArgs args{};
+    args.n = g.n;
+    args.lines_a = g.lines_a;
+    args.win = ax.win;
+    args.conv = ax.conv;
+    args.cinf = ax.cinf;
+    args.minf = ax.minf;
+    args.cp = ax.cp;
+    args.mult = ax.mult;
+    const float kh = (float)ax.k, kl = (float)(ax.k - (double)kh);
+    if (mode == 0) {
+        args.kk_hi = make_float2(kh, kh);
+        args.kk_lo = make_float2(kl, kl);
+    } else {
+        args.kk_hi = make_float2(-kh, kh);
+        args.kk_lo = make_float2(-kl, kl);
+    }
+    if (nl) {
+        args.px = nl->px;
+        args.py = nl->py;
+        args.pz = nl->pz;
+        args.g = nl->g;
+        args.scale = nl->scale;
+    }
+    args.partials = norm_out ? norm_out->buf : nullptr;
+    args.err = err;
+    const Shape sh = shape_of(shape);
+    const int tiles = (g.lines_a + 32 * sh.K - 1) / (32 * sh.K);
+    const bool has_nl = nl != nullptr, norm = norm_out != nullptr;
+    const int lb = g.lines_b;
+    switch (shape) {
+    case 1: return launch_shape<kShapes[1].K, kShapes[1].S>(mode, axis, has_nl, norm, map, args, tiles, lb, st);
+    case 2: return launch_shape<kShapes[2].K, kShapes[2].S>(mode, axis, has_nl, norm, map, args, tiles, lb, st);
+    case 3: return launch_shape<kShapes[3].K, kShapes[3].S>(mode, axis, has_nl, norm, map, args, tiles, lb, st);
+    default: return launch_shape<kShapes[0].K, kShapes[0].S>(mode, axis, has_nl, norm, map, args, tiles, lb, st);
+    }
+}
+
+cudaError_t launch_ff_from_c128(void *dst, const void *src, long long count, const double *scale,
+                                double *reset_scale, cudaStream_t st)
+{
+    k_ff_from_c128<<<point_blocks(count), 256, 0, st>>>((float4 *)dst, (const double2 *)src, count,
+                                                         scale);
+    cudaError_t e = cudaGetLastError();
+    // every block has read the scale once the conversion kernel is done
+    if (e == cudaSuccess && reset_scale) {
+        k_ff_set_one<<<1, 1, 0, st>>>(reset_scale);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t launch_ff_to_c128(void *dst, const void *src, long long count, const double *scale,
+                              cudaStream_t st)
+{
+    k_ff_to_c128<<<point_blocks(count), 256, 0, st>>>((double2 *)dst, (const float4 *)src, count,
+                                                       scale);
+    return cudaGetLastError();
+}
+
+}  // namespace gp

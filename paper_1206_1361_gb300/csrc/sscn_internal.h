@@ -106,7 +106,66 @@ struct Partials {
     const double *line_weight = nullptr;
 };
 
-enum Precision { kC128 = 0, kC64 = 1 };
+enum Precision { kC128 = 0, kC64 = 1, kCFF = 2 };
+
+// ---- float-float form (sscn_ff.cu) ------------------------------------------
+// psi as complex float-float values: per point a float4 (re_hi, im_hi, re_lo,
+// im_lo), re = re_hi + re_lo (about 48 significant bits), swept with FP32
+// error-free transformations on the FP32 pipe.
+//
+// A float-float coefficient k = kr + i ki expanded into the packed operands
+// of z k = z (kr, kr) + swap(z) (-ki, ki): rh = (kr_hi, kr_hi), rl = (kr_lo,
+// kr_lo), ih = (-ki_hi, ki_hi), il = (-ki_lo, ki_lo) (32 bytes).
+struct FfCoef {
+    float2 rh, rl, ih, il;
+};
+// The Crank-Nicolson tables of one axis and mode in that form: c'_i and
+// mult_i (m entries each, split from the FP64 tables), the index from which
+// they are constant and those constants, the back-substitution window W
+// (smallest with max|c'|^(W+1) < 2^-50; 0 if none up to the chunk), and the
+// coupling |kappa| = dt / (4 h^2).
+struct FfAxis {
+    int n = 0;
+    FfCoef *cp = nullptr, *mult = nullptr;
+    int conv = 0, win = 0;
+    FfCoef cinf{}, minf{};
+    double k = 0;
+};
+// calcnu of the float-float x sweep: the factor table along the line in
+// expanded form (exp(-tau omega_x^2 x_i^2 / 2)), the FP64 factor tables of
+// the line's (y, z) indices, G and the pending imaginary-time scale.
+struct FfNonlin {
+    const FfCoef *px = nullptr;
+    const double2 *py = nullptr, *pz = nullptr;
+    StepG g;
+    const double *scale = nullptr;
+};
+// Host: the float-float tables of one axis from its FP64 tables (cp64,
+// mult64: m entries; conv64 / cmax: where they turn constant, their largest
+// |c'|); fills `out` but not its device pointers, writes the expanded
+// tables to cp / mult (host arrays of m entries).
+void ff_tables(int m, const double2 *cp64, const double2 *mult64, int conv64, double cmax,
+               double k, int chunk, FfAxis &out, FfCoef *cp, FfCoef *mult);
+FfCoef ff_expand(double2 v);
+int ff_shapes();
+int ff_chunk(int shape);
+int ff_blocks(int shape, const SweepGeom &g);
+// Tensor map of a float-float psi for the sweep along `axis` (the layout of
+// complex128: two 8-byte units per point).
+cudaError_t make_ff_map(int shape, void *psi, int nx, int ny, int nz, int axis, CUtensorMap *out);
+// Windowed TMA-staged float-float sweep: nl != nullptr fuses calcnu into
+// the loads (x sweep); norm_out adds the FP64 sum |u|^2 per block; err
+// receives bit 2 on a wait timeout.
+cudaError_t launch_sweep_ff(int shape, int mode, int axis, const CUtensorMap &map,
+                            const FfAxis &ax, const SweepGeom &g, const FfNonlin *nl,
+                            const Partials *norm_out, int *err, cudaStream_t st);
+// dst (float-float) <- split(scale * src) over count points (scale nullptr:
+// 1); with reset_scale, *reset_scale <- 1 afterwards.
+cudaError_t launch_ff_from_c128(void *dst, const void *src, long long count, const double *scale,
+                                double *reset_scale, cudaStream_t st);
+// dst (complex128) <- scale * (hi + lo) over count points (scale nullptr: 1).
+cudaError_t launch_ff_to_c128(void *dst, const void *src, long long count, const double *scale,
+                              cudaStream_t st);
 
 // ---- launchers (sscn_kernels.cu) -------------------------------------------
 // All launchers enqueue on `st` and return the launch error (cudaSuccess if

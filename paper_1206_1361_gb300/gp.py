@@ -4,7 +4,8 @@ library; nothing here computes.
 
 psi arguments may be a numpy array (host), a torch tensor (host or CUDA), or a
 raw integer address with ``on_device`` given explicitly.  complex128 pairs
-with GP_C128 and complex64 with GP_C64.  Failures raise ``GPError`` carrying
+with GP_C128 and GP_CFF (the float-float form keeps float-float pairs on the
+device and exchanges complex128) and complex64 with GP_C64.  Failures raise ``GPError`` carrying
 the library's code and message.
 """
 import ctypes
@@ -16,13 +17,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgp.so")
 
 GP_IMAG, GP_REAL = 0, 1
-GP_C128, GP_C64 = 0, 1
+GP_C128, GP_C64, GP_CFF = 0, 1, 2
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ENONFINITE, GP_ETIMEOUT, GP_EINTERNAL, GP_EFULL = (
     0, -1, -2, -3, -4, -5, -6, -7)
 GP_MAX_EDGE = 8192
 GP_OPT_SWEEP_PATH, GP_OPT_TILE_SHAPE, GP_OPT_SPLITTING, GP_OPT_POTENTIAL_TABLE = 1, 2, 3, 4
 GP_PATH_AUTO, GP_PATH_EXACT, GP_PATH_TMA, GP_PATH_WINDOW, GP_PATH_SLAB = 0, 1, 2, 3, 4
 GP_SPLIT_LIE, GP_SPLIT_STRANG = 0, 1
+GP_PEAK_FP64_FMA, GP_PEAK_FP32_FMA, GP_PEAK_FP32X2_FMA = 0, 1, 2
 
 ERROR_NAMES = {GP_EINVAL: "GP_EINVAL", GP_ENOMEM: "GP_ENOMEM", GP_ECUDA: "GP_ECUDA",
                GP_ENONFINITE: "GP_ENONFINITE", GP_ETIMEOUT: "GP_ETIMEOUT",
@@ -79,6 +81,8 @@ SIGNATURES = {
     "gp_footprint": (_int, [ctypes.POINTER(gp_grid), _int, ctypes.POINTER(ctypes.c_size_t)]),
     "gp_sweep_noalloc": (_int, [_vp, ctypes.POINTER(gp_grid), _int, _dbl, _dbl, _int, _int,
                                 _vp]),
+    "gp_measure_peak": (_int, [_int, _i64, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)]),
     "gp_last_error": (ctypes.c_char_p, [_vp]),
     "gp_destroy": (None, [_vp]),
     "gp_batch_create": (_int, [_int, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
@@ -329,6 +333,16 @@ def gp_sweep_noalloc(psi_device, grid, axis, h, dt, mode, precision, cuda_stream
         raise GPError(rc, gp_last_error(None))
 
 
+def gp_measure_peak(kind, iters=20000):
+    """Measured TFLOP/s of one arithmetic pipe of the current device (and the
+    milliseconds of the best launch)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    rc = load_library().gp_measure_peak(int(kind), int(iters), ctypes.byref(tf), ctypes.byref(ms))
+    if rc != GP_OK:
+        raise GPError(rc, gp_last_error(None))
+    return tf.value, ms.value
+
+
 def gp_last_error(ctx=None):
     msg = load_library().gp_last_error(ctx)
     return msg.decode() if msg else ""
@@ -367,7 +381,8 @@ class Solver:
 
     @property
     def dtype(self):
-        return np.complex128 if self.precision == GP_C128 else np.complex64
+        """Host dtype of gp_load / gp_store (GP_CFF exchanges complex128)."""
+        return np.complex64 if self.precision == GP_C64 else np.complex128
 
     def load(self, psi=None):
         gp_load(self.ctx, psi)
@@ -399,6 +414,10 @@ class Solver:
         import torch
         gp_apply_pending_scale(self.ctx)
         gp_sync(self.ctx)
+        if self.precision == GP_CFF:
+            # float-float pairs: (..., 4) float32 = (re_hi, im_hi, re_lo, im_lo)
+            return torch.as_tensor(_DeviceArray(gp_device_psi(self.ctx), self.array_shape + (4,),
+                                                "<f4"), device="cuda")
         typestr = "<c16" if self.precision == GP_C128 else "<c8"
         return torch.as_tensor(_DeviceArray(gp_device_psi(self.ctx), self.array_shape, typestr),
                                device="cuda")
