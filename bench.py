@@ -76,6 +76,8 @@ def parse_args():
                     help="workload name for --probe (default: the benchmark workload)")
     ap.add_argument("--probe-shape", type=int, default=None, help="TMA tile shape for --probe")
     ap.add_argument("--probe-path", type=int, default=None, help="sweep path (GP_PATH_*) for --probe")
+    ap.add_argument("--probe-precision", type=int, default=None,
+                    help="precision (GP_C128 0, GP_C64 1, GP_CFF 2) for --probe")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP64, FP32 and packed FP32x2 multiply-add rates of "
                          "this GPU (the alu roofline denominators), print one JSON line, exit")
@@ -709,8 +711,8 @@ def run_probe(args):
         torch.cuda.synchronize()
         return 0
     case = CASES[args.probe_case] if args.probe_case else workload()
-    with gp.Solver(case.shape, case.h, case.dt, *case.trap, case.g, gp.GP_REAL,
-                   case.precision) as s:
+    prec = case.precision if args.probe_precision is None else args.probe_precision
+    with gp.Solver(case.shape, case.h, case.dt, *case.trap, case.g, gp.GP_REAL, prec) as s:
         if args.probe_shape is not None:
             gp.gp_set_option(s.ctx, gp.GP_OPT_TILE_SHAPE, args.probe_shape)
         if args.probe_path is not None:

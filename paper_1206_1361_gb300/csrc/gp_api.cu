@@ -69,6 +69,7 @@ struct gp_ctx {
     gp::FfAxis ffax[2][3];          // [mode][axis]
     gp::FfCoef *ffpx[2][3]{};       // [mode][axis] exp(-tau w_k^2 x^2 / 2), expanded
     void *ffmem = nullptr;          // one allocation for all of them
+    float2 *obs_ff = nullptr;       // x_i^2, then w_x^2 x_i^2 / 2, as float-float pairs
 
     CUtensorMap maps[3];            // 64-byte aligned type
     bool map_ok[3]{};
@@ -228,6 +229,18 @@ int upload_tables(gp_ctx *c)
         GP_CK(c, cudaMemcpy(c->obs_tab, x2.data(), x2.size() * sizeof(double), cudaMemcpyHostToDevice));
         std::vector<float> x2f(x2.begin(), x2.end());
         GP_CK(c, cudaMemcpy(c->obs_tab32, x2f.data(), x2f.size() * sizeof(float), cudaMemcpyHostToDevice));
+        if (is_ff(c)) {
+            const int nx = c->grid.nx, nt = c->grid.nx + c->grid.ny + c->grid.nz;
+            std::vector<float2> t(2 * (size_t)nx);
+            for (int i = 0; i < nx; ++i) {
+                for (int q = 0; q < 2; ++q) {
+                    const double v = x2[(size_t)q * nt + i];
+                    const float h = (float)v;
+                    t[(size_t)q * nx + i] = make_float2(h, (float)(v - (double)h));
+                }
+            }
+            GP_CK(c, cudaMemcpy(c->obs_ff, t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        }
     }
     for (int mode = 0; mode < 2; ++mode) {
         for (int k = 0; k < 3; ++k) {
@@ -416,7 +429,7 @@ size_t footprint_bytes(const gp_grid &g, int prec)
         if (prec == GP_CFF)
             for (int sh = 0; sh < gp::ff_shapes(); ++sh) blocks = std::max(blocks, gp::ff_blocks(sh, geom(g, k)));
     }
-    if (prec == GP_CFF) tables += ff_coefs(g) * sizeof(gp::FfCoef);
+    if (prec == GP_CFF) tables += ff_coefs(g) * sizeof(gp::FfCoef) + 2 * (size_t)g.nx * sizeof(float2);
     blocks = std::max(blocks, gp::kReduceBlocks);
     gp::ObsArgs oa{};
     oa.nx = g.nx;
@@ -449,6 +462,7 @@ void release(gp_ctx *c)
     fr(c->psi);
     fr(c->work);
     fr(c->ffmem);
+    fr(c->obs_ff);
     for (auto &row : c->ax)
         for (auto &a : row) { fr(a.cp64); fr(a.mult64); fr(a.cp32); fr(a.mult32); }
     for (int mode = 0; mode < 2; ++mode)
@@ -762,12 +776,10 @@ int enqueue_observables(gp_ctx *c)
     if (c->axial)
         GP_CK(c, gp::launch_observables_axial(c->psi, obs_args(c), c->h[0], c->obs_partials,
                                               c->sums, c->stream));
-    else if (is_ff(c)) {
-        // FP64 observables of the float-float state (hi + lo) through the work buffer
-        GP_CK(c, gp::launch_ff_to_c128(c->work, c->psi, points(c->grid), nullptr, c->stream));
-        GP_CK(c, gp::launch_observables(GP_C128, c->work, obs_args(c), c->obs_partials, c->sums,
-                                        c->stream));
-    } else
+    else if (is_ff(c))
+        GP_CK(c, gp::launch_observables_ff(c->psi, obs_args(c), c->obs_ff, c->obs_ff + c->grid.nx,
+                                           c->obs_partials, c->sums, c->stream));
+    else
         GP_CK(c, gp::launch_observables(c->prec, c->psi, obs_args(c), c->obs_partials, c->sums,
                                         c->stream));
     GP_CK(c, cudaMemcpyAsync(c->host_sums, c->sums, gp::kObsWidth * sizeof(double),
@@ -1005,6 +1017,7 @@ int create_ctx(const gp_grid *grid, const double dx[3], double dt, double gamma,
     }
     if (precision == GP_CFF) {
         if ((rc = alloc(c, &c->ffmem, ff_coefs(c->grid) * sizeof(gp::FfCoef)))) return bail(rc);
+        if ((rc = alloc(c, (void **)&c->obs_ff, 2 * (size_t)c->grid.nx * sizeof(float2)))) return bail(rc);
         gp::FfCoef *q = static_cast<gp::FfCoef *>(c->ffmem);
         for (int mode_i = 0; mode_i < 2; ++mode_i)
             for (int k = 0; k < 3; ++k) {

@@ -463,6 +463,80 @@ __global__ void k_ff_to_c128(double2 *__restrict__ dst, const float4 *__restrict
     }
 }
 
+// --------------------------------------------------------------- observables
+//
+// One warp per x-line (j, k), lanes over the line's points (coalesced 16-byte
+// loads of the pairs): per point a = |psi|^2, x_i^2 a, V_x(i) a, a^2 and the
+// neighbour terms R = Re(psi_next conj(psi)) along x, y, z (zero beyond the
+// last stored point), each a float-float product summed per lane in
+// float-float (TwoSum + Fast2Sum after every addition), then across the warp
+// the same way.  Lane 0 turns the line's 7 sums into the 9-wide FP64 row of
+// the FP64 observables (the y, z factors are constant on the line; the
+// finish forms K = 2 S0 - 2 R), so the rows and the fixed-order finish are
+// shared with the other forms.
+__device__ __forceinline__ float2 lane_sum(C z)
+{
+    const float2 s = s_two_sum(z.hi.x, z.hi.y);
+    return f2(s.x, s.y + (z.lo.x + z.lo.y));
+}
+
+__global__ void __launch_bounds__(256)
+k_observables_ff(const float4 *__restrict__ psi, ObsArgs a, const float2 *__restrict__ x2ff,
+                 const float2 *__restrict__ vxff, double *__restrict__ partials)
+{
+    const int lane = threadIdx.x & 31;
+    const long long line = (long long)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    if (line >= (long long)ny * nz) return;       // whole warp
+    const int j = (int)(line % ny), k = (int)(line / ny);
+    const long long plane = (long long)nx * ny;
+    const float4 *row = psi + line * nx;
+    const bool has_y = j + 1 < ny, has_z = nz > 1 && k + 1 < nz;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto cv = [](float4 v) { return C{f2(v.x, v.y), f2(v.z, v.w)}; };
+    float2 acc[7];                                  // S0, Sx, SVx, S4, Rx, Ry, Rz
+#pragma unroll
+    for (int q = 0; q < 7; ++q) acc[q] = f2(0.f, 0.f);
+    auto put = [&](int q, float2 t) { acc[q] = s_norm(s_add(acc[q], t)); };
+    for (int i = lane; i < nx; i += 32) {
+        const C v = cv(row[i]);
+        const C nb = cv(i + 1 < nx ? row[i + 1] : zero);
+        const C nyv = cv(has_y ? row[i + nx] : zero);
+        const float2 am = abs2(v);
+        put(0, am);
+        put(1, s_mul(x2ff[i], am));
+        put(2, s_mul(vxff[i], am));
+        put(3, s_mul(am, am));
+        put(4, lane_sum(lmul(nb, v.hi, v.lo)));
+        put(5, lane_sum(lmul(nyv, v.hi, v.lo)));
+        if (nz > 1) {
+            const C nzv = cv(has_z ? row[i + plane] : zero);
+            put(6, lane_sum(lmul(nzv, v.hi, v.lo)));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float2 t = f2(__shfl_down_sync(0xffffffffu, acc[q].x, o),
+                                __shfl_down_sync(0xffffffffu, acc[q].y, o));
+            acc[q] = s_norm(s_add(acc[q], t));
+        }
+    if (lane == 0) {
+        const double sc = *a.scale, s2 = sc * sc, r0 = join(acc[0]);
+        double *out = partials + line * kObsWidth;
+        out[0] = s2 * r0;
+        out[1] = s2 * join(acc[1]);
+        out[2] = s2 * a.y2[j] * r0;
+        out[3] = s2 * a.z2[k] * r0;
+        out[4] = s2 * (join(acc[2]) + (a.vy[j] + a.vz[k]) * r0);
+        out[5] = s2 * s2 * join(acc[3]);
+        out[6] = s2 * join(acc[4]);
+        out[7] = s2 * join(acc[5]);
+        out[8] = s2 * join(acc[6]);
+    }
+}
+
 int point_blocks(long long count)
 {
     const long long b = (count + 255) / 256;
@@ -593,6 +667,17 @@ cudaError_t launch_ff_from_c128(void *dst, const void *src, long long count, con
         e = cudaGetLastError();
     }
     return e;
+}
+
+cudaError_t launch_observables_ff(const void *psi, const ObsArgs &a, const float2 *x2ff,
+                                  const float2 *vxff, double *scratch, double *sums, cudaStream_t st)
+{
+    const long long lines = (long long)a.ny * a.nz;
+    const long long blocks = (lines * 32 + 255) / 256;
+    k_observables_ff<<<(unsigned)blocks, 256, 0, st>>>((const float4 *)psi, a, x2ff, vxff, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_rows_finish(scratch, lines, scratch + lines * kObsWidth, sums, st);
 }
 
 cudaError_t launch_ff_to_c128(void *dst, const void *src, long long count, const double *scale,

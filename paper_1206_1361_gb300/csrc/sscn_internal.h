@@ -163,6 +163,12 @@ cudaError_t launch_sweep_ff(int shape, int mode, int axis, const CUtensorMap &ma
 // 1); with reset_scale, *reset_scale <- 1 afterwards.
 cudaError_t launch_ff_from_c128(void *dst, const void *src, long long count, const double *scale,
                                 double *reset_scale, cudaStream_t st);
+// Observables rows of a float-float psi (one per x-line: the FP64 row layout
+// with R_k neighbour sums) and their fixed-order finish into sums[9].
+// x2ff / vxff: x_i^2 and omega_x^2 x_i^2 / 2 as float-float pairs (nx each).
+struct ObsArgs;
+cudaError_t launch_observables_ff(const void *psi, const ObsArgs &a, const float2 *x2ff,
+                                  const float2 *vxff, double *scratch, double *sums, cudaStream_t st);
 // dst (complex128) <- scale * (hi + lo) over count points (scale nullptr: 1).
 cudaError_t launch_ff_to_c128(void *dst, const void *src, long long count, const double *scale,
                               cudaStream_t st);
