@@ -2,10 +2,10 @@
 benchmark times (the 10-step graph, an observables report every 10 steps,
 the automatic sweep path):
 
-* 256^3 FP64: imaginary-time ground-state steps at g = 20, then the quench to
-  g = 18 in real time for 2000 steps, element by element against the oracle
-  (relative L2 of psi <= 1e-10; observables <= 1e-10; norm drift of both
-  within the rounding bound);
+* 256^3 FP64 and float-float: imaginary-time ground-state steps at g = 20,
+  then the quench to g = 18 in real time for 2000 steps, element by element
+  against the oracle (relative L2 of psi <= 1e-10; observables <= 1e-10;
+  norm drift of both within the rounding bound);
 * 512 x 512 x 256 complex64 real time from the Gaussian seed against the FP64
   oracle (relative L2 bound derived from FP32 rounding per pass; mu <= 1e-6);
 * the 256 batched instances advanced together, sampled instances against
@@ -23,36 +23,55 @@ from tests.gpu_util import oracle_params, rel_l2, require_gpu
 pytestmark = pytest.mark.gpu
 
 
-def test_real_256_quench_2000_steps_matches_oracle():
+_ORACLE_256 = {}
+
+
+def oracle_real_256(prep):
+    """The oracle's 256^3 quench (ground-state prep steps at g = 20, then 2000
+    real-time steps at g = 18): final psi, observables and the norm after the
+    quench; computed once per session and shared by both precisions."""
+    if prep not in _ORACLE_256:
+        c = REAL_256
+        pi = oracle_params(c.shape, c.h, c.dt, c.trap, c.extra["g_ground"], 0)
+        want = oracle.seed(pi)
+        oracle.step(pi, want, prep)
+        pr = oracle_params(c.shape, c.h, c.dt, c.trap, c.g, 1)
+        n0 = oracle.observables(pr, want)["norm"]
+        oracle.step(pr, want, c.steps)
+        _ORACLE_256[prep] = (want, oracle.observables(pr, want), n0)
+    return _ORACLE_256[prep]
+
+
+@pytest.mark.parametrize("precision", [gp.GP_C128, gp.GP_CFF])
+def test_real_256_quench_2000_steps_matches_oracle(precision):
+    """The benchmark's workload and launch configuration (the 10-step graph,
+    an observables report every 10 steps) on the FP64 form and on the
+    float-float form, against the same oracle run."""
     require_gpu()
     c = REAL_256
     prep, every = 100, c.extra["report_every"]
-    with gp.Solver(c.shape, c.h, c.dt, *c.trap, c.extra["g_ground"], gp.GP_IMAG) as s:
+    with gp.Solver(c.shape, c.h, c.dt, *c.trap, c.extra["g_ground"], gp.GP_IMAG, precision) as s:
         s.load(None).step(prep)
         s.set_params(c.g, gp.GP_REAL)
         for _ in range(c.steps // every):
             s.step(every)
             obs = s.observables()
         got = s.psi()
-    pi = oracle_params(c.shape, c.h, c.dt, c.trap, c.extra["g_ground"], 0)
-    want = oracle.seed(pi)
-    oracle.step(pi, want, prep)
-    pr = oracle_params(c.shape, c.h, c.dt, c.trap, c.g, 1)
-    n0 = oracle.observables(pr, want)["norm"]
-    oracle.step(pr, want, c.steps)
+    want, ref, n0 = oracle_real_256(prep)
     assert rel_l2(got, want) <= 1e-10
-    ref = oracle.observables(pr, want)
     for k in ("norm", "mu", "energy", "rms_x", "rms_y", "rms_z", "rms_r"):
         assert abs(obs[k] - ref[k]) <= 1e-10 * abs(ref[k]), (k, obs[k], ref[k])
     # Real time conserves N up to the unitarity defect of the rounded
     # arithmetic: the stored LU factors reproduce I - kappa L with a
     # Hermitian part off by ~2 ulp, which the Cayley step u = (2 (I - kappa
-    # L)^-1 - I) psi turns into a norm change of up to ~4 2^-52 per sweep,
-    # and the phase factor's modulus is off by ~2 2^-52.  Those defects are
+    # L)^-1 - I) psi turns into a norm change of up to ~4 ulp per sweep,
+    # and the phase factor's modulus is off by ~2 ulp.  Those defects are
     # fixed, so on a slowly varying state they add up linearly in the steps
-    # (both sides drift ~1.5e-15 per step here).
-    bound = c.steps * (3 * 4 + 2) * 2.0 ** -52
-    assert abs(obs["norm"] - n0) <= bound and abs(ref["norm"] - n0) <= bound, \
+    # (both sides drift ~1.5e-15 per step here).  The float-float form's unit
+    # is 2^-48 (tables split from FP64, hi + lo pairs) instead of 2^-52.
+    unit = 2.0 ** -48 if precision == gp.GP_CFF else 2.0 ** -52
+    bound = c.steps * (3 * 4 + 2) * unit
+    assert abs(obs["norm"] - n0) <= bound and abs(ref["norm"] - n0) <= 2.0 ** -52 / unit * bound, \
         (obs["norm"] - n0, ref["norm"] - n0)
 
 
