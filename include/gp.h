@@ -200,11 +200,16 @@ int gp_apply_pending_scale(gp_ctx *ctx);
  * 16 MiB (+512 KiB of tables) that every GPU loading libgp holds until exit,
  * so grids above 1048576 complex128 or 2097152 complex64 points are rejected
  * with GP_EINVAL.  The first call on each device looks up the array's device
- * address (make that first call before any stream capture).  All calls share
- * the one array, which keeps the last call's contents: calls whose work
- * overlaps on the GPU race with each other.  Errors: GP_EINVAL for bad
- * arguments, GP_ECUDA if a CUDA call fails; the message is in
- * gp_last_error(NULL).
+ * address (make that first call before any stream capture); the address is
+ * kept for the life of the process, so the library must not outlive a
+ * cudaDeviceReset of that device.  The coefficient tables are written into
+ * the array by a small kernel on cuda_stream (nothing is staged through host
+ * memory).  All calls share the one array, which keeps the last call's
+ * contents: calls whose work overlaps on the GPU race with each other.  The
+ * x sweep (axis 0) runs one line per thread along contiguous x, so its
+ * accesses are not coalesced and it is several times slower than the y and
+ * z sweeps.  Errors: GP_EINVAL for bad arguments, GP_ECUDA if a CUDA call
+ * fails; the message is in gp_last_error(NULL).
  */
 int gp_sweep_noalloc(void *psi_device, const gp_grid *grid, int axis, double h,
                      double dt, int mode, int precision, void *cuda_stream);
@@ -382,6 +387,20 @@ int gp_batch_store(gp_batch *b, int slot, void *psi_out, int64_t count, int on_d
 int gp_batch_set_params(gp_batch *b, int slot, double g, int mode);
 /* Advance every instance in the batch by n steps (asynchronous). */
 int gp_batch_step(gp_batch *b, int64_t n);
+/*
+ * Budget, in nanoseconds of %globaltimer, of each dependency wait of the
+ * batch's persistent kernel (a work item of one sweep waits until every item
+ * of its instance's previous sweep has completed); default 2e9.  The paper
+ * has no counterpart: this is failure detection for the persistent kernel.
+ * A wait that exceeds its budget sets the batch's abort flag, every warp
+ * leaves at its next item, and the next synchronising call (gp_batch_sync,
+ * gp_batch_observables, gp_batch_store) returns GP_ETIMEOUT once; the steps
+ * of that launch are then incomplete, so reload the instances before
+ * stepping on.  ns = 0 makes every wait that is not satisfied at once give
+ * up (used to test the path).  Takes effect at the next gp_batch_step.
+ * GP_EINVAL for ns < 0.
+ */
+int gp_batch_set_wait_ns(gp_batch *b, int64_t ns);
 /* Observables of every instance, out[slot] for slot < capacity (unused slots
  * get step = -1); synchronises. */
 int gp_batch_observables(gp_batch *b, gp_obs *out, int capacity);

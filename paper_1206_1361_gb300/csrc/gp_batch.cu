@@ -58,7 +58,7 @@ template <typename T> __device__ __forceinline__ typename BC<T>::c mkb(T x, T y)
 constexpr int kTileLines = 16;
 constexpr int kObsWidthB = gp::kObsWidth;
 constexpr int kMaxEdge32 = 512, kMaxEdge64 = 384;
-constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr uint64_t kWaitNs = 2000000000ull;   // default dependency-wait budget
 constexpr unsigned kPollMaxNs = 512;
 
 // Device descriptor of one active instance.
@@ -96,6 +96,7 @@ struct LaunchArgs {
     int *done;                      // [N] completed items per instance
     int *err;
     int *abort_flag;
+    unsigned long long wait_ns;     // budget of one dependency wait
 };
 
 __device__ __forceinline__ uint64_t gtime()
@@ -117,14 +118,14 @@ __device__ __forceinline__ void red_release_add(int *p, int v)
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ bool wait_done(const int *ctr, int need, const int *abort_flag)
+__device__ bool wait_done(const int *ctr, int need, const int *abort_flag, unsigned long long budget)
 {
     if (ld_acquire(ctr) >= need) return true;
     const uint64_t t0 = gtime();
     unsigned ns = 32;                      // polling interval, doubled up to kPollMaxNs
     while (ld_acquire(ctr) < need) {
         if (*(volatile const int *)abort_flag) return false;
-        if (gtime() - t0 > kWaitNs) return false;
+        if (gtime() - t0 >= budget) return false;
         __nanosleep(ns);
         ns = min(2 * ns, kPollMaxNs);
     }
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(32) k_batch_steps(const LaunchArgs A)
             asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char *>(&I) + lane * 128));
         const int need = s * A.tot[i] + A.cum[i * 4 + p];
         int ok = 1;
-        if (lane == 0) ok = wait_done(&A.done[i], need, A.abort_flag);
+        if (lane == 0) ok = wait_done(&A.done[i], need, A.abort_flag, A.wait_ns);
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
             if (lane == 0) {
@@ -543,6 +544,7 @@ struct gp_batch {
     size_t inst_cap = 0;
     double *h_sums = nullptr;       // pinned
     int *h_err = nullptr;           // pinned
+    unsigned long long wait_ns = kWaitNs;
     LaunchArgs args{};
     size_t smem = 0;
     int grid = 0;
@@ -867,8 +869,14 @@ int batch_sync_errors(gp_batch *b)
 {
     GP_BCK(b, cudaMemcpyAsync(b->h_err, b->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     GP_BCK(b, cudaStreamSynchronize(b->stream));
-    if (b->h_err[0] & 2) return bfail(b, GP_ETIMEOUT, "a batched step's bounded dependency wait gave up");
-    if (b->h_err[0] & 1) return bfail(b, GP_ENONFINITE, "a norm became non-finite or zero");
+    const int bits = b->h_err[0];
+    if (bits) {
+        // reported once: the next calls start clean
+        GP_BCK(b, cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+        GP_BCK(b, cudaStreamSynchronize(b->stream));
+    }
+    if (bits & 2) return bfail(b, GP_ETIMEOUT, "a batched step's bounded dependency wait gave up");
+    if (bits & 1) return bfail(b, GP_ENONFINITE, "a norm became non-finite or zero");
     return GP_OK;
 }
 
@@ -1066,6 +1074,13 @@ int gp_batch_remove(gp_batch *b, int slot)
     return GP_OK;
 }
 
+int gp_batch_set_wait_ns(gp_batch *b, int64_t ns)
+{
+    if (!b || ns < 0) return bfail(b, GP_EINVAL, "gp_batch_set_wait_ns: need ns >= 0");
+    b->wait_ns = (unsigned long long)ns;
+    return GP_OK;
+}
+
 int gp_batch_step(gp_batch *b, int64_t n)
 {
     if (!b || n < 0) return bfail(b, GP_EINVAL, "gp_batch_step: bad arguments");
@@ -1073,6 +1088,7 @@ int gp_batch_step(gp_batch *b, int64_t n)
     if (rc) return rc;
     if (n == 0 || b->active.empty()) return GP_OK;
     LaunchArgs A = b->args;
+    A.wait_ns = b->wait_ns;
     const int N = A.N;
     // at most 2^31 items per launch: split long runs into chunks of steps
     const long long max_steps = std::max<long long>(1, (1LL << 30) / std::max<long long>(1, A.ips));

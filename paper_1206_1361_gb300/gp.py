@@ -93,6 +93,7 @@ SIGNATURES = {
     "gp_batch_store": (_int, [_vp, _int, _vp, _i64, _int]),
     "gp_batch_set_params": (_int, [_vp, _int, _dbl, _int]),
     "gp_batch_step": (_int, [_vp, _i64]),
+    "gp_batch_set_wait_ns": (_int, [_vp, _i64]),
     "gp_batch_observables": (_int, [_vp, ctypes.POINTER(gp_obs), _int]),
     "gp_batch_remove": (_int, [_vp, _int]),
     "gp_batch_info": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int),
@@ -517,6 +518,11 @@ def gp_batch_step(b, n):
     _berr(b, load_library().gp_batch_step(b, int(n)))
 
 
+def gp_batch_set_wait_ns(b, ns):
+    """Budget of each dependency wait of the batch's persistent kernel (ns)."""
+    _berr(b, load_library().gp_batch_set_wait_ns(b, int(ns)))
+
+
 def gp_batch_observables(b, capacity, slots=None):
     """List of capacity dicts, one per slot id (step == -1: unused slot); with
     `slots`, a dict of those slots' entries only (no conversion of the rest)."""
@@ -567,6 +573,10 @@ class Batch:
 
     def step(self, n):
         gp_batch_step(self.b, n)
+        return self
+
+    def set_wait_ns(self, ns):
+        gp_batch_set_wait_ns(self.b, ns)
         return self
 
     def observables(self):
