@@ -12,8 +12,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libgp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-         "--expt-relaxed-constexpr"]
+# Host code is compiled without floating-point contraction: the coefficient
+# tables computed on the host must match the device's explicitly rounded
+# arithmetic bit for bit, on x86 and Arm hosts alike.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "-I", INCLUDE, "--expt-relaxed-constexpr"]
 
 
 def _nvcc():

@@ -802,14 +802,10 @@ void gp::set_thread_error(const char *msg) { g_create_error = msg ? msg : ""; }
 
 void gp::host_thomas_tables(int m, double kre, double kim, double2 *cp, double2 *mult)
 {
-    const std::complex<double> kappa(kre, kim);
-    std::complex<double> prev = 0.0;
+    double2 prev = make_double2(0.0, 0.0);
     for (int i = 0; i < m; ++i) {
-        const std::complex<double> f = 1.0 / ((1.0 + 2.0 * kappa) + kappa * prev);
-        const std::complex<double> c = -kappa * f;
-        mult[i] = make_double2(f.real(), f.imag());
-        cp[i] = make_double2(c.real(), c.imag());
-        prev = c;
+        thomas_step(kre, kim, prev.x, prev.y, mult[i], cp[i]);
+        prev = cp[i];
     }
 }
 

@@ -35,6 +35,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes +
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;                       // guards the fields below
 void *g_scratch_addr[kMaxDevices];        // device address per device ordinal
+// host working arrays of the table recurrence (its constant tails and
+// derived fields are passed to the kernels by value)
 double2 g_cp64[kTableEntries], g_mult64[kTableEntries];
 float4 g_cp32[kTableEntries], g_mult32[kTableEntries];
 
@@ -42,6 +44,55 @@ int reject(int code, const char *msg)
 {
     gp::set_thread_error(msg);
     return code;
+}
+
+__device__ float4 split_rn(double2 v)
+{
+    const float hx = __double2float_rn(v.x), hy = __double2float_rn(v.y);
+    return make_float4(hx, hy, __double2float_rn(__dsub_rn(v.x, (double)hx)),
+                       __double2float_rn(__dsub_rn(v.y, (double)hy)));
+}
+
+// The sweep's Thomas tables, written on the device into the table part of the
+// static array (nothing is staged through host memory, so the call does not
+// wait for earlier work on the stream).  Thread 0 runs the FP64 recurrence up
+// to conv64, the index from which the host (running the same explicitly
+// rounded recurrence) found every entry equal to the last; thread 32 runs
+// the recurrence of the FP32-rounded kappa for the complex64 tables (hi + lo
+// pairs) up to conv32; then all threads fill the constant tails.
+__global__ void k_noalloc_tables(int m, int conv64, int conv32, double kre, double kim,
+                                 double kre32, double kim32, double2 *cp64, double2 *mult64,
+                                 float4 *cp32, float4 *mult32)
+{
+    __shared__ double2 tail[4];
+    if (threadIdx.x == 0 || threadIdx.x == 32) {
+        const bool f64 = threadIdx.x == 0;
+        const double kr = f64 ? kre : kre32, ki = f64 ? kim : kim32;
+        const int last = f64 ? conv64 : conv32;
+        double2 prev = make_double2(0.0, 0.0), mu = prev, c = prev;
+        for (int i = 0; i <= last; ++i) {
+            gp::thomas_step(kr, ki, prev.x, prev.y, mu, c);
+            if (f64) {
+                cp64[i] = c;
+                mult64[i] = mu;
+            } else {
+                cp32[i] = split_rn(c);
+                mult32[i] = split_rn(mu);
+            }
+            prev = c;
+        }
+        tail[f64 ? 0 : 2] = c;
+        tail[f64 ? 1 : 3] = mu;
+    }
+    __syncthreads();
+    for (int i = conv64 + 1 + threadIdx.x; i < m; i += blockDim.x) {
+        cp64[i] = tail[0];
+        mult64[i] = tail[1];
+    }
+    for (int i = conv32 + 1 + threadIdx.x; i < m; i += blockDim.x) {
+        cp32[i] = split_rn(tail[2]);
+        mult32[i] = split_rn(tail[3]);
+    }
 }
 
 }  // namespace
@@ -96,14 +147,14 @@ extern "C" int gp_sweep_noalloc(void *psi_device, const gp_grid *grid, int axis,
     ax.mult64 = ax.cp64 + kTableEntries;
     ax.cp32 = reinterpret_cast<float4 *>(ax.mult64 + kTableEntries);
     ax.mult32 = ax.cp32 + kTableEntries;
-    // pageable sources: each copy returns once its bytes are staged
-    const struct { void *dst; const void *src; size_t bytes; } copies[4] = {
-        {ax.cp64, g_cp64, m * sizeof(double2)}, {ax.mult64, g_mult64, m * sizeof(double2)},
-        {ax.cp32, g_cp32, m * sizeof(float4)}, {ax.mult32, g_mult32, m * sizeof(float4)}};
-    for (const auto &cp : copies) {
-        e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return reject(GP_ECUDA, cudaGetErrorString(e));
-    }
+    // the host ran the recurrence for the by-value fields (conv, the constant
+    // tails, the middle-row multipliers, the window); the device writes the
+    // same tables into the static array
+    const double kre = ax.kre, kim = ax.kim;
+    k_noalloc_tables<<<1, 256, 0, st>>>(m, ax.conv64, ax.conv32, kre, kim, (double)(float)kre,
+                                        (double)(float)kim, ax.cp64, ax.mult64, ax.cp32, ax.mult32);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return reject(GP_ECUDA, cudaGetErrorString(e));
 
     gp::SweepGeom g{};
     const long long nx = grid->nx, ny = grid->ny;

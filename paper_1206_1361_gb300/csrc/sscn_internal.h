@@ -347,6 +347,39 @@ cudaError_t launch_sweep_tma(int prec, int shape, int mode, int axis, const CUte
 // (c'_0 = 0), stored 0-based in FP64 on the host.
 void host_thomas_tables(int m, double kre, double kim, double2 *cp, double2 *mult);
 
+// One step of that recurrence, from c'_{i-1} = (pr, pi) to mult_i and c'_i,
+// in real arithmetic in a fixed order with every operation rounded once:
+//   z = (1 + 2 kre + kre pr - kim pi) + i (2 kim + kre pi + kim pr),
+//   mult = (zr / |z|^2, -zi / |z|^2),  c' = -(kappa mult).
+// The host build turns off floating-point contraction, so host and device
+// (explicitly rounded intrinsics) produce the same bits.
+#if defined(__CUDA_ARCH__)
+#define GP_RN_MUL(a, b) __dmul_rn((a), (b))
+#define GP_RN_ADD(a, b) __dadd_rn((a), (b))
+#define GP_RN_SUB(a, b) __dsub_rn((a), (b))
+#define GP_RN_DIV(a, b) __ddiv_rn((a), (b))
+#else
+#define GP_RN_MUL(a, b) ((a) * (b))
+#define GP_RN_ADD(a, b) ((a) + (b))
+#define GP_RN_SUB(a, b) ((a) - (b))
+#define GP_RN_DIV(a, b) ((a) / (b))
+#endif
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline void thomas_step(double kre, double kim, double pr, double pi, double2 &mult, double2 &cp)
+{
+    const double zr = GP_RN_SUB(GP_RN_ADD(GP_RN_ADD(1.0, GP_RN_ADD(kre, kre)), GP_RN_MUL(kre, pr)),
+                                GP_RN_MUL(kim, pi));
+    const double zi = GP_RN_ADD(GP_RN_ADD(GP_RN_ADD(kim, kim), GP_RN_MUL(kre, pi)), GP_RN_MUL(kim, pr));
+    const double d = GP_RN_ADD(GP_RN_MUL(zr, zr), GP_RN_MUL(zi, zi));
+    const double mr = GP_RN_DIV(zr, d), mi = -GP_RN_DIV(zi, d);
+    mult.x = mr;
+    mult.y = mi;
+    cp.x = -GP_RN_SUB(GP_RN_MUL(kre, mr), GP_RN_MUL(kim, mi));
+    cp.y = -GP_RN_ADD(GP_RN_MUL(kre, mi), GP_RN_MUL(kim, mr));
+}
+
 // Record msg as the message gp_last_error(NULL) returns in this thread.
 void set_thread_error(const char *msg);
 

@@ -2,13 +2,15 @@
 for callers that cannot allocate device memory (code running inside another
 framework's operator with only the buffers it was handed, or loops that cannot
 take cudaMalloc's device-wide synchronisation).  Its scratch lives in a static
-device array, so this file checks it against the context path (gp_step), on
-two calls in a row, and that grids beyond the array are refused.  Collected
+device array, so this file checks it against the context path (gp_step) and
+against the oracle's sweep on every axis and mode, on two calls in a row, and
+that grids beyond the array are refused.  Collected
 last on purpose: it must pass alone in a fresh process and after every other
 test."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1206_1361_gb300 import gp
 from tests.gpu_util import rel_l2, require_gpu
 
@@ -50,6 +52,33 @@ def test_noalloc_sweeps_match_gp_step_on_two_calls(precision, dtype, shape):
             stream.synchronize()
             got = dev.cpu().numpy()
             assert rel_l2(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("precision,dtype,tol", [
+    (gp.GP_C128, np.complex128, 1e-12),
+    # complex64: the FP32 roundings of a few dozen operations per point of one
+    # sweep, 2^-24 each
+    (gp.GP_C64, np.complex64, 32 * 2.0 ** -24)])
+@pytest.mark.parametrize("mode", [gp.GP_IMAG, gp.GP_REAL])
+def test_noalloc_each_axis_matches_the_oracle_sweep(precision, dtype, tol, mode):
+    """Each axis, both modes: one sweep of gp_sweep_noalloc against the FP64
+    oracle's sweep (calclux / calcluy / calcluz) of the same state, on two
+    calls in a row (the second call reuses the array the first one wrote)."""
+    require_gpu()
+    import torch
+    shape, h, dt = (40, 36, 30), (0.3, 0.25, 0.2), 0.01
+    psi0 = rand_state(shape, 11, dtype)
+    p = oracle.Params.make(shape, h, dt, 1.0, 1.0, 1.0, 0.0, mode)
+    stream = torch.cuda.Stream()
+    for ax in (0, 1, 2):
+        want = psi0.astype(np.complex128)
+        oracle.sweep(p, ax, want)
+        for _call in range(2):
+            dev = torch.from_numpy(psi0.copy()).cuda()
+            gp.gp_sweep_noalloc(dev, shape, ax, h[ax], dt, mode, precision, stream)
+            stream.synchronize()
+            got = dev.cpu().numpy().astype(np.complex128)
+            assert rel_l2(got, want) <= tol, (ax, mode)
 
 
 def test_noalloc_imaginary_time_sweep_matches_dense_solve():
