@@ -227,6 +227,35 @@ def test_thomas_fermi_limit_2d():
     assert 5 < excess[0] / excess[2] < 12
 
 
+def test_thomas_fermi_limit_3d():
+    """3D: mu / mu_TF -> 1 from above as g grows, mu_TF = (15 g gamma nu lambda
+    / (4 pi))^(2/5) / 2, on 64^3 boxes of +-1.25 R_TF started from the
+    Thomas-Fermi profile: the excess falls monotonically, is below 3 % at
+    g = 1e4 and shrinks by a factor 3 - 8 over the decade of g (the leading
+    correction, the kinetic energy of the surface layer, scales like
+    (omega / mu)^2 ln(mu / omega), ~4.5x here)."""
+    w, n = (1.0, 1.25, 1.5), 64
+    excess = []
+    for g in (1e3, 3e3, 1e4):
+        mu_tf = 0.5 * (15.0 * g * w[0] * w[1] * w[2] / (4 * math.pi)) ** 0.4
+        h = 2.5 * math.sqrt(2 * mu_tf) / min(w) / n
+        dt = min(0.25 * h * h, 0.05 / mu_tf)
+        p = oracle.Params.make((n, n, n), (h, h, h), dt, *w, g, 0)
+        x = coords(n, h)
+        v = 0.5 * (w[0] ** 2 * x[None, None, :] ** 2 + w[1] ** 2 * x[None, :, None] ** 2 +
+                   w[2] ** 2 * x[:, None, None] ** 2)
+        psi = np.sqrt(np.maximum(mu_tf - v, 0) / g).astype(np.complex128)
+        psi[:, :, 0] = 0
+        psi[:, 0, :] = 0
+        psi[0] = 0
+        psi /= math.sqrt(h ** 3 * np.sum(np.abs(psi) ** 2))
+        oracle.step(p, psi, 3 * int(2 / dt))
+        excess.append(oracle.observables(p, psi)["mu"] / mu_tf - 1)
+    assert excess[0] > excess[1] > excess[2] > 0
+    assert excess[2] <= 0.03
+    assert 3 < excess[0] / excess[2] < 8
+
+
 # ------------------------------------------------ observables on a Gaussian
 
 def test_observables_of_the_analytic_gaussian():
