@@ -48,6 +48,7 @@ def run_ff(shape, h, dt, w, g, mode, steps, psi0=None, shape_idx=None, every=Non
 
 SHAPES = [
     ((130, 33, 20), (0.1, 0.2, 0.15)),     # ragged tiles in y, z
+    ((131, 70, 9), (0.1, 0.15, 0.3)),      # odd nx
     ((96, 200, 17), (0.12, 0.1, 0.2)),
     ((34, 18, 129), (0.2, 0.3, 0.1)),
     ((258, 130, 1), (0.08, 0.1, 1.0)),    # 2D
