@@ -214,6 +214,70 @@ int gp_apply_pending_scale(gp_ctx *ctx);
 int gp_sweep_noalloc(void *psi_device, const gp_grid *grid, int axis, double h,
                      double dt, int mode, int precision, void *cuda_stream);
 
+/*
+ * Z-slab decomposition of one grid over several GPUs (real time, complex128,
+ * plain splitting).  The paper's largest threaded runs are real-time grids of
+ * the 1000 x 1000 x 300 class; a grid beyond one GPU's memory is split along
+ * z, one rank per GPU.  Rank r holds the global planes [bounds[r],
+ * bounds[r+1]) of the nx * ny * nz grid (bounds[0] = 0, bounds[nranks] = nz,
+ * 1 <= nranks <= 8, every rank >= 2 unknown planes: bounds[1] >= 3 and
+ * bounds[r+1] - bounds[r] >= 2 above).  Its context's psi is (nz_local, ny,
+ * nx) with nz_local = bounds[1] (rank 0) or bounds[r+1] - bounds[r] + 1: a
+ * leading plane (the Dirichlet plane for rank 0, a zero stand-in for the
+ * neighbour's last plane otherwise) and then the rank's planes.  The x and y
+ * sweeps and the nonlinear step are local; the z sweep (I - kappa L) v = psi,
+ * u = 2 v - psi, is a partitioned tridiagonal solve: each rank solves its own
+ * block with the coupling to its neighbours cut, publishes the two boundary
+ * planes of that solution, and corrects its planes after solving the
+ * reduced system of all ranks' boundary values, line by line (2 (nranks - 1)
+ * unknowns).  The caller moves the boundary planes between ranks (an
+ * all-gather); nothing in the library talks to another GPU.
+ *
+ * gp_create_slab: the grid as in gp_create but global; returns GP_EINVAL for
+ * an invalid partition.  The other calls of a context that apply to a slab
+ * are gp_load / gp_store / gp_device_psi (the local buffer), gp_set_params
+ * (real time only), gp_set_modulation, gp_set_option (plain splitting),
+ * gp_sync and gp_destroy; gp_step, gp_observables, gp_time_kernels and
+ * gp_autotune return GP_EINVAL.
+ */
+int gp_create_slab(const gp_grid *global_grid, const double dx[3], double dt, double gamma,
+                   double nu, double lambda, double g, int nranks, const int *bounds, int rank,
+                   void *cuda_stream, gp_ctx **out);
+/* Complex128 values each rank publishes per step (2 nx ny: its first and
+ * last unknown planes); the gathered buffer is nranks times that. */
+int gp_slab_exchange_count(gp_ctx *ctx, int64_t *count);
+/* This rank's part of the unnormalised Gaussian seed (global coordinates);
+ * the caller sums the norm over ranks and applies gp_slab_scale. */
+int gp_slab_seed(gp_ctx *ctx);
+/* psi <- factor * psi on this rank (synchronises). */
+int gp_slab_scale(gp_ctx *ctx, double factor);
+/*
+ * First half of one SSCN step: the nonlinear step fused into the x sweep, the
+ * y sweep and the block-local z sweep, then bnd_device (2 nx ny complex128,
+ * device) <- this rank's block solution on its first and last unknown
+ * planes.  Enqueued on the context's stream.
+ */
+int gp_slab_step_begin(gp_ctx *ctx, void *bnd_device);
+/*
+ * Second half: bnd_all_device (device, nranks * 2 nx ny complex128, rank q's
+ * planes at offset q * 2 nx ny in gp_slab_step_begin's layout) gives the
+ * reduced system; this rank's planes are corrected to the coupled solution.
+ * Enqueued on the context's stream after everything that wrote
+ * bnd_all_device (the caller orders its collective on that stream).
+ */
+int gp_slab_step_end(gp_ctx *ctx, const void *bnd_all_device);
+/* out_device (nx ny complex128) <- this rank's first unknown plane (the plane
+ * its lower neighbour needs for the z-derivative term of the observables). */
+int gp_slab_first_plane(gp_ctx *ctx, void *out_device);
+/*
+ * This rank's 9 observable sums (FP64; synchronises); next_first_device is
+ * the next rank's gp_slab_first_plane (NULL on the last rank), for the term
+ * across the interface.  The sums of all ranks add up to those of the whole
+ * grid; gp_slab_observables finishes them.
+ */
+int gp_slab_local_sums(gp_ctx *ctx, const void *next_first_device, double sums[9]);
+int gp_slab_observables(gp_ctx *ctx, const double global_sums[9], gp_obs *out);
+
 /* Options of a context (gp_set_option / gp_get_option). */
 enum {
     /* Sweep kernel: GP_PATH_AUTO picks per axis and mode; GP_PATH_EXACT is one

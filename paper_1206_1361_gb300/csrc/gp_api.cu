@@ -71,6 +71,16 @@ struct gp_ctx {
     void *ffmem = nullptr;          // one allocation for all of them
     float2 *obs_ff = nullptr;       // x_i^2, then w_x^2 x_i^2 / 2, as float-float pairs
 
+    // z-slab of a grid split over several GPUs (gp_create_slab): local plane k
+    // is global plane z0 + k of a z_global-plane grid
+    bool slab = false;
+    int slab_P = 1, slab_rank = 0, z_global = 0, z0 = 0, slab_nloc = 0;
+    double2 *slab_consts = nullptr;    // device: the reduced system's two inverse rows (4 P)
+    double2 *slab_spike = nullptr;     // device: s then t on the local unknown planes
+    void *slab_saved = nullptr;        // device: psi on the first / last unknown plane
+    double *slab_part = nullptr;       // device: interface reduction partials + result
+    double *slab_host = nullptr;       // pinned: interface result
+
     CUtensorMap maps[3];            // 64-byte aligned type
     bool map_ok[3]{};
     bool tma_ok[2][3]{};            // [mode][axis] TMA path eligible
@@ -161,6 +171,7 @@ double cell_volume(const gp_ctx *c)
 double axis_coord(const gp_ctx *c, int k, int i)
 {
     if (c->axial && k == 0) return (i + 0.5) * c->h[0];
+    if (c->slab && k == 2) return coord(c->z_global, c->h[2], c->z0 + i);
     return coord(edge(c->grid, k), c->h[k], i);
 }
 
@@ -462,6 +473,11 @@ void release(gp_ctx *c)
     fr(c->psi);
     fr(c->work);
     fr(c->ffmem);
+    fr(c->slab_consts);
+    fr(c->slab_spike);
+    fr(c->slab_saved);
+    fr(c->slab_part);
+    if (c->slab_host) cudaFreeHost(c->slab_host);
     fr(c->obs_ff);
     for (auto &row : c->ax)
         for (auto &a : row) { fr(a.cp64); fr(a.mult64); fr(a.cp32); fr(a.mult32); }
@@ -895,9 +911,13 @@ int gp_footprint(const gp_grid *grid, int precision, size_t *bytes)
 }
 
 namespace {
+// Where a z-slab context sits in its grid (gp_create_slab).
+struct SlabSpec {
+    int P, rank, z_global, z0;
+};
 int create_ctx(const gp_grid *grid, const double dx[3], double dt, double gamma, double nu,
                double lambda, double g, int mode, int precision, void *cuda_stream, bool axial,
-               gp_ctx **out);
+               gp_ctx **out, const SlabSpec *slab = nullptr);
 }
 
 int gp_create(const gp_grid *grid, const double dx[3], double dt, double gamma, double nu,
@@ -947,7 +967,7 @@ int gp_footprint_axial(int nr, int nz, int precision, size_t *bytes)
 namespace {
 int create_ctx(const gp_grid *grid, const double dx[3], double dt, double gamma, double nu,
                double lambda, double g, int mode, int precision, void *cuda_stream, bool axial,
-               gp_ctx **out)
+               gp_ctx **out, const SlabSpec *slab)
 {
     const int nd = grid->nz > 1 ? 3 : 2;
     if (!(dt > 0) || !std::isfinite(dt)) return fail(nullptr, GP_EINVAL, "gp_create: dt must be > 0");
@@ -972,6 +992,13 @@ int create_ctx(const gp_grid *grid, const double dx[3], double dt, double gamma,
     c->mode = mode;
     c->prec = precision;
     c->axial = axial;
+    if (slab) {
+        c->slab = true;
+        c->slab_P = slab->P;
+        c->slab_rank = slab->rank;
+        c->z_global = slab->z_global;
+        c->z0 = slab->z0;
+    }
 
     auto bail = [&](int rc) {
         g_create_error = c->last_error;
@@ -1097,6 +1124,7 @@ int create_ctx(const gp_grid *grid, const double dx[3], double dt, double gamma,
 int gp_load(gp_ctx *c, const void *psi, int64_t count, int on_device)
 {
     if (!c) return fail(nullptr, GP_EINVAL, "gp_load: null context");
+    if (c->slab && !psi) return fail(c, GP_EINVAL, "gp_load: a z-slab seeds with gp_slab_seed");
     const long long n = points(c->grid);
     c->scale_pending = false;
     c->step = 0;
@@ -1179,6 +1207,8 @@ int gp_set_params(gp_ctx *c, double g, int mode)
     if (!c) return fail(nullptr, GP_EINVAL, "gp_set_params: null context");
     if (!std::isfinite(g) || (mode != GP_IMAG && mode != GP_REAL))
         return fail(c, GP_EINVAL, "gp_set_params: bad g or mode");
+    if (c->slab && mode != GP_REAL)
+        return fail(c, GP_EINVAL, "gp_set_params: a z-slab runs in real time");
     if (mode != c->mode) {
         int rc = materialize_scale(c);
         if (rc) return rc;
@@ -1204,6 +1234,7 @@ int gp_set_modulation(gp_ctx *c, double g1, double omega)
 int gp_step(gp_ctx *c, int64_t n)
 {
     if (!c) return fail(nullptr, GP_EINVAL, "gp_step: null context");
+    if (c->slab) return fail(c, GP_EINVAL, "gp_step: a z-slab steps with gp_slab_step_begin / _end");
     if (n < 0) return fail(c, GP_EINVAL, "gp_step: n < 0");
     if (n == 0) return GP_OK;
     if (int rc = prepare_pot3(c)) return rc;
@@ -1222,14 +1253,13 @@ int gp_step(gp_ctx *c, int64_t n)
     return GP_OK;
 }
 
-int gp_observables(gp_ctx *c, gp_obs *o)
+namespace {
+// N, mu, E and the rms sizes from the 9 sums of the observables pass
+// (complex64: K_k; otherwise R_k in place of K_k).
+void finish_observables(const gp_ctx *c, const double *sums, gp_obs *o)
 {
-    if (!c || !o) return fail(c, GP_EINVAL, "gp_observables: null argument");
-    int rc0 = enqueue_observables(c);
-    if (rc0) return rc0;
-    int rc = read_errors(c);
     double s[gp::kObsWidth];
-    std::memcpy(s, c->host_sums, sizeof(s));
+    std::memcpy(s, sums, sizeof(s));
     if (c->prec != GP_C64 && !c->axial)
         for (int k = 6; k < 9; ++k) s[k] = 2.0 * s[0] - 2.0 * s[k];     // K_k from R_k
     const double w = cell_volume(c);
@@ -1255,6 +1285,17 @@ int gp_observables(gp_ctx *c, gp_obs *o)
     }
     o->step = c->step;
     o->t = c->step * c->dt;
+}
+}  // namespace
+
+int gp_observables(gp_ctx *c, gp_obs *o)
+{
+    if (!c || !o) return fail(c, GP_EINVAL, "gp_observables: null argument");
+    if (c->slab) return fail(c, GP_EINVAL, "gp_observables: a z-slab needs the sums of every rank (gp_slab_*)");
+    int rc0 = enqueue_observables(c);
+    if (rc0) return rc0;
+    int rc = read_errors(c);
+    finish_observables(c, c->host_sums, o);
     if (rc) return rc;
     const double v[7] = {o->norm, o->mu, o->energy, o->rms_x, o->rms_y, o->rms_z, o->rms_r};
     for (double x : v)
@@ -1264,8 +1305,8 @@ int gp_observables(gp_ctx *c, gp_obs *o)
 
 int gp_time_kernels(gp_ctx *c, int64_t steps, double *ms_out, int n_out)
 {
-    if (!c || !ms_out || n_out < 5 || steps < 1)
-        return fail(c, GP_EINVAL, "gp_time_kernels: need steps >= 1 and n_out >= 5");
+    if (!c || !ms_out || n_out < 5 || steps < 1 || c->slab)
+        return fail(c, GP_EINVAL, "gp_time_kernels: need steps >= 1 and n_out >= 5 (not on a z-slab)");
     if (int rc0 = prepare_pot3(c)) return rc0;
     cudaEvent_t ev[5];
     for (auto &e : ev) GP_CK(c, cudaEventCreate(&e));
@@ -1309,6 +1350,8 @@ int gp_set_option(gp_ctx *c, int option, int value)
             return fail(c, GP_EINVAL, "gp_set_option: unknown splitting");
         if (value == GP_SPLIT_STRANG && is_ff(c))
             return fail(c, GP_EINVAL, "gp_set_option: the float-float form runs the plain splitting");
+        if (value == GP_SPLIT_STRANG && c->slab)
+            return fail(c, GP_EINVAL, "gp_set_option: a z-slab runs the plain splitting");
         c->split = value;
         drop_graph(c);
         return GP_OK;
@@ -1368,7 +1411,7 @@ int gp_set_option(gp_ctx *c, int option, int value)
 
 int gp_autotune(gp_ctx *c, int steps, int *path_out, int *shape_out, double *ms_out)
 {
-    if (!c || steps < 1) return fail(c, GP_EINVAL, "gp_autotune: need steps >= 1");
+    if (!c || steps < 1 || c->slab) return fail(c, GP_EINVAL, "gp_autotune: need steps >= 1 (not on a z-slab)");
     const size_t bytes = (size_t)points(c->grid) * elem_bytes(c->prec);
     void *saved = nullptr;
     double *saved_scale = nullptr;
@@ -1525,6 +1568,271 @@ void gp_destroy(gp_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     release(c);
     delete c;
+}
+
+
+// ------------------------------------------------------------------ z-slabs
+
+namespace {
+// Solve (I - kappa L) x = b (m unknowns) with the host FP64 tables (the same
+// recurrence as the device tables).
+void host_solve(int m, const double2 *cp, const double2 *mult, std::complex<double> kappa,
+                const std::vector<std::complex<double>> &b, std::vector<std::complex<double>> &x)
+{
+    std::vector<std::complex<double>> d(m);
+    std::complex<double> prev = 0.0;
+    for (int i = 0; i < m; ++i) {
+        prev = (b[i] + kappa * prev) * std::complex<double>(mult[i].x, mult[i].y);
+        d[i] = prev;
+    }
+    x.assign(m, 0.0);
+    x[m - 1] = d[m - 1];
+    for (int i = m - 2; i >= 0; --i) x[i] = d[i] - std::complex<double>(cp[i].x, cp[i].y) * x[i + 1];
+}
+
+// s = A^{-1} (kappa e_first), t = A^{-1} (kappa e_last) of an m-unknown block
+void spikes(int m, double kim, std::vector<std::complex<double>> &s, std::vector<std::complex<double>> &t)
+{
+    std::vector<double2> cp(m), mult(m);
+    gp::host_thomas_tables(m, 0.0, kim, cp.data(), mult.data());
+    const std::complex<double> kappa(0.0, kim);
+    std::vector<std::complex<double>> b(m, 0.0);
+    b[0] = kappa;
+    host_solve(m, cp.data(), mult.data(), kappa, b, s);
+    b[0] = 0.0;
+    b[m - 1] = kappa;
+    host_solve(m, cp.data(), mult.data(), kappa, b, t);
+}
+
+long long slab_plane(const gp_ctx *c) { return (long long)c->grid.nx * c->grid.ny; }
+
+// The reduced system of the boundary values, the same on every z line: with
+// unknowns L_q (q = 0 .. P-2) at index 2q and F_q (q = 1 .. P-1) at 2q - 1,
+//     L_q - sL_q L_{q-1} - tL_q F_{q+1} = yL_q,   F_q - sF_q L_{q-1} - tF_q F_{q+1} = yF_q.
+// w <- the rows of its inverse that give L_{rank-1} (w[0 .. 2P)) and
+// F_{rank+1} (w[2P .. 4P)), each as weights of the gathered values in their
+// layout (rank q's yF at 2q, yL at 2q + 1); false if the matrix is singular.
+bool reduced_rows(int P, int rank, const std::vector<std::complex<double>> &sF,
+                  const std::vector<std::complex<double>> &sL, const std::vector<std::complex<double>> &tF,
+                  const std::vector<std::complex<double>> &tL, std::vector<double2> &w)
+{
+    using cd = std::complex<double>;
+    const int n = 2 * (P - 1);
+    auto iL = [](int q) { return 2 * q; };
+    auto iF = [](int q) { return 2 * q - 1; };
+    std::vector<cd> a((size_t)n * n, 0.0), inv((size_t)n * n, 0.0);
+    auto A = [&](int r, int k) -> cd & { return a[(size_t)r * n + k]; };
+    auto X = [&](int r, int k) -> cd & { return inv[(size_t)r * n + k]; };
+    for (int q = 0; q < P; ++q) {
+        if (q <= P - 2) {
+            A(iL(q), iL(q)) = 1.0;
+            if (q >= 1) A(iL(q), iL(q - 1)) = -sL[q];
+            A(iL(q), iF(q + 1)) = -tL[q];
+        }
+        if (q >= 1) {
+            A(iF(q), iF(q)) = 1.0;
+            A(iF(q), iL(q - 1)) = -sF[q];
+            if (q <= P - 2) A(iF(q), iF(q + 1)) = -tF[q];
+        }
+    }
+    for (int r = 0; r < n; ++r) X(r, r) = 1.0;
+    // Gauss-Jordan with partial pivoting
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::abs(A(r, col)) > std::abs(A(piv, col))) piv = r;
+        if (std::abs(A(piv, col)) == 0.0) return false;
+        for (int k = 0; k < n; ++k) {
+            std::swap(A(col, k), A(piv, k));
+            std::swap(X(col, k), X(piv, k));
+        }
+        const cd d = A(col, col);
+        for (int k = 0; k < n; ++k) {
+            A(col, k) /= d;
+            X(col, k) /= d;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            const cd f = A(r, col);
+            if (f == 0.0) continue;
+            for (int k = 0; k < n; ++k) {
+                A(r, k) -= f * A(col, k);
+                X(r, k) -= f * X(col, k);
+            }
+        }
+    }
+    // column of the unknown's equation -> slot of its right-hand side
+    auto slot = [&](int k) { return (k % 2 == 0) ? 2 * (k / 2) + 1 : 2 * ((k + 1) / 2); };
+    const int rows[2] = {rank >= 1 ? iL(rank - 1) : -1, rank <= P - 2 ? iF(rank + 1) : -1};
+    for (int h = 0; h < 2; ++h) {
+        if (rows[h] < 0) continue;
+        for (int k = 0; k < n; ++k) {
+            const cd v = X(rows[h], k);
+            w[(size_t)h * 2 * P + slot(k)] = make_double2(v.real(), v.imag());
+        }
+    }
+    return true;
+}
+}  // namespace
+
+int gp_create_slab(const gp_grid *global, const double dx[3], double dt, double gamma, double nu,
+                   double lambda, double g, int nranks, const int *bounds, int rank,
+                   void *cuda_stream, gp_ctx **out)
+{
+    if (out) *out = nullptr;
+    if (!out || !valid_grid(global) || global->nz < 3 || !dx || !bounds)
+        return fail(nullptr, GP_EINVAL, "gp_create_slab: invalid grid (3D) or null argument");
+    if (nranks < 1 || nranks > gp::kSlabMaxRanks || rank < 0 || rank >= nranks)
+        return fail(nullptr, GP_EINVAL, "gp_create_slab: 1 <= nranks <= 8 and 0 <= rank < nranks");
+    if (bounds[0] != 0 || bounds[nranks] != global->nz)
+        return fail(nullptr, GP_EINVAL, "gp_create_slab: bounds must run from 0 to nz");
+    for (int q = 0; q < nranks; ++q) {
+        const int unknowns = bounds[q + 1] - bounds[q] - (q == 0 ? 1 : 0);
+        if (unknowns < 2) return fail(nullptr, GP_EINVAL, "gp_create_slab: every slab needs >= 2 unknown planes");
+    }
+    for (int k = 0; k < 3; ++k)
+        if (!(dx[k] > 0) || !std::isfinite(dx[k])) return fail(nullptr, GP_EINVAL, "gp_create_slab: dx must be > 0");
+    const int nzl = rank == 0 ? bounds[1] : bounds[rank + 1] - bounds[rank] + 1;
+    const gp_grid local{global->nx, global->ny, nzl};
+    const SlabSpec spec{nranks, rank, global->nz, rank == 0 ? 0 : bounds[rank] - 1};
+    gp_ctx *c = nullptr;
+    int rc = create_ctx(&local, dx, dt, gamma, nu, lambda, g, GP_REAL, GP_C128, cuda_stream, false, &c, &spec);
+    if (rc) return rc;
+    // spikes of every rank's block: the reduced matrix, this rank's spikes
+    const double kim = dt / (4.0 * dx[2] * dx[2]);
+    std::vector<std::complex<double>> sF(nranks), sL(nranks), tF(nranks), tL(nranks), s, t;
+    for (int q = 0; q < nranks && !rc; ++q) {
+        const int m = bounds[q + 1] - bounds[q] - (q == 0 ? 1 : 0);
+        spikes(m, kim, s, t);
+        sF[q] = s[0];
+        sL[q] = s[m - 1];
+        tF[q] = t[0];
+        tL[q] = t[m - 1];
+        if (q == rank) {
+            c->slab_nloc = m;
+            std::vector<double2> sp(2 * (size_t)m);
+            for (int i = 0; i < m; ++i) {
+                sp[i] = make_double2(s[i].real(), s[i].imag());
+                sp[m + i] = make_double2(t[i].real(), t[i].imag());
+            }
+            if ((rc = alloc(c, (void **)&c->slab_spike, sp.size() * sizeof(double2)))) break;
+            cudaError_t e = cudaMemcpy(c->slab_spike, sp.data(), sp.size() * sizeof(double2), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) rc = cuda_fail(c, e, "gp_create_slab: spikes");
+        }
+    }
+    std::vector<double2> w(4 * (size_t)nranks, make_double2(0.0, 0.0));
+    if (!rc && nranks > 1 && !reduced_rows(nranks, rank, sF, sL, tF, tL, w))
+        rc = fail(c, GP_EINVAL, "gp_create_slab: singular reduced system");
+    const long long plane = slab_plane(c);
+    if (!rc) rc = alloc(c, (void **)&c->slab_consts, w.size() * sizeof(double2));
+    if (!rc) {
+        cudaError_t e = cudaMemcpy(c->slab_consts, w.data(), w.size() * sizeof(double2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "gp_create_slab: reduced rows");
+    }
+    if (!rc) rc = alloc(c, &c->slab_saved, 2 * (size_t)plane * sizeof(double2));
+    if (!rc) rc = alloc(c, (void **)&c->slab_part, (gp::kReduceBlocks + 1) * sizeof(double));
+    if (!rc) {
+        cudaError_t e = cudaMallocHost((void **)&c->slab_host, sizeof(double));
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "cudaMallocHost");
+    }
+    if (rc) {
+        g_create_error = c->last_error;
+        gp_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return GP_OK;
+}
+
+int gp_slab_exchange_count(gp_ctx *c, int64_t *count)
+{
+    if (!c || !c->slab || !count) return fail(c, GP_EINVAL, "gp_slab_exchange_count: not a z-slab");
+    *count = 2 * slab_plane(c);
+    return GP_OK;
+}
+
+int gp_slab_seed(gp_ctx *c)
+{
+    if (!c || !c->slab) return fail(c, GP_EINVAL, "gp_slab_seed: not a z-slab");
+    c->step = 0;
+    c->scale_pending = false;
+    GP_CK(c, gp::launch_set_step(c->step_dev, 0, c->stream));
+    GP_CK(c, gp::launch_slab_seed(c->psi, c->grid.nx, c->grid.ny, c->grid.nz, c->z_global, c->z0, c->h,
+                                  c->w, c->stream));
+    return GP_OK;
+}
+
+int gp_slab_scale(gp_ctx *c, double factor)
+{
+    if (!c || !c->slab || !std::isfinite(factor)) return fail(c, GP_EINVAL, "gp_slab_scale: bad argument");
+    GP_CK(c, cudaMemcpyAsync(c->scale, &factor, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    GP_CK(c, gp::launch_apply_scale(GP_C128, c->psi, points(c->grid), c->scale, c->stream));
+    GP_CK(c, cudaStreamSynchronize(c->stream));   // `factor`
+    return GP_OK;
+}
+
+int gp_slab_step_begin(gp_ctx *c, void *bnd)
+{
+    if (!c || !c->slab || !bnd) return fail(c, GP_EINVAL, "gp_slab_step_begin: not a z-slab or null buffer");
+    if (int rc = prepare_pot3(c)) return rc;
+    const long long plane = slab_plane(c);
+    const int kl = c->grid.nz - 1;
+    gp::NonlinArgs nl = pointwise_args(c, 0, false, 0.0, 1.0, c->scale);
+    if (uses_pot3(c) && pot3_for(c)) nl.p3 = pot3_for(c);
+    GP_CK(c, launch_sweep(c, 0, &nl, false, nullptr, nullptr));
+    GP_CK(c, launch_sweep(c, 1, nullptr, false, nullptr, nullptr));
+    GP_CK(c, gp::launch_slab_capture(c->psi, c->slab_saved, plane, 1, kl, c->stream));
+    GP_CK(c, launch_sweep(c, 2, nullptr, false, nullptr, nullptr));
+    GP_CK(c, gp::launch_slab_bnd(c->psi, c->slab_saved, bnd, plane, 1, kl, c->stream));
+    return GP_OK;
+}
+
+int gp_slab_step_end(gp_ctx *c, const void *bnd_all)
+{
+    if (!c || !c->slab || !bnd_all) return fail(c, GP_EINVAL, "gp_slab_step_end: not a z-slab or null buffer");
+    GP_CK(c, gp::launch_slab_correct(c->psi, bnd_all, c->slab_consts, c->slab_spike, c->slab_P,
+                                     slab_plane(c), c->slab_nloc, c->stream));
+    if (modulated(c)) GP_CK(c, gp::launch_add_step(c->step_dev, c->stream));
+    c->step += 1;
+    return GP_OK;
+}
+
+int gp_slab_first_plane(gp_ctx *c, void *out)
+{
+    if (!c || !c->slab || !out) return fail(c, GP_EINVAL, "gp_slab_first_plane: not a z-slab or null buffer");
+    const long long plane = slab_plane(c);
+    GP_CK(c, cudaMemcpyAsync(out, static_cast<double2 *>(c->psi) + plane, plane * sizeof(double2),
+                             cudaMemcpyDeviceToDevice, c->stream));
+    return GP_OK;
+}
+
+int gp_slab_local_sums(gp_ctx *c, const void *next_first, double sums[9])
+{
+    if (!c || !c->slab || !sums) return fail(c, GP_EINVAL, "gp_slab_local_sums: not a z-slab or null argument");
+    const long long plane = slab_plane(c);
+    int rc = enqueue_observables(c);
+    if (rc) return rc;
+    if (next_first) {
+        const double2 *last = static_cast<const double2 *>(c->psi) + (long long)(c->grid.nz - 1) * plane;
+        GP_CK(c, gp::launch_slab_interface(last, next_first, plane, c->slab_part,
+                                           c->slab_part + gp::kReduceBlocks, c->stream));
+        GP_CK(c, cudaMemcpyAsync(c->slab_host, c->slab_part + gp::kReduceBlocks, sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->stream));
+    }
+    if ((rc = read_errors(c))) return rc;
+    std::memcpy(sums, c->host_sums, gp::kObsWidth * sizeof(double));
+    if (next_first) sums[8] += *c->slab_host;      // R_z across the interface
+    return GP_OK;
+}
+
+int gp_slab_observables(gp_ctx *c, const double sums[9], gp_obs *out)
+{
+    if (!c || !c->slab || !sums || !out) return fail(c, GP_EINVAL, "gp_slab_observables: not a z-slab or null argument");
+    finish_observables(c, sums, out);
+    const double v[7] = {out->norm, out->mu, out->energy, out->rms_x, out->rms_y, out->rms_z, out->rms_r};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(c, GP_ENONFINITE, "gp_slab_observables: non-finite result");
+    return GP_OK;
 }
 
 }  // extern "C"

@@ -383,6 +383,30 @@ inline void thomas_step(double kre, double kim, double pr, double pi, double2 &m
 // Record msg as the message gp_last_error(NULL) returns in this thread.
 void set_thread_error(const char *msg);
 
+// ---- z-slab decomposition of one grid over several GPUs (sscn_zslab.cu) -----
+constexpr int kSlabMaxRanks = 8;
+// Unnormalised Gaussian seed of a slab: local plane k at global plane z0 + k
+// of an nzg-plane grid; local plane 0 and the x, y Dirichlet nodes zero.
+cudaError_t launch_slab_seed(void *psi, int nx, int ny, int nzl, int nzg, int z0, const double h[3],
+                             const double w[3], cudaStream_t st);
+// saved <- psi's local planes kf and kl (two planes of `plane` points).
+cudaError_t launch_slab_capture(const void *psi, void *saved, long long plane, int kf, int kl,
+                                cudaStream_t st);
+// bnd <- (u_loc + psi_saved) / 2 on planes kf and kl: the zero-coupling
+// solution y on the slab's first and last unknown planes.
+cudaError_t launch_slab_bnd(const void *psi, const void *saved, void *bnd, long long plane, int kf,
+                            int kl, cudaStream_t st);
+// alpha = L_{rank-1}, beta = F_{rank+1} of every z line as the combinations
+// w[0 .. 2P) and w[2P .. 4P) of all ranks' bnd blocks ([P][first | last]
+// [plane]), then psi[k] += 2 (s[k] alpha + t[k] beta) for local planes
+// k = 1 .. nloc (spike: s then t, nloc entries each).  P = 1: nothing.
+cudaError_t launch_slab_correct(void *psi, const void *bnd_all, const double2 *w,
+                                const double2 *spike, int P, long long plane, int nloc,
+                                cudaStream_t st);
+// *out <- sum over the plane of Re(next * conj(last)) (fixed-order partials).
+cudaError_t launch_slab_interface(const void *last_plane, const void *next_plane, long long plane,
+                                  double *partials, double *out, cudaStream_t st);
+
 constexpr int kObsWidth = 9;
 constexpr int kReduceBlocks = 608;      // 4 x 152 SMs for grid-stride reductions
 

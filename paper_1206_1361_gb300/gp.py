@@ -83,6 +83,17 @@ SIGNATURES = {
                                 _vp]),
     "gp_measure_peak": (_int, [_int, _i64, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)]),
+    "gp_create_slab": (_int, [ctypes.POINTER(gp_grid), ctypes.POINTER(ctypes.c_double), _dbl,
+                              _dbl, _dbl, _dbl, _dbl, _int, ctypes.POINTER(_int), _int, _vp,
+                              ctypes.POINTER(_vp)]),
+    "gp_slab_exchange_count": (_int, [_vp, ctypes.POINTER(_i64)]),
+    "gp_slab_seed": (_int, [_vp]),
+    "gp_slab_scale": (_int, [_vp, _dbl]),
+    "gp_slab_step_begin": (_int, [_vp, _vp]),
+    "gp_slab_step_end": (_int, [_vp, _vp]),
+    "gp_slab_first_plane": (_int, [_vp, _vp]),
+    "gp_slab_local_sums": (_int, [_vp, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "gp_slab_observables": (_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(gp_obs)]),
     "gp_last_error": (ctypes.c_char_p, [_vp]),
     "gp_destroy": (None, [_vp]),
     "gp_batch_create": (_int, [_int, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
@@ -342,6 +353,59 @@ def gp_measure_peak(kind, iters=20000):
     if rc != GP_OK:
         raise GPError(rc, gp_last_error(None))
     return tf.value, ms.value
+
+
+def gp_create_slab(grid, dx, dt, gamma, nu, lam, g, bounds, rank, cuda_stream=None):
+    """One rank's context of a grid split along z (see zslab.py)."""
+    gr = gp_grid(*[int(v) for v in grid])
+    h = (ctypes.c_double * 3)(*[float(v) for v in dx])
+    b = (_int * len(bounds))(*[int(v) for v in bounds])
+    out = _vp()
+    rc = load_library().gp_create_slab(ctypes.byref(gr), h, float(dt), float(gamma), float(nu),
+                                       float(lam), float(g), len(bounds) - 1, b, int(rank),
+                                       _stream_handle(cuda_stream), ctypes.byref(out))
+    if rc != GP_OK:
+        raise GPError(rc, gp_last_error(None))
+    return out.value
+
+
+def gp_slab_exchange_count(ctx):
+    n = _i64()
+    _err(ctx, load_library().gp_slab_exchange_count(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def gp_slab_seed(ctx):
+    _err(ctx, load_library().gp_slab_seed(ctx))
+
+
+def gp_slab_scale(ctx, factor):
+    _err(ctx, load_library().gp_slab_scale(ctx, float(factor)))
+
+
+def gp_slab_step_begin(ctx, bnd_device):
+    _err(ctx, load_library().gp_slab_step_begin(ctx, bnd_device))
+
+
+def gp_slab_step_end(ctx, bnd_all_device):
+    _err(ctx, load_library().gp_slab_step_end(ctx, bnd_all_device))
+
+
+def gp_slab_first_plane(ctx, out_device):
+    _err(ctx, load_library().gp_slab_first_plane(ctx, out_device))
+
+
+def gp_slab_local_sums(ctx, next_first_device=None):
+    s = (ctypes.c_double * 9)()
+    _err(ctx, load_library().gp_slab_local_sums(ctx, next_first_device, s))
+    return np.array(s[:], dtype=np.float64)
+
+
+def gp_slab_observables(ctx, global_sums):
+    s = (ctypes.c_double * 9)(*[float(v) for v in global_sums])
+    o = gp_obs()
+    _err(ctx, load_library().gp_slab_observables(ctx, s, ctypes.byref(o)))
+    return o.as_dict()
 
 
 def gp_last_error(ctx=None):
