@@ -18,9 +18,15 @@ def cache_path():
                                        "autotune.json"))
 
 
+# Revision of the libraries' tile-shape tables: a cached shape index names an
+# entry of the table it was measured on.
+SHAPE_TABLE = 2
+
+
 def problem_key(shape, h, dt, precision, mode):
     kap = ["%.2g" % (dt / (4.0 * hk * hk)) for hk in h[:3 if shape[2] > 1 else 2]]
-    return "%dx%dx%d/p%d/m%d/k%s" % (shape[0], shape[1], shape[2], precision, mode, ",".join(kap))
+    return "%dx%dx%d/p%d/m%d/k%s/t%d" % (shape[0], shape[1], shape[2], precision, mode,
+                                        ",".join(kap), SHAPE_TABLE)
 
 
 def _load(path):

@@ -2,10 +2,11 @@
 //
 // Acc<double> adds in FP64.  Acc<float> serves the complex64 form, whose
 // per-point terms are FP32 products of FP32 values: a thread's run of terms
-// (at most one grid line) is summed with Kahan's compensated summation in
-// FP32 -- error within about two FP32 ulps of the partial, below the rounding
-// of the complex64 state itself -- and handed to the FP64 reductions across
-// threads, lines and blocks.  On GB300 an FP64 add costs as much FP64-pipe
+// (a grid line, or a lane's points of several lines) is summed with Kahan's
+// compensated summation in FP32 -- error within about two FP32 ulps of the
+// partial, independent of the number of terms, below the rounding of the
+// complex64 state itself -- and handed to the FP64 reductions across threads
+// and blocks.  On GB300 an FP64 add costs as much FP64-pipe
 // time as ~60 FP32 operations, so this keeps the complex64 kernels off the
 // FP64 pipe.
 #pragma once

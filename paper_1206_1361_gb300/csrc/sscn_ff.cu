@@ -72,6 +72,9 @@ __device__ __forceinline__ C ld(const unsigned char *p)
     const float4 v = *reinterpret_cast<const float4 *>(p);
     return C{f2(v.x, v.y), f2(v.z, v.w)};
 }
+// point c of a chunk loaded whole from tensor memory (tmem_ld32)
+#define GP_FF_FROM(w, c) C{f2((w)[4 * (c)], (w)[4 * (c) + 1]), f2((w)[4 * (c) + 2], (w)[4 * (c) + 3])}
+
 __device__ __forceinline__ void st(unsigned char *p, C z)
 {
     *reinterpret_cast<float4 *>(p) = make_float4(z.hi.x, z.hi.y, z.lo.x, z.lo.y);
@@ -173,13 +176,42 @@ template <int L, int AXIS> struct FfTile {
     }
 };
 
+// Columns of tensor memory a CTA of the TMEM-ring shapes allocates: d' of
+// two chunks of C points, 4 FP32 words (re hi, im hi, re lo, im lo) each.
+constexpr int kTmemCols = 2 * kC * 4;
+
+template <int K, int S, bool TM>
+constexpr size_t ff_smem_bytes()
+{
+    constexpr size_t L = 32 * K;
+    return 1024 + (size_t)S * L * kC * 16 + (TM ? 0 : 2 * (size_t)kC * L * 16) +
+           2 * S * sizeof(uint64_t) + 32 * sizeof(double) + 16;
+}
+
+// Resident CTAs per SM the TMEM shapes are built for: as many as shared
+// memory admits, at most 512 / kTmemCols (the columns of one SM).
+template <int K, int S, bool TM>
+constexpr int ff_min_blocks()
+{
+    if (!TM) return 1;
+    constexpr int by_smem = (int)((227 * 1024) / ff_smem_bytes<K, S, TM>());
+    constexpr int by_tmem = 512 / kTmemCols;
+    return by_smem < by_tmem ? by_smem : by_tmem;
+}
+
 // Warp-specialised CTA: K consumer warps own L = 32 K lines; warp K is the
 // producer, whose lane 0 issues every TMA load and store.  full[s] completes
 // when a chunk has landed, ready[s] when all K consumer warps have written
 // the chunk's final values; the producer stores a ready chunk and reuses its
 // stage once the store has read shared memory.
-template <int MODE, int AXIS, bool NL, bool NORM, int K, int S>
-__global__ void __launch_bounds__(32 * (K + 1))
+// TM: the d' ring lives in tensor memory (each consumer thread's line in
+// its TMEM lane), which leaves shared memory to the stages and so admits
+// more resident CTAs; every lane of a consumer warp then runs the same
+// instruction stream (the tcgen05 accesses are warp-wide), lanes past the
+// end of a ragged tile computing on the zeros TMA filled in, whose rows the
+// TMA store clips.
+template <int MODE, int AXIS, bool NL, bool NORM, int K, int S, bool TM>
+__global__ void __launch_bounds__(32 * (K + 1), ff_min_blocks<K, S, TM>())
 k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
 {
     constexpr int L = 32 * K;
@@ -190,9 +222,10 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *stages = smem;
     float4 *ring = reinterpret_cast<float4 *>(stages + S * G::kStageBytes);   // [2][C][L]
-    uint64_t *full = reinterpret_cast<uint64_t *>(ring + 2 * Cc * L);
+    uint64_t *full = reinterpret_cast<uint64_t *>(ring + (TM ? 0 : 2 * Cc * L));
     uint64_t *ready = full + S;
     double *red = reinterpret_cast<double *>(ready + S);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(red + 32);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = warp == K;
@@ -200,6 +233,7 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
     const int tile0 = blockIdx.x * L;
     const int a = tile0 + l;
     const bool active = !producer && a < args.lines_a;
+    const bool run = TM ? !producer : active;       // computes (see TM above)
     const int m = args.n - 1;
     const int Q = (args.n + Cc - 1) / Cc;
     const int conv = args.conv, win = args.win;
@@ -212,6 +246,10 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
     auto stage_ptr = [&](int q) { return stages + (q % S) * G::kStageBytes; };
     auto at = [&](int q, int c) { return stage_ptr(q) + G::off(l, c); };
 
+    if (TM && warp == 0) {
+        tmem_alloc(tslot, kTmemCols);
+        tmem_relinquish();
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -219,7 +257,11 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
         }
         fence_mbar_init();
     }
+    if (TM) tmem_fence_before();
     __syncthreads();
+    if (TM) tmem_fence_after();
+    // this warp's TMEM lanes (consumer warps 0 .. K-1 reach lanes 32 (w % 4) ..)
+    const uint32_t tbase = TM ? *tslot + ((uint32_t)(32 * (warp & 3)) << 16) : 0u;
 
     bool failed = false;
     float2 nacc = f2(0.f, 0.f);        // float-float sum of |u|^2 (NORM)
@@ -258,19 +300,25 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
     } else {
         const FfLine<MODE> cn{args.kk_hi, args.kk_lo};
         FfCalcnu<MODE> nl;
-        if (NL && active) nl.setup(args, a, blockIdx.y);
+        // lanes past a ragged tile's end take the last line's factors
+        if (NL && run) nl.setup(args, active ? a : args.lines_a - 1, blockIdx.y);
         auto cp = [&](int t) -> FfCoef { return t < conv ? args.cp[t] : args.cinf; };
         auto mult = [&](int t) -> FfCoef { return t < conv ? args.mult[t] : args.minf; };
         auto slot = [&](int i) -> float4 * {
             return ring + ((i / Cc) & 1) * Cc * L + (i % Cc) * L + l;
         };
-        auto put = [&](int i, C d) { *slot(i) = make_float4(d.hi.x, d.hi.y, d.lo.x, d.lo.y); };
+        // TMEM column of point i: chunk parity, then 4 words per point
+        auto tcol = [&](int i) -> uint32_t { return (uint32_t)((((i / Cc) & 1) * Cc + i % Cc) * 4); };
+        auto put = [&](int i, C d) {
+            if (TM) tmem_st4(tbase + tcol(i), d.hi.x, d.hi.y, d.lo.x, d.lo.y);
+            else *slot(i) = make_float4(d.hi.x, d.hi.y, d.lo.x, d.lo.y);
+        };
         auto get = [&](int i) -> C {
-            const float4 v = *slot(i);
+            const float4 v = TM ? tmem_ld4(tbase + tcol(i)) : *slot(i);
             return C{f2(v.x, v.y), f2(v.z, v.w)};
         };
         auto acc_norm = [&](C u) {
-            if (NORM) nacc = s_norm(s_add(nacc, abs2(u)));
+            if (NORM && active) nacc = s_norm(s_add(nacc, abs2(u)));
         };
         auto output = [&](C v, unsigned char *tile_slot) {
             const C u = twice_minus(v, ld(tile_slot));
@@ -279,12 +327,14 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
         };
         C d = cz();
         for (int q = 0; q < Q; ++q) {
-            if (!mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs)) {
+            bool ok = mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs);
+            if (TM) ok = __all_sync(0xffffffffu, ok);    // the warp leaves together
+            if (!ok) {
                 failed = true;
                 break;
             }
             const bool last = q == Q - 1;
-            const bool fast = active && q >= 2 && !last && (q - 1) * Cc - 1 >= conv &&
+            const bool fast = run && q >= 2 && !last && (q - 1) * Cc - 1 >= conv &&
                               (q + 1) * Cc - 1 <= m;
             if (fast) {
                 // interior chunk: every point an unknown, constant tables
@@ -300,15 +350,35 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
                     d = cn.fwd(p, d, minf);
                     put(q * Cc + c, d);
                 }
-                C v = get(q * Cc + win - 1);
-                for (int c = win - 2; c >= 0; --c) v = cn.back(get(q * Cc + c), cinf, v);
+                if constexpr (TM) {
+                    // window: the seed d'_{W-1} by its own load (a runtime
+                    // column), then back through the chunk's points W-2 .. 0
+                    C v = get(q * Cc + win - 1);
+                    {
+                        float w[32];
+                        tmem_ld32(tbase + tcol(q * Cc), w);
 #pragma unroll
-                for (int c = Cc - 1; c >= 0; --c) {
-                    v = cn.back(get((q - 1) * Cc + c), cinf, v);
-                    output(v, at(q - 1, c));
+                        for (int c = Cc - 2; c >= 0; --c)
+                            if (c <= win - 2) v = cn.back(GP_FF_FROM(w, c), cinf, v);
+                    }
+                    float w[32];
+                    tmem_ld32(tbase + tcol((q - 1) * Cc), w);
+#pragma unroll
+                    for (int c = Cc - 1; c >= 0; --c) {
+                        v = cn.back(GP_FF_FROM(w, c), cinf, v);
+                        output(v, at(q - 1, c));
+                    }
+                } else {
+                    C v = get(q * Cc + win - 1);
+                    for (int c = win - 2; c >= 0; --c) v = cn.back(get(q * Cc + c), cinf, v);
+#pragma unroll
+                    for (int c = Cc - 1; c >= 0; --c) {
+                        v = cn.back(get((q - 1) * Cc + c), cinf, v);
+                        output(v, at(q - 1, c));
+                    }
                 }
             } else {
-                if (active) {
+                if (run) {
 #pragma unroll 2
                     for (int c = 0; c < Cc; ++c) {
                         const int j = q * Cc + c;
@@ -323,7 +393,7 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
                         }
                     }
                 }
-                if (active) {
+                if (run) {
                     if (!last && q >= 1) {
                         C v = get(q * Cc + win - 1);
                         for (int c = win - 2; c >= 0; --c) v = cn.back(get(q * Cc + c), cp(q * Cc + c - 1), v);
@@ -354,6 +424,16 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
         }
     }
     if (failed) atomicOr(args.err, kErrTimeout);
+    if (TM) {
+        // every warp is done with tensor memory before it is released
+        if (!producer) tmem_wait_st();
+        tmem_fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            tmem_fence_after();
+            tmem_dealloc(*tslot, kTmemCols);
+        }
+    }
     if (NORM) {
         double v = join(nacc);
 #pragma unroll
@@ -370,45 +450,49 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
     }
 }
 
-template <int K, int S>
-constexpr size_t ff_smem_bytes()
-{
-    constexpr size_t L = 32 * K;
-    return 1024 + (size_t)S * L * kC * 16 + 2 * (size_t)kC * L * 16 + 2 * S * sizeof(uint64_t) +
-           32 * sizeof(double);
-}
-
-template <int MODE, int AXIS, bool NL, bool NORM, int K, int S>
+template <int MODE, int AXIS, bool NL, bool NORM, int K, int S, bool TM>
 cudaError_t launch_inst(const CUtensorMap &map, const FfArgs &args, int tiles, int lines_b,
                         cudaStream_t st)
 {
-    auto kern = k_sweep_ff<MODE, AXIS, NL, NORM, K, S>;
-    constexpr size_t smem = ff_smem_bytes<K, S>();
-    static bool configured[64] = {};
+    auto kern = k_sweep_ff<MODE, AXIS, NL, NORM, K, S, TM>;
+    static size_t smem_of[64] = {};           // per device ordinal, 0: not configured
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!configured[dev]) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    if (!smem_of[dev]) {
+        size_t smem = ff_smem_bytes<K, S, TM>();
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        configured[dev] = true;
+        // TM: no more resident CTAs than one SM's tensor memory holds (an
+        // allocation beyond it would wait for another CTA to finish), so
+        // pad the shared memory until the occupancy says so
+        for (;;) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            if (!TM) break;
+            int blocks = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * (K + 1), smem);
+            if (e != cudaSuccess) return e;
+            if (blocks * kTmemCols <= 512) break;
+            smem += 1024;
+            if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+        }
+        smem_of[dev] = smem;
     }
-    kern<<<dim3(tiles, lines_b), 32 * (K + 1), smem, st>>>(map, args);
+    kern<<<dim3(tiles, lines_b), 32 * (K + 1), smem_of[dev], st>>>(map, args);
     return cudaGetLastError();
 }
 
-template <int AXIS, int K, int S>
+template <int AXIS, int K, int S, bool TM>
 cudaError_t launch_axis(int mode, bool nl, bool norm, const CUtensorMap &map, const FfArgs &args,
                         int tiles, int lines_b, cudaStream_t st)
 {
     // calcnu rides on the x sweep only
     if (nl && AXIS != 0) return cudaErrorInvalidValue;
 #define GP_FF(MODE, NLV, NORMV) \
-    return launch_inst<MODE, AXIS, (NLV && AXIS == 0), NORMV, K, S>(map, args, tiles, lines_b, st)
+    return launch_inst<MODE, AXIS, (NLV && AXIS == 0), NORMV, K, S, TM>(map, args, tiles, lines_b, st)
     if (mode == 0) {
         if (nl) { if (norm) GP_FF(0, true, true); GP_FF(0, true, false); }
         if (norm) GP_FF(0, false, true);
@@ -420,18 +504,22 @@ cudaError_t launch_axis(int mode, bool nl, bool norm, const CUtensorMap &map, co
 #undef GP_FF
 }
 
-// Tile shapes (consumer warps K, stages S); a CTA owns 32 K lines.
-struct Shape { int K, S; };
-constexpr Shape kShapes[] = {{2, 3}, {1, 4}, {2, 4}, {4, 3}};
-constexpr int kNumShapes = 4;
+// Tile shapes (consumer warps K, stages S, d' ring in tensor memory); a CTA
+// owns 32 K lines.  Index 0 is the default: the fastest measured at 256^3
+// (4 consumer warps, 3 stages, TMEM ring: 4 CTAs and 16 consumer warps per
+// SM, against 5 CTAs and 10 consumer warps with the ring in shared memory).
+struct Shape { int K, S; bool TM; };
+constexpr Shape kShapes[] = {{4, 3, true},  {2, 3, true},  {2, 4, true}, {2, 3, false},
+                             {1, 4, false}, {2, 4, false}, {4, 3, false}};
+constexpr int kNumShapes = 7;
 
-template <int K, int S>
+template <int K, int S, bool TM>
 cudaError_t launch_shape(int mode, int axis, bool nl, bool norm, const CUtensorMap &map,
                          const FfArgs &args, int tiles, int lines_b, cudaStream_t st)
 {
-    if (axis == 0) return launch_axis<0, K, S>(mode, nl, norm, map, args, tiles, lines_b, st);
-    if (axis == 1) return launch_axis<1, K, S>(mode, nl, norm, map, args, tiles, lines_b, st);
-    return launch_axis<2, K, S>(mode, nl, norm, map, args, tiles, lines_b, st);
+    if (axis == 0) return launch_axis<0, K, S, TM>(mode, nl, norm, map, args, tiles, lines_b, st);
+    if (axis == 1) return launch_axis<1, K, S, TM>(mode, nl, norm, map, args, tiles, lines_b, st);
+    return launch_axis<2, K, S, TM>(mode, nl, norm, map, args, tiles, lines_b, st);
 }
 
 Shape shape_of(int s) { return kShapes[s < 0 || s >= kNumShapes ? 0 : s]; }
@@ -465,15 +553,21 @@ __global__ void k_ff_to_c128(double2 *__restrict__ dst, const float4 *__restrict
 
 // --------------------------------------------------------------- observables
 //
-// One warp per x-line (j, k), lanes over the line's points (coalesced 16-byte
-// loads of the pairs): per point a = |psi|^2, x_i^2 a, V_x(i) a, a^2 and the
+// A thread owns one x and walks a chunk of kObsLines consecutive y-lines of
+// one plane (blocks over x segments, line chunks and planes; coalesced
+// 16-byte loads of the pairs): each point is loaded once as the thread's own
+// value and carried to the next line as that line's y-neighbour; the
+// x-neighbour comes from the next lane (lane 31 loads it), the z-neighbour
+// from the next plane, which that plane's blocks, resident at the same time,
+// find in L2.  Per point: a = |psi|^2, a^2, y_j^2 a, V_y(j) a and the
 // neighbour terms R = Re(psi_next conj(psi)) along x, y, z (zero beyond the
-// last stored point), each a float-float product summed per lane in
-// float-float (TwoSum + Fast2Sum after every addition), then across the warp
-// the same way.  Lane 0 turns the line's 7 sums into the 9-wide FP64 row of
-// the FP64 observables (the y, z factors are constant on the line; the
-// finish forms K = 2 S0 - 2 R), so the rows and the fixed-order finish are
-// shared with the other forms.
+// last stored point), each a float-float product summed per thread in
+// float-float (TwoSum + Fast2Sum after every addition); the factors constant
+// for the thread (x^2, V_x) or the block (z^2, V_z) multiply its sum of a
+// once.  Warp sums combine the same way, the block's in FP64, and each
+// block writes one 9-wide FP64 row of the FP64 observables (the finish forms
+// K = 2 S0 - 2 R), so the rows and the fixed-order finish are shared with
+// the other forms.
 __device__ __forceinline__ float2 lane_sum(C z)
 {
     const float2 s = s_two_sum(z.hi.x, z.hi.y);
@@ -482,58 +576,88 @@ __device__ __forceinline__ float2 lane_sum(C z)
 
 __global__ void __launch_bounds__(256)
 k_observables_ff(const float4 *__restrict__ psi, ObsArgs a, const float2 *__restrict__ x2ff,
-                 const float2 *__restrict__ vxff, double *__restrict__ partials)
+                 const float2 *__restrict__ vxff, double *__restrict__ rows)
 {
-    const int lane = threadIdx.x & 31;
-    const long long line = (long long)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    __shared__ float2 yt[2][kObsLines];
+    __shared__ double red[8][8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    if (line >= (long long)ny * nz) return;       // whole warp
-    const int j = (int)(line % ny), k = (int)(line / ny);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j0 = blockIdx.y * kObsLines, j1 = min(j0 + kObsLines, ny);
+    const int k = blockIdx.z;
+    if (threadIdx.x < kObsLines && j0 + (int)threadIdx.x < ny) {
+        yt[0][threadIdx.x] = split(a.y2[j0 + threadIdx.x]);
+        yt[1][threadIdx.x] = split(a.vy[j0 + threadIdx.x]);
+    }
+    __syncthreads();
+    const bool in = i < nx, has_z = nz > 1 && k + 1 < nz;
     const long long plane = (long long)nx * ny;
-    const float4 *row = psi + line * nx;
-    const bool has_y = j + 1 < ny, has_z = nz > 1 && k + 1 < nz;
+    const float4 *pk = psi + k * plane;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     auto cv = [](float4 v) { return C{f2(v.x, v.y), f2(v.z, v.w)}; };
-    float2 acc[7];                                  // S0, Sx, SVx, S4, Rx, Ry, Rz
+    float2 acc[7];                          // S0, Sy, SVy, S4, Rx, Ry, Rz
 #pragma unroll
     for (int q = 0; q < 7; ++q) acc[q] = f2(0.f, 0.f);
     auto put = [&](int q, float2 t) { acc[q] = s_norm(s_add(acc[q], t)); };
-    for (int i = lane; i < nx; i += 32) {
-        const C v = cv(row[i]);
-        const C nb = cv(i + 1 < nx ? row[i + 1] : zero);
-        const C nyv = cv(has_y ? row[i + nx] : zero);
+    float4 v4 = in ? pk[(long long)j0 * nx + i] : zero;
+#pragma unroll 2
+    for (int j = j0; j < j1; ++j) {
+        const long long at = (long long)j * nx + i;
+        const float4 vn4 = (in && j + 1 < ny) ? pk[at + nx] : zero;      // y-neighbour
+        const float4 vz4 = (in && has_z) ? pk[at + plane] : zero;        // z-neighbour
+        float4 nb4;                                                      // x-neighbour
+        nb4.x = __shfl_down_sync(0xffffffffu, v4.x, 1);
+        nb4.y = __shfl_down_sync(0xffffffffu, v4.y, 1);
+        nb4.z = __shfl_down_sync(0xffffffffu, v4.z, 1);
+        nb4.w = __shfl_down_sync(0xffffffffu, v4.w, 1);
+        if (lane == 31) nb4 = (i + 1 < nx) ? pk[at + 1] : zero;
+        const C v = cv(v4);
         const float2 am = abs2(v);
         put(0, am);
-        put(1, s_mul(x2ff[i], am));
-        put(2, s_mul(vxff[i], am));
+        put(1, s_mul(yt[0][j - j0], am));
+        put(2, s_mul(yt[1][j - j0], am));
         put(3, s_mul(am, am));
-        put(4, lane_sum(lmul(nb, v.hi, v.lo)));
-        put(5, lane_sum(lmul(nyv, v.hi, v.lo)));
-        if (nz > 1) {
-            const C nzv = cv(has_z ? row[i + plane] : zero);
-            put(6, lane_sum(lmul(nzv, v.hi, v.lo)));
-        }
+        put(4, lane_sum(lmul(cv(nb4), v.hi, v.lo)));
+        put(5, lane_sum(lmul(cv(vn4), v.hi, v.lo)));
+        if (nz > 1) put(6, lane_sum(lmul(cv(vz4), v.hi, v.lo)));
+        v4 = vn4;
     }
+    // S0, Sx, Sy, SVx + SVy, S4, Rx, Ry, Rz
+    const float2 x2 = in ? x2ff[i] : f2(0.f, 0.f), vx = in ? vxff[i] : f2(0.f, 0.f);
+    float2 t8[8] = {acc[0], s_mul(x2, acc[0]), acc[1], s_norm(s_add(s_mul(vx, acc[0]), acc[2])),
+                    acc[3], acc[4], acc[5], acc[6]};
 #pragma unroll
-    for (int q = 0; q < 7; ++q)
+    for (int q = 0; q < 8; ++q)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float2 t = f2(__shfl_down_sync(0xffffffffu, acc[q].x, o),
-                                __shfl_down_sync(0xffffffffu, acc[q].y, o));
-            acc[q] = s_norm(s_add(acc[q], t));
+            const float2 t = f2(__shfl_down_sync(0xffffffffu, t8[q].x, o),
+                                __shfl_down_sync(0xffffffffu, t8[q].y, o));
+            t8[q] = s_norm(s_add(t8[q], t));
         }
-    if (lane == 0) {
-        const double sc = *a.scale, s2 = sc * sc, r0 = join(acc[0]);
-        double *out = partials + line * kObsWidth;
-        out[0] = s2 * r0;
-        out[1] = s2 * join(acc[1]);
-        out[2] = s2 * a.y2[j] * r0;
-        out[3] = s2 * a.z2[k] * r0;
-        out[4] = s2 * (join(acc[2]) + (a.vy[j] + a.vz[k]) * r0);
-        out[5] = s2 * s2 * join(acc[3]);
-        out[6] = s2 * join(acc[4]);
-        out[7] = s2 * join(acc[5]);
-        out[8] = s2 * join(acc[6]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) red[wib][q] = join(t8[q]);
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double t = 0.0;
+        for (int w = 0; w < nwarps; ++w) t += red[w][threadIdx.x];
+        red[0][threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double sc = *a.scale, s2 = sc * sc;
+        const double *t = red[0];
+        double *out = rows + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x * kObsWidth +
+                      (long long)blockIdx.x * kObsWidth;
+        out[0] = s2 * t[0];
+        out[1] = s2 * t[1];
+        out[2] = s2 * t[2];
+        out[3] = s2 * a.z2[k] * t[0];
+        out[4] = s2 * (t[3] + a.vz[k] * t[0]);
+        out[5] = s2 * s2 * t[4];
+        out[6] = s2 * t[5];
+        out[7] = s2 * t[6];
+        out[8] = s2 * t[7];
     }
 }
 
@@ -647,12 +771,18 @@ cudaError_t launch_sweep_ff(int shape, int mode, int axis, const CUtensorMap &ma
     const int tiles = (g.lines_a + 32 * sh.K - 1) / (32 * sh.K);
     const bool has_nl = nl != nullptr, norm = norm_out != nullptr;
     const int lb = g.lines_b;
+#define GP_FF_SHAPE(I) \
+    launch_shape<kShapes[I].K, kShapes[I].S, kShapes[I].TM>(mode, axis, has_nl, norm, map, args, tiles, lb, st)
     switch (shape) {
-    case 1: return launch_shape<kShapes[1].K, kShapes[1].S>(mode, axis, has_nl, norm, map, args, tiles, lb, st);
-    case 2: return launch_shape<kShapes[2].K, kShapes[2].S>(mode, axis, has_nl, norm, map, args, tiles, lb, st);
-    case 3: return launch_shape<kShapes[3].K, kShapes[3].S>(mode, axis, has_nl, norm, map, args, tiles, lb, st);
-    default: return launch_shape<kShapes[0].K, kShapes[0].S>(mode, axis, has_nl, norm, map, args, tiles, lb, st);
+    case 1: return GP_FF_SHAPE(1);
+    case 2: return GP_FF_SHAPE(2);
+    case 3: return GP_FF_SHAPE(3);
+    case 4: return GP_FF_SHAPE(4);
+    case 5: return GP_FF_SHAPE(5);
+    case 6: return GP_FF_SHAPE(6);
+    default: return GP_FF_SHAPE(0);
     }
+#undef GP_FF_SHAPE
 }
 
 cudaError_t launch_ff_from_c128(void *dst, const void *src, long long count, const double *scale,
@@ -672,12 +802,14 @@ cudaError_t launch_ff_from_c128(void *dst, const void *src, long long count, con
 cudaError_t launch_observables_ff(const void *psi, const ObsArgs &a, const float2 *x2ff,
                                   const float2 *vxff, double *scratch, double *sums, cudaStream_t st)
 {
-    const long long lines = (long long)a.ny * a.nz;
-    const long long blocks = (lines * 32 + 255) / 256;
-    k_observables_ff<<<(unsigned)blocks, 256, 0, st>>>((const float4 *)psi, a, x2ff, vxff, scratch);
+    dim3 grid;
+    int threads = 0;
+    obs_walk_geometry(a.nx, a.ny, a.nz, grid, threads);
+    k_observables_ff<<<grid, threads, 0, st>>>((const float4 *)psi, a, x2ff, vxff, scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_rows_finish(scratch, lines, scratch + lines * kObsWidth, sums, st);
+    const long long nrows = (long long)grid.x * grid.y * grid.z;
+    return launch_rows_finish(scratch, nrows, scratch + nrows * kObsWidth, sums, st);
 }
 
 cudaError_t launch_ff_to_c128(void *dst, const void *src, long long count, const double *scale,

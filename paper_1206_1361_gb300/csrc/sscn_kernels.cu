@@ -447,50 +447,87 @@ __global__ void k_add_step(long long *step) { *step += 1; }
 constexpr int kObsThreads = 256;
 constexpr int kObsChunk = 1024;          // lines per first-stage finish block
 
-__global__ void __launch_bounds__(kObsThreads)
-k_observables_c64(const float2 *__restrict__ psi, ObsArgs a, double *__restrict__ partials)
+// A thread owns one x and walks a chunk of kObsLines consecutive y-lines of
+// one plane (blocks over x segments, line chunks and planes): each point is
+// loaded once as the thread's own value and carried to the next line as that
+// line's y-neighbour; the x-neighbour comes from the next lane (lane 31 loads
+// it), the z-neighbour from the next plane, which the blocks of that plane
+// (resident at the same time) find in L2.  The factors constant for the
+// thread (x^2, V_x) or the block (z^2, V_z) multiply its partial of |psi|^2
+// once; those of a line (y^2, V_y) are staged in shared memory per block.
+// Each block writes one row of 9 sums.
+__global__ void __launch_bounds__(256)
+k_observables_c64(const float2 *__restrict__ psi, ObsArgs a, double *__restrict__ rows)
 {
-    const int lane = threadIdx.x & 31;
-    const long long line = (long long)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    __shared__ float yt[2][kObsLines];
+    __shared__ double red[8][9];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    if (line >= (long long)ny * nz) return;       // whole warp
-    const int j = (int)(line % ny), k = (int)(line / ny);
-    const long long plane = (long long)nx * ny;
-    const float2 *row = psi + line * nx;
-    const bool has_y = j + 1 < ny, has_z = k + 1 < nz;
-    const float2 zero = make_float2(0.f, 0.f);
-    Acc<float> acc[7];                            // S0, Sx, SVx, S4, Kx, Ky, Kz
-    for (int i = lane; i < nx; i += 32) {
-        const float2 v = row[i];
-        const float am = fmaf(v.x, v.x, v.y * v.y);
-        acc[0].add(am);
-        acc[1].add_prod(a.x2f[i], am);
-        acc[2].add_prod(a.vxf[i], am);
-        acc[3].add_prod(am, am);
-        const float2 nb = (i + 1 < nx) ? row[i + 1] : zero;
-        acc[4].add_sq2(nb.x - v.x, nb.y - v.y);
-        const float2 ny_ = has_y ? row[i + nx] : zero;
-        acc[5].add_sq2(ny_.x - v.x, ny_.y - v.y);
-        if (nz > 1) {
-            const float2 nz_ = has_z ? row[i + plane] : zero;
-            acc[6].add_sq2(nz_.x - v.x, nz_.y - v.y);
-        }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j0 = blockIdx.y * kObsLines, j1 = min(j0 + kObsLines, ny);
+    const int k = blockIdx.z;
+    if (threadIdx.x < kObsLines && j0 + (int)threadIdx.x < ny) {
+        yt[0][threadIdx.x] = (float)a.y2[j0 + threadIdx.x];
+        yt[1][threadIdx.x] = (float)a.vy[j0 + threadIdx.x];
     }
-    double r[7];
+    __syncthreads();
+    const bool in = i < nx, has_z = k + 1 < nz;
+    const long long plane = (long long)nx * ny;
+    const float2 *pk = psi + k * plane;
+    const float2 zero = make_float2(0.f, 0.f);
+    Acc<float> s0, sy, svy, s4, kx, ky, kz;
+    float2 v = in ? pk[(long long)j0 * nx + i] : zero;
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+        const long long at = (long long)j * nx + i;
+        const float2 vn = (in && j + 1 < ny) ? pk[at + nx] : zero;      // y-neighbour
+        const float2 vz = (in && has_z) ? pk[at + plane] : zero;         // z-neighbour
+        float2 nb;                                                       // x-neighbour
+        nb.x = __shfl_down_sync(0xffffffffu, v.x, 1);
+        nb.y = __shfl_down_sync(0xffffffffu, v.y, 1);
+        if (lane == 31) nb = (i + 1 < nx) ? pk[at + 1] : zero;
+        const float am = fmaf(v.x, v.x, v.y * v.y);
+        s0.add(am);
+        sy.add(yt[0][j - j0] * am);
+        svy.add(yt[1][j - j0] * am);
+        s4.add(am * am);
+        kx.add_sq2(nb.x - v.x, nb.y - v.y);
+        ky.add_sq2(vn.x - v.x, vn.y - v.y);
+        if (nz > 1) kz.add_sq2(vz.x - v.x, vz.y - v.y);
+        v = vn;
+    }
+    const float p0 = s0.s - s0.c;
+    const float x2 = in ? a.x2f[i] : 0.f, vx = in ? a.vxf[i] : 0.f;
+    // S0, Sx, Sy, SVx + SVy, S4, Kx, Ky, Kz
+    const float ps[8][2] = {{s0.s, s0.c}, {x2 * p0, 0.f}, {sy.s, sy.c}, {vx * p0 + (svy.s - svy.c), 0.f},
+                            {s4.s, s4.c}, {kx.s, kx.c}, {ky.s, ky.c}, {kz.s, kz.c}};
+    double r[8];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) r[q] = warp_sum_comp(acc[q].s, acc[q].c);
-    if (lane == 0) {
-        const double sc = *a.scale, s2 = sc * sc, r0 = r[0];
-        double *out = partials + line * kObsWidth;
-        out[0] = s2 * r0;
-        out[1] = s2 * r[1];
-        out[2] = s2 * a.y2[j] * r0;
-        out[3] = s2 * a.z2[k] * r0;
-        out[4] = s2 * (r[2] + (a.vy[j] + a.vz[k]) * r0);
-        out[5] = s2 * s2 * r[3];
-        out[6] = s2 * r[4];
-        out[7] = s2 * r[5];
-        out[8] = s2 * r[6];
+    for (int q = 0; q < 8; ++q) r[q] = warp_sum_comp(ps[q][0], ps[q][1]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) red[wib][q] = r[q];
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double t = 0.0;
+        for (int w = 0; w < nwarps; ++w) t += red[w][threadIdx.x];
+        red[0][threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double sc = *a.scale, s2 = sc * sc;
+        const double *t = red[0];
+        double *out = rows + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x * kObsWidth +
+                      (long long)blockIdx.x * kObsWidth;
+        out[0] = s2 * t[0];
+        out[1] = s2 * t[1];
+        out[2] = s2 * t[2];
+        out[3] = s2 * a.z2[k] * t[0];
+        out[4] = s2 * (t[3] + a.vz[k] * t[0]);
+        out[5] = s2 * s2 * t[4];
+        out[6] = s2 * t[5];
+        out[7] = s2 * t[6];
+        out[8] = s2 * t[7];
     }
 }
 
@@ -706,11 +743,24 @@ cudaError_t launch_add_step(long long *step, cudaStream_t st)
     return cudaGetLastError();
 }
 
+void obs_walk_geometry(int nx, int ny, int nz, dim3 &grid, int &threads)
+{
+    threads = 32 * ((nx + 31) / 32);
+    if (threads > 256) threads = 256;
+    grid = dim3((unsigned)((nx + threads - 1) / threads), (unsigned)((ny + kObsLines - 1) / kObsLines),
+                (unsigned)nz);
+}
+
 long long obs_scratch_doubles(const ObsArgs &a)
 {
-    const long long lines = (long long)a.ny * a.nz;
-    const long long chunks = (lines + kObsChunk - 1) / kObsChunk;
-    return (lines + chunks) * kObsWidth;
+    dim3 grid;
+    int threads = 0;
+    obs_walk_geometry(a.nx, a.ny, a.nz, grid, threads);
+    long long rows = (long long)a.ny * a.nz;       // a row per line (FP64)
+    const long long walk = (long long)grid.x * grid.y * grid.z;
+    if (walk > rows) rows = walk;
+    const long long chunks = (rows + kObsChunk - 1) / kObsChunk;
+    return (rows + chunks) * kObsWidth;
 }
 
 cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
@@ -722,8 +772,14 @@ cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
         const long long blocks = (lines + kObsThreads - 1) / kObsThreads;
         k_observables<double><<<(unsigned)blocks, kObsThreads, 0, st>>>((const double2 *)psi, a, rows);
     } else {
-        const long long blocks = (lines * 32 + kObsThreads - 1) / kObsThreads;
-        k_observables_c64<<<(unsigned)blocks, kObsThreads, 0, st>>>((const float2 *)psi, a, rows);
+        dim3 grid;
+        int threads = 0;
+        obs_walk_geometry(a.nx, a.ny, a.nz, grid, threads);
+        k_observables_c64<<<grid, threads, 0, st>>>((const float2 *)psi, a, rows);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const long long nrows = (long long)grid.x * grid.y * grid.z;
+        return launch_rows_finish(rows, nrows, rows + nrows * kObsWidth, sums, st);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

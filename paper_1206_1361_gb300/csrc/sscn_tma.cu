@@ -85,6 +85,9 @@ struct TmaArgs {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per chunk wait
 constexpr int kErrTimeout = 2;
+// Columns of tensor memory a CTA of the TMEM-ring shapes allocates: d' of
+// two chunks, 32 FP32 words per chunk (16 complex64 points).
+constexpr int kTmemCols = 64;
 
 template <typename T, int L, int C, int S, int AXIS>
 struct TileGeom {
@@ -112,11 +115,38 @@ struct TileGeom {
 // NL: calcnu on each point as it arrives (x sweep); NLOUT: calcnu on each
 // result before it is stored (the symmetric splitting's second half step in
 // the last real-time sweep).
-template <typename T, int MODE, int AXIS, bool NL, bool NORM, int K, int C, int S,
+// TM (complex64): the d' ring lives in tensor memory, each consumer thread's
+// line in its TMEM lane, which leaves shared memory to the stages and admits
+// more resident CTAs; every lane of a consumer warp then runs the same
+// instruction stream (the tcgen05 accesses are warp-wide), lanes past the end
+// of a ragged tile computing on the zeros TMA filled in, whose rows the TMA
+// store clips.
+template <typename T, int K, int C, int S, bool TM>
+constexpr size_t tma_smem_bytes()
+{
+    constexpr size_t L = 32 * K;
+    return 1024 + (size_t)S * L * C * sizeof(typename CT2<T>::c) +
+           (TM ? 0 : 2 * (size_t)C * L * sizeof(typename CT2<T>::c)) + 2 * S * sizeof(uint64_t) +
+           32 * sizeof(double) + 16;
+}
+
+// Resident CTAs per SM the TMEM shapes are built for: as many as shared
+// memory admits, at most 512 / kTmemCols.
+template <typename T, int K, int C, int S, bool TM>
+constexpr int tma_min_blocks()
+{
+    if (!TM) return 1;
+    constexpr int by_smem = (int)((227 * 1024) / tma_smem_bytes<T, K, C, S, TM>());
+    constexpr int by_tmem = 512 / kTmemCols;
+    return by_smem < by_tmem ? by_smem : by_tmem;
+}
+
+template <typename T, int MODE, int AXIS, bool NL, bool NORM, int K, int C, int S, bool TM,
           bool NLOUT = false>
-__global__ void __launch_bounds__(32 * (K + 1))
+__global__ void __launch_bounds__(32 * (K + 1), (tma_min_blocks<T, K, C, S, TM>()))
 k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
 {
+    static_assert(!TM || (sizeof(T) == 4 && C == 16), "the TMEM ring holds complex64 chunks of 16");
     using Cv = typename CT2<T>::c;
     constexpr int L = 32 * K;
     using G = TileGeom<T, L, C, S, AXIS>;
@@ -126,9 +156,10 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *stages = smem;
     Cv *ring = reinterpret_cast<Cv *>(stages + S * G::kStageBytes);     // [2][C][L]
-    uint64_t *full = reinterpret_cast<uint64_t *>(ring + 2 * C * L);
+    uint64_t *full = reinterpret_cast<uint64_t *>(ring + (TM ? 0 : 2 * C * L));
     uint64_t *ready = full + S;
     double *red = reinterpret_cast<double *>(ready + S);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(red + 32);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = warp == K;
@@ -136,6 +167,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
     const int tile0 = blockIdx.x * L;
     const int a = tile0 + l;
     const bool active = !producer && a < args.lines_a;
+    const bool run = TM ? !producer : active;       // computes (see TM above)
     const int m = args.n - 1;
     const int Q = (args.n + C - 1) / C;             // chunks covering stored points 0 .. m
     using F = typename Coef<T>::t;
@@ -169,6 +201,10 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
     auto stage_ptr = [&](int q) { return stages + (q % S) * G::kStageBytes; };
     auto at = [&](int q, int c) -> Cv * { return reinterpret_cast<Cv *>(stage_ptr(q) + G::off(l, c)); };
 
+    if (TM && warp == 0) {
+        tmem_alloc(tslot, kTmemCols);
+        tmem_relinquish();
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -176,7 +212,11 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
         }
         fence_mbar_init();
     }
+    if (TM) tmem_fence_before();
     __syncthreads();
+    if (TM) tmem_fence_after();
+    // this warp's TMEM lanes (consumer warps 0 .. K-1 reach lanes 32 (w % 4) ..)
+    const uint32_t tbase = TM ? *tslot + ((uint32_t)(32 * (warp & 3)) << 16) : 0u;
 
     bool failed = false;
     Acc<T> nacc;
@@ -216,24 +256,41 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
         }
     } else {
         Calcnu<T, MODE> nl{};
-        if ((NL || NLOUT) && active) {
+        if ((NL || NLOUT) && run) {
+            // lanes past a ragged tile's end take the last line's factors
             const F *py = static_cast<const F *>(args.py), *pz = static_cast<const F *>(args.pz);
-            nl.setup(static_cast<const F *>(args.px), py, pz, args.tx, args.ty, args.tz, a,
-                     blockIdx.y, args.g.value(), args.scale);
+            nl.setup(static_cast<const F *>(args.px), py, pz, args.tx, args.ty, args.tz,
+                     active ? a : args.lines_a - 1, blockIdx.y, args.g.value(), args.scale);
         }
         // complex64: increment form with the forward pass one point behind
         // the newest point (it needs psi_{i+1}); FP64: u = 2 v - psi
         auto slot = [&](int i) -> Cv & { return ring[((i / C) & 1) * C * L + (i % C) * L + l]; };
+        // TMEM column of point i: chunk parity, then 2 words per point
+        auto tcol = [&](int i) -> uint32_t { return (uint32_t)((((i / C) & 1) * C + i % C) * 2); };
+        auto put = [&](int i, Cv d) {
+            if constexpr (TM) tmem_st2(tbase + tcol(i), d.x, d.y);
+            else slot(i) = d;
+        };
+        auto get = [&](int i) -> Cv {
+            if constexpr (TM) {
+                const float2 v = tmem_ld2(tbase + tcol(i));
+                return mk2<T>(v.x, v.y);
+            } else {
+                return slot(i);
+            }
+        };
         auto output = [&](Cv v, Cv *tile_slot, int i) {
             Cv u = INC ? LineOps<T, MODE>::out_inc(v, *tile_slot) : LineOps<T, MODE>::out(v, *tile_slot);
             if (NLOUT) u = nl.apply(u, i);
             *tile_slot = u;
-            if (NORM) nacc.add(fma(u.x, u.x, u.y * u.y));
+            if (NORM && active) nacc.add(fma(u.x, u.x, u.y * u.y));
         };
         const Cv zero = mk2<T>((T)0, (T)0);
         Cv d = zero, pa = zero, pb = zero;          // INC: psi~_{i-1}, psi~_i
         for (int q = 0; q < Q; ++q) {
-            if (!mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs)) {
+            bool ok = mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs);
+            if (TM) ok = __all_sync(0xffffffffu, ok);    // the warp leaves together
+            if (!ok) {
                 failed = true;
                 break;
             }
@@ -241,7 +298,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
             // Interior chunks -- all points unknowns, tables converged to their
             // constants, neither the first chunks nor the last -- take a path
             // with no guards, no table loads and compile-time offsets.
-            const bool fast = active && q >= 2 && !last && (q - 1) * C - 1 >= conv &&
+            const bool fast = run && q >= 2 && !last && (q - 1) * C - 1 >= conv &&
                               (q + 1) * C - 1 <= m;
             if (fast) {
                 unsigned char *sq = stage_ptr(q), *sp = stage_ptr(q - 1);
@@ -250,7 +307,8 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                 auto fwd_at = [&](int c, Cv pj) {
                     if (INC) {
                         d = cn.fwd(cn.lap(pa, pb, pj), d, minf);
-                        if (c == 0) rp[(C - 1) * L] = d;
+                        if constexpr (TM) put(q * C + c - 1, d);
+                        else if (c == 0) rp[(C - 1) * L] = d;
                         else rq[(c - 1) * L] = d;
                         pa = pb;
                         pb = pj;
@@ -263,7 +321,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                 auto final_at = [&](Cv v, Cv p, int c) {
                     Cv u = INC ? LineOps<T, MODE>::out_inc(v, p) : LineOps<T, MODE>::out(v, p);
                     if (NLOUT) u = nl.apply(u, (q - 1) * C + c);
-                    if (NORM) nacc.add(fma(u.x, u.x, u.y * u.y));
+                    if (NORM && active) nacc.add(fma(u.x, u.x, u.y * u.y));
                     return u;
                 };
                 if constexpr (AXIS == 0 && sizeof(T) == 4) {
@@ -283,6 +341,31 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                         fwd_at(c, p0);
                         fwd_at(c + 1, p1);
                     }
+                    if constexpr (TM) {
+                        // window: the seed d'_{W-1} by its own load (a runtime
+                        // column), back through points W-2 .. 0 of chunk q,
+                        // then chunk q - 1 loaded whole
+                        Cv v = get(q * C + win - 1);
+                        {
+                            float r[32];
+                            tmem_ld32(tbase + tcol(q * C), r);
+#pragma unroll
+                            for (int c = C - 2; c >= 0; --c)
+                                if (c <= win - 2) v = cn.back(mk2<T>(r[2 * c], r[2 * c + 1]), cinf, v);
+                        }
+                        float r[32];
+                        tmem_ld32(tbase + tcol((q - 1) * C), r);
+#pragma unroll
+                        for (int c = C - 1; c >= 1; c -= 2) {
+                            float4 *t2 = reinterpret_cast<float4 *>(sp + G::off(l, c - 1));
+                            const float4 w = *t2;
+                            v = cn.back(mk2<T>(r[2 * c], r[2 * c + 1]), cinf, v);
+                            const Cv u1 = final_at(v, mk2<T>(w.z, w.w), c);
+                            v = cn.back(mk2<T>(r[2 * c - 2], r[2 * c - 1]), cinf, v);
+                            const Cv u0 = final_at(v, mk2<T>(w.x, w.y), c - 1);
+                            *t2 = make_float4(u0.x, u0.y, u1.x, u1.y);
+                        }
+                    } else {
                     Cv v = rq[(win - 1) * L];
                     for (int c = win - 2; c >= 0; --c) v = cn.back(rq[c * L], cinf, v);
 #pragma unroll
@@ -295,6 +378,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                         const Cv u0 = final_at(v, mk2<T>(w.x, w.y), c - 1);
                         *t2 = make_float4(u0.x, u0.y, u1.x, u1.y);
                     }
+                    }
                 } else {
 #pragma unroll
                     for (int c = 0; c < C; ++c) {
@@ -306,6 +390,24 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                         }
                         fwd_at(c, pj);
                     }
+                    if constexpr (TM) {
+                        Cv v = get(q * C + win - 1);
+                        {
+                            float r[32];
+                            tmem_ld32(tbase + tcol(q * C), r);
+#pragma unroll
+                            for (int c = C - 2; c >= 0; --c)
+                                if (c <= win - 2) v = cn.back(mk2<T>(r[2 * c], r[2 * c + 1]), cinf, v);
+                        }
+                        float r[32];
+                        tmem_ld32(tbase + tcol((q - 1) * C), r);
+#pragma unroll
+                        for (int c = C - 1; c >= 0; --c) {
+                            Cv *tc = reinterpret_cast<Cv *>(sp + G::off(l, c));
+                            v = cn.back(mk2<T>(r[2 * c], r[2 * c + 1]), cinf, v);
+                            *tc = final_at(v, *tc, c);
+                        }
+                    } else {
                     Cv v = rq[(win - 1) * L];
                     for (int c = win - 2; c >= 0; --c) v = cn.back(rq[c * L], cinf, v);
 #pragma unroll
@@ -314,10 +416,11 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                         v = cn.back(rp[c * L], cinf, v);
                         *tc = final_at(v, *tc, c);
                     }
+                    }
                 }
             } else {
                 // forward elimination through chunk q
-                if (active) {
+                if (run) {
 #pragma unroll 4
                     for (int c = 0; c < C; ++c) {
                         const int j = q * C + c;
@@ -333,7 +436,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                             const int i = j - 1;
                             if (i >= 1 && i <= m) {
                                 d = cn.fwd(cn.lap(pa, pb, pj), d, mult(i - 1));
-                                slot(i) = d;
+                                put(i, d);
                             }
                             pa = pb;
                             pb = pj;
@@ -344,26 +447,26 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                                 *at(q, c) = p;
                             }
                             d = cn.fwd(p, d, mult(j - 1));
-                            slot(j) = d;
+                            put(j, d);
                         }
                     }
                     if (INC && last && Q * C - 1 == m) {
                         // point m: its right neighbour is the virtual zero node
                         d = cn.fwd(cn.lap(pa, pb, zero), d, mult(m - 1));
-                        slot(m) = d;
+                        put(m, d);
                     }
                 }
-                if (active) {
+                if (run) {
                     if (!last && q >= 1) {
                         // windowed: seed W points into chunk q, output chunk q - 1
-                        Cv v = slot(q * C + win - 1);
+                        Cv v = get(q * C + win - 1);
                         for (int c = win - 2; c >= 0; --c)
-                            v = cn.back(slot(q * C + c), cp(q * C + c - 1), v);
+                            v = cn.back(get(q * C + c), cp(q * C + c - 1), v);
 #pragma unroll 4
                         for (int c = C - 1; c >= 0; --c) {
                             const int i = (q - 1) * C + c;
                             if (i < 1) break;
-                            v = cn.back(slot(i), cp(i - 1), v);
+                            v = cn.back(get(i), cp(i - 1), v);
                             output(v, at(q - 1, c), i);
                         }
                     } else if (last) {
@@ -371,7 +474,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
                         Cv v = d;
                         const int lo = q >= 1 ? (q - 1) * C : 0;
                         for (int i = m; i >= lo && i >= 1; --i) {
-                            if (i < m) v = cn.back(slot(i), cp(i - 1), v);
+                            if (i < m) v = cn.back(get(i), cp(i - 1), v);
                             output(v, at(i / C, i % C), i);
                         }
                     }
@@ -388,6 +491,16 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
         }
     }
     if (failed) atomicOr(args.err, kErrTimeout);
+    if (TM) {
+        // every warp is done with tensor memory before it is released
+        if (!producer) tmem_wait_st();
+        tmem_fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            tmem_fence_after();
+            tmem_dealloc(*tslot, kTmemCols);
+        }
+    }
     if (NORM) {
         // block sum of the per-line norm contributions, fixed order
         double v = nacc.get();
@@ -405,41 +518,44 @@ k_sweep_tma(const __grid_constant__ CUtensorMap map, const TmaArgs args)
     }
 }
 
-template <typename T, int K, int C, int S>
-constexpr size_t tma_smem_bytes()
-{
-    constexpr size_t L = 32 * K;
-    return 1024 + (size_t)S * L * C * sizeof(typename CT2<T>::c) +
-           2 * (size_t)C * L * sizeof(typename CT2<T>::c) + 2 * S * sizeof(uint64_t) +
-           32 * sizeof(double);
-}
-
-template <typename T, int MODE, int AXIS, bool NL, bool NORM, int K, int C, int S,
+template <typename T, int MODE, int AXIS, bool NL, bool NORM, int K, int C, int S, bool TM,
           bool NLOUT = false>
 cudaError_t launch_tma_inst(const CUtensorMap &map, const TmaArgs &args, int tiles, int lines_b,
                             cudaStream_t st)
 {
-    auto kern = k_sweep_tma<T, MODE, AXIS, NL, NORM, K, C, S, NLOUT>;
-    constexpr size_t smem = tma_smem_bytes<T, K, C, S>();
+    auto kern = k_sweep_tma<T, MODE, AXIS, NL, NORM, K, C, S, TM, NLOUT>;
     constexpr int threads = 32 * (K + 1);
-    static bool configured[64] = {};          // per device ordinal
+    static size_t smem_of[64] = {};           // per device ordinal, 0: not configured
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!configured[dev]) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    if (!smem_of[dev]) {
+        size_t smem = tma_smem_bytes<T, K, C, S, TM>();
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        configured[dev] = true;
+        // TM: no more resident CTAs than one SM's tensor memory holds (an
+        // allocation beyond it would wait for another CTA to finish), so
+        // pad the shared memory until the occupancy says so
+        for (;;) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            if (!TM) break;
+            int blocks = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, threads, smem);
+            if (e != cudaSuccess) return e;
+            if (blocks * kTmemCols <= 512) break;
+            smem += 1024;
+            if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+        }
+        smem_of[dev] = smem;
     }
-    kern<<<dim3(tiles, lines_b), threads, smem, st>>>(map, args);
+    kern<<<dim3(tiles, lines_b), threads, smem_of[dev], st>>>(map, args);
     return cudaGetLastError();
 }
 
-template <typename T, int AXIS, int K, int C, int S>
+template <typename T, int AXIS, int K, int C, int S, bool TM>
 cudaError_t launch_tma_axis(int mode, bool nl, bool norm, bool nlout, const CUtensorMap &map,
                             const TmaArgs &args, int tiles, int lines_b, cudaStream_t st)
 {
@@ -448,14 +564,14 @@ cudaError_t launch_tma_axis(int mode, bool nl, bool norm, bool nlout, const CUte
         if constexpr (AXIS == 0) return cudaErrorInvalidValue;
         else {
             if (mode != 1 || norm || nl) return cudaErrorInvalidValue;
-            return launch_tma_inst<T, 1, AXIS, false, false, K, C, S, true>(map, args, tiles,
-                                                                           lines_b, st);
+            return launch_tma_inst<T, 1, AXIS, false, false, K, C, S, TM, true>(map, args, tiles,
+                                                                               lines_b, st);
         }
     }
     // calcnu is fused into the x sweep only
 #define GP_TMA(MODE, NLV, NORMV)                                                             \
-    return launch_tma_inst<T, MODE, AXIS, (NLV && AXIS == 0), NORMV, K, C, S>(map, args, tiles, \
-                                                                           lines_b, st)
+    return launch_tma_inst<T, MODE, AXIS, (NLV && AXIS == 0), NORMV, K, C, S, TM>(map, args,   \
+                                                                               tiles, lines_b, st)
     if (mode == 0) {
         if (nl) { if (norm) GP_TMA(0, true, true); GP_TMA(0, true, false); }
         if (norm) GP_TMA(0, false, true);
@@ -470,20 +586,24 @@ cudaError_t launch_tma_axis(int mode, bool nl, bool norm, bool nlout, const CUte
 // Tile shapes (consumer warps K, points per chunk C, stages S); a CTA owns
 // 32 K lines.  C is fixed by the 128-byte swizzled x rows (16 complex64 / 8
 // complex128 points); K and S trade CTAs per SM against chunks in flight.
-struct Shape { int K, C, S; };
+// TM: the d' ring in tensor memory (complex64 only).
+struct Shape { int K, C, S; bool TM; };
 // Index 0 is the default: the fastest measured at 512 x 512 x 256 complex64
-// (2 consumer warps, 3 stages: 5 CTAs per SM) and 256^3 complex128.
-constexpr Shape kShapes32[] = {{2, 16, 3}, {1, 16, 4}, {2, 16, 4}, {4, 16, 3}, {1, 16, 3}};
-constexpr Shape kShapes64[] = {{1, 8, 4}, {2, 8, 4}, {4, 8, 3}};
-constexpr int kNumShapes32 = 5, kNumShapes64 = 3;
+// (4 consumer warps, 3 stages, TMEM ring: 16 consumer warps per SM against
+// 10 with the ring in shared memory) and 256^3 complex128.
+constexpr Shape kShapes32[] = {{4, 16, 3, true},  {2, 16, 3, true},  {2, 16, 4, true},
+                               {2, 16, 3, false}, {1, 16, 4, false}, {2, 16, 4, false},
+                               {4, 16, 3, false}, {1, 16, 3, false}};
+constexpr Shape kShapes64[] = {{1, 8, 4, false}, {2, 8, 4, false}, {4, 8, 3, false}};
+constexpr int kNumShapes32 = 8, kNumShapes64 = 3;
 
-template <typename T, int K, int C, int S>
+template <typename T, int K, int C, int S, bool TM>
 cudaError_t launch_shape(int mode, int axis, bool nl, bool norm, bool nlout, const CUtensorMap &map,
                          const TmaArgs &args, int tiles, int lines_b, cudaStream_t st)
 {
-    if (axis == 0) return launch_tma_axis<T, 0, K, C, S>(mode, nl, norm, nlout, map, args, tiles, lines_b, st);
-    if (axis == 1) return launch_tma_axis<T, 1, K, C, S>(mode, nl, norm, nlout, map, args, tiles, lines_b, st);
-    return launch_tma_axis<T, 2, K, C, S>(mode, nl, norm, nlout, map, args, tiles, lines_b, st);
+    if (axis == 0) return launch_tma_axis<T, 0, K, C, S, TM>(mode, nl, norm, nlout, map, args, tiles, lines_b, st);
+    if (axis == 1) return launch_tma_axis<T, 1, K, C, S, TM>(mode, nl, norm, nlout, map, args, tiles, lines_b, st);
+    return launch_tma_axis<T, 2, K, C, S, TM>(mode, nl, norm, nlout, map, args, tiles, lines_b, st);
 }
 
 Shape shape_of(int prec, int shape)
@@ -576,8 +696,8 @@ cudaError_t launch_sweep_tma(int prec, int shape, int mode, int axis, const CUte
     const int lb = g.lines_b;
 #define GP_SHAPE(T, SH, I)                                                                   \
     if (shape == I)                                                                          \
-        return launch_shape<T, SH[I].K, SH[I].C, SH[I].S>(mode, axis, has_nl, norm, nlout, map, \
-                                                          args, tiles, lb, st)
+        return launch_shape<T, SH[I].K, SH[I].C, SH[I].S, SH[I].TM>(mode, axis, has_nl, norm,   \
+                                                                    nlout, map, args, tiles, lb, st)
     if (prec == kC128) {
         GP_SHAPE(double, kShapes64, 1);
         GP_SHAPE(double, kShapes64, 2);
@@ -588,6 +708,9 @@ cudaError_t launch_sweep_tma(int prec, int shape, int mode, int axis, const CUte
     GP_SHAPE(float, kShapes32, 2);
     GP_SHAPE(float, kShapes32, 3);
     GP_SHAPE(float, kShapes32, 4);
+    GP_SHAPE(float, kShapes32, 5);
+    GP_SHAPE(float, kShapes32, 6);
+    GP_SHAPE(float, kShapes32, 7);
     GP_SHAPE(float, kShapes32, 0);
 #undef GP_SHAPE
     return cudaErrorInvalidValue;

@@ -1,8 +1,9 @@
 // sscn_tma.cuh -- inline-PTX wrappers for the TMA-pipelined sweeps: mbarrier
 // set-up, arrival and bounded waits, 3-D tensor copies between global and
 // shared memory (cp.async.bulk.tensor), bulk-group commit / wait, and the
-// proxy fences between generic shared-memory writes and TMA stores.  Each
-// wrapper is one PTX instruction (or a bounded loop around one).
+// proxy fences between generic shared-memory writes and TMA stores, and
+// tensor-memory allocation, loads and stores.  Each wrapper is one PTX
+// instruction (or a bounded loop around one, or a load with its waits).
 #pragma once
 
 #include <cstdint>
@@ -98,6 +99,109 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// ---- tensor memory (TMEM) as per-line scratch --------------------------------
+// 128 lanes x 512 32-bit columns per SM.  A CTA allocates columns (a power
+// of two, 32 .. 512) across all 128 lanes; warp w reaches lanes
+// 32 (w % 4) .. 32 (w % 4) + 31, lane i of the warp holding row 32 (w % 4) + i.
+// Every tcgen05 instruction below is warp-wide (.sync.aligned): all 32 lanes
+// execute it together with the same address.  An address is
+// (lane << 16) | column.
+
+// One whole warp: allocate `cols` columns, base address -> *slot (shared).
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t cols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(cols)
+                 : "memory");
+}
+
+// The CTA allocates no more (lets other CTAs' allocations proceed).
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t base, uint32_t cols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(cols)
+                 : "memory");
+}
+
+// Order tcgen05 operations around a thread barrier (before / after it).
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Wait until this thread's earlier tensor-memory stores have completed.
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Columns addr, addr + 1 of this thread's lane <- (a, b).
+__device__ __forceinline__ void tmem_st2(uint32_t addr, float a, float b)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(addr),
+                 "r"(__float_as_uint(a)), "r"(__float_as_uint(b))
+                 : "memory");
+}
+
+// Columns addr, addr + 1 of this thread's lane, after this thread's earlier
+// stores have completed; returns once the values are in registers.
+__device__ __forceinline__ float2 tmem_ld2(uint32_t addr)
+{
+    uint32_t a, b;
+    asm volatile(
+        "tcgen05.wait::st.sync.aligned;\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(a), "=r"(b)
+        : "r"(addr)
+        : "memory");
+    return make_float2(__uint_as_float(a), __uint_as_float(b));
+}
+
+// Columns addr .. addr + 3 of this thread's lane <- (a, b, c, d).
+__device__ __forceinline__ void tmem_st4(uint32_t addr, float a, float b, float c, float d)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr),
+                 "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(__float_as_uint(c)),
+                 "r"(__float_as_uint(d))
+                 : "memory");
+}
+
+// Columns addr .. addr + 3 of this thread's lane, after this thread's
+// earlier stores have completed; returns once the values are in registers.
+__device__ __forceinline__ float4 tmem_ld4(uint32_t addr)
+{
+    uint32_t a, b, c, d;
+    asm volatile(
+        "tcgen05.wait::st.sync.aligned;\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+        : "r"(addr)
+        : "memory");
+    return make_float4(__uint_as_float(a), __uint_as_float(b), __uint_as_float(c), __uint_as_float(d));
+}
+
+// Columns addr .. addr + 31 of this thread's lane, likewise.
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.wait::st.sync.aligned;\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(addr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
 
 }  // namespace tma
 }  // namespace gp

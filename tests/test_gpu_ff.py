@@ -70,10 +70,10 @@ def test_ff_random_state_steps_match_oracle(shape, h, mode):
     assert rel_l2(got, want) <= 1e-12
 
 
-@pytest.mark.parametrize("shape_idx", range(4))
+@pytest.mark.parametrize("shape_idx", range(7))
 def test_ff_every_tile_shape_matches_oracle(shape_idx):
     require_gpu()
-    assert gp.gp_tile_shapes(gp.GP_CFF) == 4
+    assert gp.gp_tile_shapes(gp.GP_CFF) == 7
     shape, h, dt, g = (70, 45, 37), (0.15, 0.15, 0.15), 4e-4, 8.0
     psi0 = rand_state(shape, 5)
     got, _ = run_ff(shape, h, dt, W3, g, gp.GP_REAL, 5, psi0, shape_idx=shape_idx)

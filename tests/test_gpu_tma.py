@@ -103,16 +103,20 @@ def test_tma_complex64_1000_imaginary_steps_mu_within_1e6():
     assert abs(obs["energy"] - ref["energy"]) <= 1e-6 * ref["energy"]
 
 
+@pytest.mark.parametrize("mode", [gp.GP_REAL, gp.GP_IMAG])
 @pytest.mark.parametrize("precision,dtype,tol", [(gp.GP_C128, np.complex128, 1e-12),
                                                  (gp.GP_C64, np.complex64, 2e-6)])
-def test_every_tile_shape_matches_oracle(precision, dtype, tol):
+def test_every_tile_shape_matches_oracle(precision, dtype, tol, mode):
+    """Every tile shape, the tensor-memory ring shapes included, on ragged
+    tiles (66 and 130 lines against 32 K per CTA) in both modes (imaginary
+    time: the norm partials and the renormalisation too)."""
     require_gpu()
     shape, h, dt, g = (130, 66, 40), (0.1, 0.12, 0.15), 2.5e-4, 5.0
     psi0 = rand_state(shape, 41)
     want = psi0.copy()
-    oracle.step(oracle_params(shape, h, dt, W3, g, gp.GP_REAL), want, 5)
+    oracle.step(oracle_params(shape, h, dt, W3, g, mode), want, 5)
     for sh in range(gp.gp_tile_shapes(precision)):
-        with gp.Solver(shape, h, dt, *W3, g, gp.GP_REAL, precision) as s:
+        with gp.Solver(shape, h, dt, *W3, g, mode, precision) as s:
             gp.gp_set_option(s.ctx, gp.GP_OPT_TILE_SHAPE, sh)
             s.set_path(gp.GP_PATH_TMA)
             assert gp.gp_get_option(s.ctx, gp.GP_OPT_TILE_SHAPE) == sh
