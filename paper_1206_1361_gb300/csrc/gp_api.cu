@@ -1159,14 +1159,19 @@ int gp_load(gp_ctx *c, const void *psi, int64_t count, int on_device)
     }
     if (count != n) return fail(c, GP_EINVAL, "gp_load: count != nx*ny*nz");
     if (is_ff(c)) {
-        // complex128 in, split into float-float pairs
-        GP_CK(c, cudaMemcpyAsync(c->work, psi, (size_t)n * sizeof(double2),
-                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                 c->stream));
-        GP_CK(c, gp::launch_zero_boundary(GP_C128, c->work, c->grid.nx, c->grid.ny, c->grid.nz,
-                                          c->stream));
-        GP_CK(c, gp::launch_ff_from_c128(c->psi, c->work, n, nullptr, c->scale, c->stream));
-        GP_CK(c, cudaStreamSynchronize(c->stream));   // the caller's buffer
+        // complex128 in, split into float-float pairs with the Dirichlet
+        // nodes zeroed (a device buffer is read in place, a host one first
+        // crosses into the work buffer)
+        const void *src = psi;
+        if (!on_device) {
+            GP_CK(c, cudaMemcpyAsync(c->work, psi, (size_t)n * sizeof(double2), cudaMemcpyHostToDevice,
+                                     c->stream));
+            src = c->work;
+        }
+        GP_CK(c, gp::launch_ff_from_c128_grid(c->psi, src, c->grid.nx, c->grid.ny, c->grid.nz, c->stream));
+        const double one = 1.0;
+        GP_CK(c, cudaMemcpyAsync(c->scale, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        GP_CK(c, cudaStreamSynchronize(c->stream));   // `one` and the caller's buffer
         return GP_OK;
     }
     GP_CK(c, cudaMemcpyAsync(c->psi, psi, (size_t)n * elem_bytes(c->prec),

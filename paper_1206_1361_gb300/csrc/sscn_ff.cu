@@ -540,6 +540,30 @@ __global__ void k_ff_from_c128(float4 *__restrict__ dst, const double2 *__restri
 
 __global__ void k_ff_set_one(double *x) { *x = 1.0; }
 
+// complex128 psi of an nx * ny * nz grid into pairs, the Dirichlet nodes
+// (index 0 of each bounded axis) set to zero: blocks walk the x-lines, threads
+// the points of a line.
+__global__ void k_ff_from_c128_grid(float4 *__restrict__ dst, const double2 *__restrict__ src, int nx,
+                                    int ny, int nz)
+{
+    const long long lines = (long long)ny * nz;
+    for (long long line = blockIdx.x; line < lines; line += gridDim.x) {
+        const int j = (int)(line % ny), k = (int)(line / ny);
+        const bool edge = j == 0 || (nz > 1 && k == 0);
+        const double2 *row = src + line * nx;
+        float4 *out = dst + line * nx;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            if (edge || i == 0) {
+                out[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                const double2 v = row[i];
+                const float2 r = split(v.x), im = split(v.y);
+                out[i] = make_float4(r.x, im.x, r.y, im.y);
+            }
+        }
+    }
+}
+
 __global__ void k_ff_to_c128(double2 *__restrict__ dst, const float4 *__restrict__ src,
                              long long count, const double *scale)
 {
@@ -797,6 +821,15 @@ cudaError_t launch_ff_from_c128(void *dst, const void *src, long long count, con
         e = cudaGetLastError();
     }
     return e;
+}
+
+cudaError_t launch_ff_from_c128_grid(void *dst, const void *src, int nx, int ny, int nz,
+                                     cudaStream_t st)
+{
+    const long long lines = (long long)ny * nz;
+    const int blocks = (int)(lines < 152 * 16 ? lines : 152 * 16);
+    k_ff_from_c128_grid<<<blocks, 256, 0, st>>>((float4 *)dst, (const double2 *)src, nx, ny, nz);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_observables_ff(const void *psi, const ObsArgs &a, const float2 *x2ff,

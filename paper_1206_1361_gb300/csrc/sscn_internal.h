@@ -161,6 +161,10 @@ cudaError_t launch_sweep_ff(int shape, int mode, int axis, const CUtensorMap &ma
                             const Partials *norm_out, int *err, cudaStream_t st);
 // dst (float-float) <- split(scale * src) over count points (scale nullptr:
 // 1); with reset_scale, *reset_scale <- 1 afterwards.
+// complex128 psi (nx * ny * nz, device) into pairs with the Dirichlet nodes
+// zeroed; src may be the caller's buffer (it is only read).
+cudaError_t launch_ff_from_c128_grid(void *dst, const void *src, int nx, int ny, int nz,
+                                     cudaStream_t st);
 cudaError_t launch_ff_from_c128(void *dst, const void *src, long long count, const double *scale,
                                 double *reset_scale, cudaStream_t st);
 // Observables rows of a float-float psi (one per x-line: the FP64 row layout

@@ -153,6 +153,28 @@ def test_ff_store_load_roundtrip_and_device_view():
         assert s.observables()["step"] == 7
 
 
+def test_ff_load_from_a_device_buffer_zeroes_the_dirichlet_nodes():
+    """gp_load from a caller's device buffer splits it in place (the buffer is
+    only read): the Dirichlet nodes come out zero, every other point within
+    2^-47 of its complex128 value, and the caller's buffer is unchanged."""
+    require_gpu()
+    import torch
+    shape, h = (37, 20, 9), (0.4, 0.4, 0.4)
+    rng = np.random.default_rng(12)
+    a = rng.standard_normal((9, 20, 37)) + 1j * rng.standard_normal((9, 20, 37))
+    dev = torch.from_numpy(a.copy()).cuda()
+    with gp.Solver(shape, h, 0.01, *W3, 1.0, gp.GP_REAL, gp.GP_CFF) as s:
+        s.load(dev)
+        back = s.psi()
+        assert np.array_equal(dev.cpu().numpy(), a)
+    want = a.copy()
+    want[:, :, 0] = 0
+    want[:, 0, :] = 0
+    want[0] = 0
+    assert np.max(np.abs(back - want)) <= 2.0 ** -47 * np.max(np.abs(a))
+    assert not back[:, :, 0].any() and not back[:, 0, :].any() and not back[0].any()
+
+
 def test_ff_rejections():
     require_gpu()
     shape, h = (32, 32, 32), (0.3, 0.3, 0.3)

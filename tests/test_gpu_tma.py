@@ -103,6 +103,25 @@ def test_tma_complex64_1000_imaginary_steps_mu_within_1e6():
     assert abs(obs["energy"] - ref["energy"]) <= 1e-6 * ref["energy"]
 
 
+def test_tma_complex64_1000_real_time_steps_against_the_oracle():
+    """The precision form's real-time regime (trap (1, 2, 4), g = 50, dt / 4h^2 =
+    0.01 as at 512 x 512 x 256) on a 96 x 80 x 64 grid, 1000 steps from the
+    Gaussian seed through the TMA path: mu, E, N and the rms widths within 1e-6
+    of the FP64 oracle."""
+    require_gpu()
+    shape, h, dt, g, w = (96, 80, 64), (0.1, 0.1, 0.1), 4e-4, 50.0, (1.0, 2.0, 4.0)
+    with gp.Solver(shape, h, dt, *w, g, gp.GP_REAL, gp.GP_C64) as s:
+        assert s.paths() == (gp.GP_PATH_TMA,) * 3
+        s.load(None).step(1000)
+        obs = s.observables()
+    p = oracle_params(shape, h, dt, w, g, 1)
+    want = oracle.seed(p)
+    oracle.step(p, want, 1000)
+    ref = oracle.observables(p, want)
+    for k, v in ref.items():
+        assert abs(obs[k] - v) <= 1e-6 * abs(v), (k, obs[k], v)
+
+
 @pytest.mark.parametrize("mode", [gp.GP_REAL, gp.GP_IMAG])
 @pytest.mark.parametrize("precision,dtype,tol", [(gp.GP_C128, np.complex128, 1e-12),
                                                  (gp.GP_C64, np.complex64, 2e-6)])
