@@ -200,9 +200,8 @@ int gp_apply_pending_scale(gp_ctx *ctx);
  * 16 MiB (+512 KiB of tables) that every GPU loading libgp holds until exit,
  * so grids above 1048576 complex128 or 2097152 complex64 points are rejected
  * with GP_EINVAL.  The first call on each device looks up the array's device
- * address (make that first call before any stream capture); the address is
- * kept for the life of the process, so the library must not outlive a
- * cudaDeviceReset of that device.  The coefficient tables are written into
+ * address; the address is kept for the life of the process, so the library
+ * must not outlive a cudaDeviceReset of that device.  The coefficient tables are written into
  * the array by a small kernel on cuda_stream (nothing is staged through host
  * memory).  All calls share the one array, which keeps the last call's
  * contents: calls whose work overlaps on the GPU race with each other.  The
