@@ -32,6 +32,7 @@
 // s P_x P_y P_z (1 + eps), eps = exp(-a) - 1, a = G s^2 |psi|^2, s the
 // pending renormalisation scale.
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <cuda.h>
@@ -56,6 +57,7 @@ struct FfArgs {
     int n;                  // stored points per line (m = n - 1 unknowns)
     int lines_a;            // extent of the in-tile line index
     int win, conv;          // window W (1 .. C), first constant table index
+    int win32;              // the window's first steps that run in FP32 (0 .. W - 1)
     FfCoef cinf, minf;      // the constants past conv
     const FfCoef *cp, *mult;
     float2 kk_hi, kk_lo;    // kappa per lane: (k, k) imaginary, (-k, k) real time
@@ -95,6 +97,15 @@ template <int MODE> struct FfLine {
     {
         if (MODE == 0) return sub(d, rmul(v, c));
         return sub(d, cmul(v, c));
+    }
+    // d - c' v on the hi parts alone (FP32): the first steps of a window,
+    // whose rounding the remaining steps damp below the float-float
+    // rounding before any result is kept
+    __device__ __forceinline__ C back32(C d, const FfCoef &c, C v) const
+    {
+        float2 r = fma2(neg(c.rh), v.hi, d.hi);
+        if (MODE != 0) r = fma2(neg(c.ih), swap(v.hi), r);
+        return C{r, f2(0.f, 0.f)};
     }
 };
 
@@ -299,6 +310,7 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
         }
     } else {
         const FfLine<MODE> cn{args.kk_hi, args.kk_lo};
+        const int win32 = args.win32;
         FfCalcnu<MODE> nl;
         // lanes past a ragged tile's end take the last line's factors
         if (NL && run) nl.setup(args, active ? a : args.lines_a - 1, blockIdx.y);
@@ -358,8 +370,11 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
                         float w[32];
                         tmem_ld32(tbase + tcol(q * Cc), w);
 #pragma unroll
-                        for (int c = Cc - 2; c >= 0; --c)
-                            if (c <= win - 2) v = cn.back(GP_FF_FROM(w, c), cinf, v);
+                        for (int c = Cc - 2; c >= 0; --c) {
+                            if (c > win - 2) continue;
+                            if (c >= win - 1 - win32) v = cn.back32(GP_FF_FROM(w, c), cinf, v);
+                            else v = cn.back(GP_FF_FROM(w, c), cinf, v);
+                        }
                     }
                     float w[32];
                     tmem_ld32(tbase + tcol((q - 1) * Cc), w);
@@ -370,7 +385,9 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
                     }
                 } else {
                     C v = get(q * Cc + win - 1);
-                    for (int c = win - 2; c >= 0; --c) v = cn.back(get(q * Cc + c), cinf, v);
+                    for (int c = win - 2; c >= 0; --c)
+                        v = c >= win - 1 - win32 ? cn.back32(get(q * Cc + c), cinf, v)
+                                                 : cn.back(get(q * Cc + c), cinf, v);
 #pragma unroll
                     for (int c = Cc - 1; c >= 0; --c) {
                         v = cn.back(get((q - 1) * Cc + c), cinf, v);
@@ -722,6 +739,13 @@ void ff_tables(int m, const double2 *cp64, const double2 *mult64, int conv64, do
             break;
         }
     }
+    // FP32 window steps: an error of 2^-24 made at window step s (s = 1 ..
+    // W - 1 from the seed, whose lo part those steps drop) passes W - s more
+    // steps, each scaling it by at most cmax, before the first result: it
+    // stays below 2^-50 when cmax^(W - s) < 2^-26
+    int kmin = 1;
+    for (double q = cmax; q >= 0x1p-26 && kmin <= 64; q *= cmax) ++kmin;
+    out.win32 = out.win > 0 ? std::max(0, std::min(out.win - 1, out.win - kmin)) : 0;
 }
 
 int ff_shapes() { return kNumShapes; }
@@ -769,6 +793,7 @@ cudaError_t launch_sweep_ff(int shape, int mode, int axis, const CUtensorMap &ma
     args.n = g.n;
     args.lines_a = g.lines_a;
     args.win = ax.win;
+    args.win32 = ax.win32;
     args.conv = ax.conv;
     args.cinf = ax.cinf;
     args.minf = ax.minf;

@@ -128,6 +128,7 @@ struct FfAxis {
     int n = 0;
     FfCoef *cp = nullptr, *mult = nullptr;
     int conv = 0, win = 0;
+    int win32 = 0;          // the window's first steps that may run in FP32
     FfCoef cinf{}, minf{};
     double k = 0;
 };
