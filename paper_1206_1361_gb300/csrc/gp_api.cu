@@ -175,17 +175,6 @@ double axis_coord(const gp_ctx *c, int k, int i)
     return coord(edge(c->grid, k), c->h[k], i);
 }
 
-// Forward-elimination tables of (I - kappa L), m unknowns:
-// denom_i = 1 + 2 kappa + kappa c'_{i-1} (c'_0 = 0), mult_i = 1/denom_i,
-// c'_i = -kappa mult_i.
-void thomas_tables(int m, std::complex<double> kappa, std::vector<double2> &cp,
-                   std::vector<double2> &mult)
-{
-    cp.resize(m);
-    mult.resize(m);
-    gp::host_thomas_tables(m, kappa.real(), kappa.imag(), cp.data(), mult.data());
-}
-
 int alloc(gp_ctx *c, void **p, size_t bytes)
 {
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);

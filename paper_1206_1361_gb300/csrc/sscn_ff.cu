@@ -351,8 +351,7 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
             if (fast) {
                 // interior chunk: every point an unknown, constant tables
                 const FfCoef minf = args.minf, cinf = args.cinf;
-#pragma unroll
-                for (int c = 0; c < Cc; ++c) {
+                auto fwd_at = [&](int c) {
                     unsigned char *tc = at(q, c);
                     C p = ld(tc);
                     if (NL) {
@@ -361,6 +360,14 @@ k_sweep_ff(const __grid_constant__ CUtensorMap map, const FfArgs args)
                     }
                     d = cn.fwd(p, d, minf);
                     put(q * Cc + c, d);
+                };
+                if constexpr (NL) {
+                    // with calcnu, unrolled by 4 (1.7 % faster than by 8)
+#pragma unroll 4
+                    for (int c = 0; c < Cc; ++c) fwd_at(c);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < Cc; ++c) fwd_at(c);
                 }
                 if constexpr (TM) {
                     // window: the seed d'_{W-1} by its own load (a runtime
