@@ -633,9 +633,9 @@ k_observables_ff(const float4 *__restrict__ psi, ObsArgs a, const float2 *__rest
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j0 = blockIdx.y * kObsLines, j1 = min(j0 + kObsLines, ny);
     const int k = blockIdx.z;
-    if (threadIdx.x < kObsLines && j0 + (int)threadIdx.x < ny) {
-        yt[0][threadIdx.x] = split(a.y2[j0 + threadIdx.x]);
-        yt[1][threadIdx.x] = split(a.vy[j0 + threadIdx.x]);
+    for (int t = threadIdx.x; t < kObsLines && j0 + t < ny; t += blockDim.x) {
+        yt[0][t] = split(a.y2[j0 + t]);
+        yt[1][t] = split(a.vy[j0 + t]);
     }
     __syncthreads();
     const bool in = i < nx, has_z = nz > 1 && k + 1 < nz;

@@ -242,7 +242,7 @@ long long obs_scratch_doubles(const ObsArgs &a);
 // Observables passes that walk y-lines (complex64, float-float): threads
 // along x (a multiple of 32, at most 256), blocks over (x segments, chunks of
 // kObsLines lines, planes); one row of sums per block.
-constexpr int kObsLines = 32;
+constexpr int kObsLines = 64;
 void obs_walk_geometry(int nx, int ny, int nz, dim3 &grid, int &threads);
 cudaError_t launch_observables(int prec, const void *psi, const ObsArgs &a,
                                double *scratch, double *sums, cudaStream_t st);

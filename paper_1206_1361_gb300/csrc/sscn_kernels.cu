@@ -466,9 +466,9 @@ k_observables_c64(const float2 *__restrict__ psi, ObsArgs a, double *__restrict_
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j0 = blockIdx.y * kObsLines, j1 = min(j0 + kObsLines, ny);
     const int k = blockIdx.z;
-    if (threadIdx.x < kObsLines && j0 + (int)threadIdx.x < ny) {
-        yt[0][threadIdx.x] = (float)a.y2[j0 + threadIdx.x];
-        yt[1][threadIdx.x] = (float)a.vy[j0 + threadIdx.x];
+    for (int t = threadIdx.x; t < kObsLines && j0 + t < ny; t += blockDim.x) {
+        yt[0][t] = (float)a.y2[j0 + t];
+        yt[1][t] = (float)a.vy[j0 + t];
     }
     __syncthreads();
     const bool in = i < nx, has_z = k + 1 < nz;
