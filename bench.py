@@ -856,6 +856,9 @@ def serving_form(gp, prefix=SERVE_PREFIX, sample=SERVE_SEQ_SAMPLE, sustained=SER
 
 PROBE_BATCH = "batch-60-requests-c64"
 PROBE_AXIAL = "axial-1024x2048-fp64"
+# the 128 x 128 x 32 instance of the batched set alone in a batch (10-step
+# launches, one more than --probe // 10): a batch's tail in miniature
+PROBE_BATCH_ONE = "batch-1-128x128x32-c64"
 
 
 def run_probe(args):
@@ -868,6 +871,7 @@ def run_probe(args):
     __graft_entry__.build()
     from paper_1206_1361_gb300 import gp
     from paper_1206_1361_gb300.workloads import CASES, request_stream
+    from paper_1206_1361_gb300.workloads import batched_instances as workloads_batched
     if args.probe_case == PROBE_BATCH:
         with gp.Batch(gp.GP_C64, 1 << 36) as b:
             for r in request_stream(count=60):
@@ -875,6 +879,15 @@ def run_probe(args):
                 b.add(i.shape, i.h, i.dt, *i.trap, i.g, gp.GP_IMAG)
             b.step(args.probe)
             gp.gp_batch_sync(b.b)
+        torch.cuda.synchronize()
+        return 0
+    if args.probe_case == PROBE_BATCH_ONE:
+        inst = [i for i in workloads_batched() if i.shape == (128, 128, 32)][0]
+        with gp.Batch(gp.GP_C64, 1 << 34) as b:
+            b.add(inst.shape, inst.h, inst.dt, *inst.trap, inst.g, gp.GP_IMAG)
+            for _ in range(1 + args.probe // 10):
+                b.step(10)
+                gp.gp_batch_sync(b.b)
         torch.cuda.synchronize()
         return 0
     if args.probe_case == PROBE_AXIAL:
