@@ -467,6 +467,16 @@ int gp_batch_set_wait_ns(gp_batch *b, int64_t ns);
 /* Observables of every instance, out[slot] for slot < capacity (unused slots
  * get step = -1); synchronises. */
 int gp_batch_observables(gp_batch *b, gp_obs *out, int capacity);
+/*
+ * Observables (the quantities of calcnorm / calcmuen / calcrms, as in
+ * gp_observables) of the instances slots[0 .. count-1] only, out[i] for
+ * slots[i]; synchronises.  A serving loop checks the few instances that are
+ * due without paying for a pass over every instance in the batch.  Results
+ * are identical to gp_batch_observables' for the same slots.  Host arrays,
+ * caller-owned.  GP_EINVAL for count < 0, a NULL array with count > 0 or an
+ * unused slot; errors of earlier launches as gp_batch_observables.
+ */
+int gp_batch_observables_of(gp_batch *b, const int *slots, int count, gp_obs *out);
 /* Release one slot's memory (stream-ordered). */
 int gp_batch_remove(gp_batch *b, int slot);
 /* Active instances, slot table size and bytes charged against the cap. */

@@ -4,7 +4,7 @@
 // Work is a queue of items (step s, phase p, instance i, tile t) in that
 // order: phases are the x, y and z Crank-Nicolson sweeps (calclux, calcluy,
 // calcluz; calcnu fused into x) and, in imaginary time, the norm finish
-// (calcnorm).  A tile is 16 lines of one instance along one axis.  Resident
+// (calcnorm).  A tile is 16 or 8 lines of one instance along one axis.  Resident
 // CTAs pop items from an atomic counter; before working on an item a CTA
 // waits until every item of the same instance's previous phase has
 // completed (a per-instance completion counter; the wait is bounded by
@@ -12,18 +12,21 @@
 // CTAs, so the waits always end; instances at different phases overlap and
 // no grid-wide barrier separates the sweeps.
 //
-// Tile solver: one warp, 16 lines staged in shared memory (coalesced loads:
-// rows for x tiles, 16-byte pieces of columns of 16 neighbouring lines for
-// y / z),
-// each line eliminated from both ends by a lane pair in place (the right-hand
-// side (1 - 2 kappa) psi_i + kappa (psi_{i-1} + psi_{i+1}) formed on the fly,
-// forward elimination overwriting psi with d', the pair meeting at the middle
-// row, back substitution overwriting d' with u), and the tile is written
-// back.  16-line tiles halve the shared memory a warp holds against 32-line
-// ones, which doubles the warps resident per SM.  Lines are at most 512
-// points (complex64) / 384 (complex128).  The per-instance decomposition depends only
-// on the instance's own shape and its norm is summed in a fixed order, so an
-// instance's result is bit-identical alone and in any mix.
+// Tile solver: one warp, the tile's lines staged in shared memory (coalesced
+// loads: rows for x tiles, 16-byte pieces of columns of neighbouring lines
+// for y / z), each line solved in place (the right-hand side
+// (1 - 2 kappa) psi_i + kappa (psi_{i-1} + psi_{i+1}) formed on the fly,
+// forward elimination overwriting psi with d', back substitution overwriting
+// d' with u), and the tile is written back.  Lines of fewer than 96 points:
+// 16-line tiles, each line eliminated exactly from both ends by a lane pair
+// (gp::solve_pair).  Longer lines: 8-line tiles, each line split into 4
+// segments solved at once by 4 lanes with look-back / look-ahead windows
+// (gp::solve_seg), which shortens an item's dependency chain (the latency of
+// a lone instance's step) and halves the shared memory a warp holds (more
+// warps resident per SM).  Lines are at most 512 points (complex64) / 384
+// (complex128).  The per-instance decomposition depends only on the
+// instance's own shape and coefficients, and its norm is summed in a fixed
+// order, so an instance's result is bit-identical alone and in any mix.
 
 #include <algorithm>
 #include <cmath>
@@ -40,6 +43,7 @@
 #include "sscn_internal.h"
 #include "sscn_line.cuh"
 #include "sscn_pair.cuh"
+#include "sscn_seg.cuh"
 
 namespace {
 
@@ -55,8 +59,11 @@ template <typename T> __device__ __forceinline__ typename BC<T>::c mkb(T x, T y)
     return r;
 }
 
-constexpr int kTileLines = 16;
+constexpr int kPairLines = 16;     // lines per tile, two-ended pair solve
+constexpr int kSegLines = 8;       // lines per tile, 4-segment solve
+constexpr int kSegMinN = 96;       // edges from which an axis uses the segment solve
 constexpr int kObsWidthB = gp::kObsWidth;
+constexpr int kObsGroup = 16;      // x-lines per warp of the observables pass
 constexpr int kMaxEdge32 = 512, kMaxEdge64 = 384;
 constexpr uint64_t kWaitNs = 2000000000ull;   // default dependency-wait budget
 constexpr unsigned kPollMaxNs = 512;
@@ -68,6 +75,8 @@ struct Inst {
     int mode;               // 0 imaginary, 1 real time
     int last_axis;          // 1 (2D) or 2 (3D)
     int tiles[3];           // tiles per axis (0 for z in 2D)
+    int rows[3];            // lines per tile per axis: kPairLines or kSegLines
+    int win[3];             // segment-solve window per axis (current mode)
     double kap[3];          // kappa / i (real time) or kappa (imaginary time)
     const void *cp[3], *mult[3];    // current-mode tables (Coef<T>), n - 1 entries
     int conv[3];                    // index from which the table entries are constant
@@ -98,6 +107,12 @@ struct LaunchArgs {
     int *abort_flag;
     unsigned long long wait_ns;     // budget of one dependency wait
 };
+
+// Rows of an instance's observables partials: groups of kObsGroup x-lines.
+__host__ __device__ __forceinline__ long long obs_groups(int ny, int nz)
+{
+    return ((long long)ny * nz + kObsGroup - 1) / kObsGroup;
+}
 
 __device__ __forceinline__ uint64_t gtime()
 {
@@ -155,12 +170,14 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
-// The exact line update of a lane pair (gp::solve_pair) on a tile row:
-// x tiles row-major (element stride 1, calcnu fused into the elimination),
-// y / z tiles column-major (stride 16).
-template <typename T, int MODE, bool NL>
-__device__ __forceinline__ void solve_line2(const Inst &I, int axis, typename BC<T>::c *row, int n,
-                                            long long line, bool top, bool active, bool norm, Acc<T> &acc)
+// The line update of one tile row: x tiles row-major (element stride 1,
+// calcnu fused into the elimination), y / z tiles column-major (stride R).
+// R = kPairLines: the exact two-ended solve of a lane pair (gp::solve_pair,
+// seg 0 the top lane); R = kSegLines: the 4-segment solve (gp::solve_seg,
+// lane seg owning segment seg).
+template <typename T, int MODE, bool NL, int R>
+__device__ __forceinline__ void solve_line(const Inst &I, int axis, typename BC<T>::c *row, int n,
+                                           long long line, int seg, bool active, bool norm, Acc<T> &acc)
 {
     using F = typename Coef<T>::t;
     gp::PairTabs<T> tb;
@@ -184,7 +201,19 @@ __device__ __forceinline__ void solve_line2(const Inst &I, int axis, typename BC
         cu.setup(static_cast<const F *>(I.ph[0]), static_cast<const F *>(I.ph[1]),
                  static_cast<const F *>(I.ph[2]), I.th[0], I.th[1], I.th[2], j, kz, I.dtg, I.scale);
     }
-    gp::solve_pair<T, MODE, NL, NL ? 1 : kTileLines>(row, 0, n, top, active, norm, acc, tb, cu);
+    if constexpr (R == kPairLines)
+        gp::solve_pair<T, MODE, NL, NL ? 1 : R>(row, 0, n, seg == 0, active, norm, acc, tb, cu);
+    else
+        gp::solve_seg<T, MODE, NL, NL ? 1 : R, 32 / R>(row, 0, n, seg, I.win[axis], active, norm, acc, tb, cu);
+}
+
+// Row pitch (elements) of an x tile: odd for the pair solve (lane r's column
+// accesses hit distinct banks), 2 mod 4 for the segment solve (the 8 rows
+// fall on distinct even bank pairs, and segments starting on points of
+// opposite parity on the odd ones).
+__host__ __device__ __forceinline__ int x_pitch(int n, int R)
+{
+    return R == kPairLines ? (n | 1) : n + ((2 - (n & 3)) & 3);
 }
 
 // Line index -> offset of its point 0 and the stride between its points.
@@ -197,33 +226,34 @@ __device__ __forceinline__ void line_geom(const Inst &I, int axis, long long L, 
     else { base = L; stride = nx * ny; }
 }
 
-// A tile in shared memory: x tiles row-major (line r at sm + r P, odd pitch
-// P: lane r's column accesses hit distinct banks), y / z tiles column-major
-// (point c of the 16 lines at sm + 16 c): neighbouring y / z lines are
-// neighbouring in memory, so a full tile of 16 consecutive lines moves as
-// 16 * sizeof(C)-byte columns in 16-byte pieces (32 / sizeof(C) columns per
-// warp instruction); other y / z tiles (a row of lines ending inside the
-// tile, a partial last tile, odd nx) go point by point.
-template <typename T>
+// A tile of R lines in shared memory: x tiles row-major (line r at
+// sm + r P, P = x_pitch), y / z tiles column-major (point c of the R lines at
+// sm + R c): neighbouring y / z lines are neighbouring in memory, so a full
+// tile of R consecutive lines moves as R * sizeof(C)-byte columns in 16-byte
+// pieces; other y / z tiles (a row of lines ending inside the tile, a
+// partial last tile, odd nx) go point by point.  Lane (r, seg) = (lane % R,
+// lane / R) works on line r.
+template <typename T, int R>
 __device__ __forceinline__ void sweep_tile(const Inst &I, int axis, int tile, typename BC<T>::c *sm, int lane)
 {
     using C = typename BC<T>::c;
+    constexpr int S = 32 / R;              // lanes per line
     const int n = I.n[axis];
-    const int P = n | 1;                   // odd row pitch: conflict-free columns
+    const int P = x_pitch(n, R);
     const long long lines = axis == 0 ? (long long)I.n[1] * I.n[2]
                           : axis == 1 ? (long long)I.n[0] * I.n[2] : (long long)I.n[0] * I.n[1];
-    const long long L0 = (long long)tile * kTileLines;
-    const int rows = (int)min((long long)kTileLines, lines - L0);
-    const int r = lane & (kTileLines - 1);
-    const bool top = lane < kTileLines, active = r < rows;
+    const long long L0 = (long long)tile * R;
+    const int rows = (int)min((long long)R, lines - L0);
+    const int r = lane & (R - 1), seg = lane / R;
+    const bool active = r < rows;
     C *psi = static_cast<C *>(I.psi);
     const int nx = I.n[0];                 // (kept in a register across the cp.async clobbers)
     constexpr int B = (int)sizeof(C);
-    constexpr int Q = B;                   // 16-byte pieces per column (16 lines)
+    constexpr int Q = R * B / 16;          // 16-byte pieces per column
     constexpr int E = 16 / B;              // elements per piece
     long long base = 0, stride = 0, base0 = 0;
-    // y / z tiles: the lane pair of line r moves the two halves of its line
-    const int c_lo = top ? 0 : n / 2, c_hi = top ? n / 2 : n;
+    // y / z tiles point by point: the S lanes of line r move a part each
+    const int c_lo = seg * n / S, c_hi = (seg + 1) * n / S;
     bool wide = false;
     if (axis == 0) {
         for (int rr = 0; rr < rows; ++rr) {
@@ -232,17 +262,17 @@ __device__ __forceinline__ void sweep_tile(const Inst &I, int axis, int tile, ty
         }
     } else {
         line_geom(I, axis, L0, base0, stride);
-        // 16 lines at unit spacing, every column starting on 16 bytes
-        wide = rows == kTileLines && (axis == 2 || (L0 % nx) + kTileLines <= nx) &&
+        // R lines at unit spacing, every column starting on 16 bytes
+        wide = rows == R && (axis == 2 || (L0 % nx) + R <= nx) &&
                ((base0 * B) & 15) == 0 && ((stride * B) & 15) == 0;
         if (wide) {
             const C *src = psi + base0 + (lane % Q) * E;
             C *dst = sm + (lane % Q) * E;
             for (int c = lane / Q; c < n; c += 32 / Q)
-                cp_async<16>(dst + c * kTileLines, src + c * stride);
+                cp_async<16>(dst + c * R, src + c * stride);
         } else if (active) {
             line_geom(I, axis, L0 + r, base, stride);
-            for (int c = c_lo; c < c_hi; ++c) cp_async<B>(&sm[c * kTileLines + r], &psi[base + c * stride]);
+            for (int c = c_lo; c < c_hi; ++c) cp_async<B>(&sm[c * R + r], &psi[base + c * stride]);
         }
     }
     // the tables the solve reads first (coefficients up to where they turn
@@ -274,11 +304,11 @@ __device__ __forceinline__ void sweep_tile(const Inst &I, int axis, int tile, ty
     C *row = axis == 0 ? sm + r * P : sm + r;
     Acc<T> acc;
     if (axis == 0) {
-        if (I.mode == 0) solve_line2<T, 0, true>(I, axis, row, n, L0 + r, top, active, norm, acc);
-        else solve_line2<T, 1, true>(I, axis, row, n, L0 + r, top, active, false, acc);
+        if (I.mode == 0) solve_line<T, 0, true, R>(I, axis, row, n, L0 + r, seg, active, norm, acc);
+        else solve_line<T, 1, true, R>(I, axis, row, n, L0 + r, seg, active, false, acc);
     } else {
-        if (I.mode == 0) solve_line2<T, 0, false>(I, axis, row, n, L0 + r, top, active, norm, acc);
-        else solve_line2<T, 1, false>(I, axis, row, n, L0 + r, top, active, false, acc);
+        if (I.mode == 0) solve_line<T, 0, false, R>(I, axis, row, n, L0 + r, seg, active, norm, acc);
+        else solve_line<T, 1, false, R>(I, axis, row, n, L0 + r, seg, active, false, acc);
     }
     __syncwarp();
     if (axis == 0) {
@@ -291,9 +321,9 @@ __device__ __forceinline__ void sweep_tile(const Inst &I, int axis, int tile, ty
         const C *src = sm + (lane % Q) * E;
         for (int c = lane / Q; c < n; c += 32 / Q)
             *reinterpret_cast<float4 *>(dst + c * stride) =
-                *reinterpret_cast<const float4 *>(src + c * kTileLines);
+                *reinterpret_cast<const float4 *>(src + c * R);
     } else if (active) {
-        for (int c = c_lo; c < c_hi; ++c) psi[base + c * stride] = sm[c * kTileLines + r];
+        for (int c = c_lo; c < c_hi; ++c) psi[base + c * stride] = sm[c * R + r];
     }
     if (norm) {
         const double v = warp_sum_d(acc.get());
@@ -402,7 +432,10 @@ __global__ void __launch_bounds__(32) k_batch_steps(const __grid_constant__ Laun
         // lane 0's acquire, then the warp barrier (which orders memory among
         // its lanes), make the previous phase's stores visible to every lane
         __syncwarp();
-        if (p < 3) sweep_tile<T>(I, p, tile, sm, lane);
+        if (p < 3) {
+            if (I.rows[p] == kSegLines) sweep_tile<T, kSegLines>(I, p, tile, sm, lane);
+            else sweep_tile<T, kPairLines>(I, p, tile, sm, lane);
+        }
         else norm_item(I, lane, A.err);
         // the barrier orders every lane's stores before lane 0's release,
         // which carries them (cumulatively) to the waiting warps
@@ -413,52 +446,68 @@ __global__ void __launch_bounds__(32) k_batch_steps(const __grid_constant__ Laun
 
 // ---------------------------------------------------------------- observables
 
-// One warp per x-line of every instance (line_pref: prefix of x-lines over
-// instances); per-line partials exactly as the single-grid observables pass.
+// One warp per group of kObsGroup consecutive x-lines of the instances
+// inst[idx[0 .. M-1]] (grp_pref: prefix of their groups), the lanes across
+// x: the sums of the observables pass (|psi|^2, x^2 |psi|^2 per axis,
+// V |psi|^2, |psi|^4 and the forward-difference kinetic terms) over the
+// group into one row of I.obs_rows.  The per-line factors (y^2, z^2 and
+// V_y + V_z) multiply each lane's partial |psi|^2 of the line in FP64; a
+// warp reduces once per group, not once per line.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_batch_obs(const Inst *inst, const long long *line_pref, int N)
+k_batch_obs(const Inst *inst, const int *idx, const long long *grp_pref, int N)
 {
     using C = typename BC<T>::c;
     const int lane = threadIdx.x & 31;
     const long long g = (long long)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (g >= line_pref[N]) return;
+    if (g >= grp_pref[N]) return;
     int lo = 0, hi = N;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (line_pref[mid] <= g) lo = mid;
+        if (grp_pref[mid] <= g) lo = mid;
         else hi = mid;
     }
-    const Inst &I = inst[lo];
-    const long long line = g - line_pref[lo];
+    const Inst &I = inst[idx[lo]];
+    const long long grp = g - grp_pref[lo];
     const int nx = I.n[0], ny = I.n[1], nz = I.n[2];
-    const int j = (int)(line % ny), k = (int)(line / ny);
+    const long long l0 = grp * kObsGroup, l1 = min((long long)ny * nz, l0 + kObsGroup);
     const long long plane = (long long)nx * ny;
-    const C *row = static_cast<const C *>(I.psi) + line * nx;
-    const bool has_y = j + 1 < ny, has_z = k + 1 < nz;
+    const C *psi = static_cast<const C *>(I.psi);
     const C zero = mkb<T>((T)0, (T)0);
-    Acc<T> s0, sx, svx, s4, kx, ky, kz;
+    Acc<T> sx, svx, s4, kx, ky, kz;
+    double s0 = 0.0, fy = 0.0, fz = 0.0, fv = 0.0;
     const T *x2 = sizeof(T) == 8 ? (const T *)I.x2[0] : (const T *)I.x2f;
     const T *vx = sizeof(T) == 8 ? (const T *)I.v[0] : (const T *)I.vf;
-    for (int i = lane; i < nx; i += 32) {
-        const C v = row[i];
-        const T am = fma(v.x, v.x, v.y * v.y);
-        s0.add(am);
-        sx.add_prod(x2[i], am);
-        svx.add_prod(vx[i], am);
-        s4.add_prod(am, am);
-        const C nb = (i + 1 < nx) ? row[i + 1] : zero;
-        kx.add_sq2(nb.x - v.x, nb.y - v.y);
-        const C ny_ = has_y ? row[i + nx] : zero;
-        ky.add_sq2(ny_.x - v.x, ny_.y - v.y);
-        if (nz > 1) {
-            const C nz_ = has_z ? row[i + plane] : zero;
-            kz.add_sq2(nz_.x - v.x, nz_.y - v.y);
+    const double *x2y = I.x2[1], *x2z = I.x2[2], *vy = I.v[1], *vz = I.v[2];
+    for (long long line = l0; line < l1; ++line) {
+        const int j = (int)(line % ny), k = (int)(line / ny);
+        const C *row = psi + line * nx;
+        const bool has_y = j + 1 < ny, has_z = k + 1 < nz;
+        Acc<T> ls;
+        for (int i = lane; i < nx; i += 32) {
+            const C v = row[i];
+            const T am = fma(v.x, v.x, v.y * v.y);
+            ls.add(am);
+            sx.add_prod(x2[i], am);
+            svx.add_prod(vx[i], am);
+            s4.add_prod(am, am);
+            const C nb = (i + 1 < nx) ? row[i + 1] : zero;
+            kx.add_sq2(nb.x - v.x, nb.y - v.y);
+            const C ny_ = has_y ? row[i + nx] : zero;
+            ky.add_sq2(ny_.x - v.x, ny_.y - v.y);
+            if (nz > 1) {
+                const C nz_ = has_z ? row[i + plane] : zero;
+                kz.add_sq2(nz_.x - v.x, nz_.y - v.y);
+            }
         }
+        const double p = ls.get();
+        s0 += p;
+        fy = fma(x2y[j], p, fy);
+        fz = fma(x2z[k], p, fz);
+        fv = fma(vy[j] + vz[k], p, fv);
     }
-    double r0, rx, rv, r4, qx, qy, qz;
+    double rx, rv, r4, qx, qy, qz;
     if constexpr (sizeof(T) == 4) {
-        r0 = warp_sum_comp(s0.s, s0.c);
         rx = warp_sum_comp(sx.s, sx.c);
         rv = warp_sum_comp(svx.s, svx.c);
         r4 = warp_sum_comp(s4.s, s4.c);
@@ -466,7 +515,6 @@ k_batch_obs(const Inst *inst, const long long *line_pref, int N)
         qy = warp_sum_comp(ky.s, ky.c);
         qz = warp_sum_comp(kz.s, kz.c);
     } else {
-        r0 = warp_sum_d(s0.get());
         rx = warp_sum_d(sx.get());
         rv = warp_sum_d(svx.get());
         r4 = warp_sum_d(s4.get());
@@ -474,14 +522,15 @@ k_batch_obs(const Inst *inst, const long long *line_pref, int N)
         qy = warp_sum_d(ky.get());
         qz = warp_sum_d(kz.get());
     }
+    const double r0 = warp_sum_d(s0), ry = warp_sum_d(fy), rz = warp_sum_d(fz), rvv = warp_sum_d(fv);
     if (lane == 0) {
         const double sc = *I.scale, s2 = sc * sc;
-        double *out = I.obs_rows + line * kObsWidthB;
+        double *out = I.obs_rows + grp * kObsWidthB;
         out[0] = s2 * r0;
         out[1] = s2 * rx;
-        out[2] = s2 * I.x2[1][j] * r0;
-        out[3] = s2 * I.x2[2][k] * r0;
-        out[4] = s2 * (rv + (I.v[1][j] + I.v[2][k]) * r0);
+        out[2] = s2 * ry;
+        out[3] = s2 * rz;
+        out[4] = s2 * (rv + rvv);
         out[5] = s2 * s2 * r4;
         out[6] = s2 * qx;
         out[7] = s2 * qy;
@@ -489,12 +538,13 @@ k_batch_obs(const Inst *inst, const long long *line_pref, int N)
     }
 }
 
-// One block per instance: its rows summed in a fixed order into sums[i][9].
-__global__ void __launch_bounds__(256) k_batch_obs_finish(const Inst *inst, double *sums)
+// One block per instance inst[idx[i]]: its rows summed in a fixed order into
+// sums[i][9].
+__global__ void __launch_bounds__(256) k_batch_obs_finish(const Inst *inst, const int *idx, double *sums)
 {
     __shared__ double red[8];
-    const Inst &I = inst[blockIdx.x];
-    const long long rows = (long long)I.n[1] * I.n[2];
+    const Inst &I = inst[idx[blockIdx.x]];
+    const long long rows = obs_groups(I.n[1], I.n[2]);
     for (int q = 0; q < kObsWidthB; ++q) {
         double v = 0.0;
         for (long long r = threadIdx.x; r < rows; r += blockDim.x) v += I.obs_rows[r * kObsWidthB + q];
@@ -546,6 +596,7 @@ struct gp_batch_slot {
     float *x2f = nullptr, *vf = nullptr;
     double *scale = nullptr, *norm = nullptr, *partials = nullptr, *obs_rows = nullptr;
     gp::AxisTables conv[2][3];      // convergence fields per mode/axis (host)
+    int win[2][3]{};                // segment-solve windows per mode/axis
 };
 
 struct gp_batch {
@@ -562,16 +613,17 @@ struct gp_batch {
     size_t ints_cap = 0;
     unsigned long long *d_head = nullptr;
     int *d_err = nullptr;           // error bits, abort flag
-    long long *d_line_pref = nullptr;
     double *d_sums = nullptr;
     size_t inst_cap = 0;
     double *h_sums = nullptr;       // pinned
+    // observables of a subset: M + 1 line prefixes then M active indices,
+    // staged in pinned memory and copied to the device in one piece
+    unsigned char *d_sub = nullptr, *h_sub = nullptr;
     int *h_err = nullptr;           // pinned
     unsigned long long wait_ns = kWaitNs;
     LaunchArgs args{};
     size_t smem = 0;
     int grid = 0;
-    long long obs_lines = 0;
     std::string last_error;
 };
 
@@ -610,10 +662,35 @@ long long lines_of(const gp_grid &g, int axis)
     return axis == 0 ? ny * nz : axis == 1 ? nx * nz : nx * ny;
 }
 
+// Lines per tile of an axis with n points per line (a function of the
+// shape alone, so tile counts do not change with the mode).
+int tile_rows(int n) { return n >= kSegMinN ? kSegLines : kPairLines; }
+
 int tiles_of(const gp_grid &g, int axis)
 {
     if (axis >= axes_of(g)) return 0;
-    return (int)((lines_of(g, axis) + kTileLines - 1) / kTileLines);
+    const int R = tile_rows(edge_of(g, axis));
+    return (int)((lines_of(g, axis) + R - 1) / R);
+}
+
+// Shared-memory elements of one tile along an axis.
+size_t tile_elems(const gp_grid &g, int axis)
+{
+    const int n = edge_of(g, axis), R = tile_rows(n);
+    return (size_t)R * (axis == 0 ? x_pitch(n, R) : n);
+}
+
+// Window of the segment solve: the least W with cmax^(W+1) < eps (cmax the
+// largest |c'_i| of the axis), or a width past any line (exact) if there is
+// none below 1024.
+int seg_window(double cmax, double eps)
+{
+    double p = cmax;
+    for (int w = 0; w < 1024; ++w) {
+        if (p < eps) return w;
+        p *= cmax;
+    }
+    return 1 << 20;
 }
 
 // Layout of a slot's aux block (byte offsets), 256-byte aligned pieces.
@@ -678,6 +755,11 @@ int upload_slot(gp_batch *b, gp_batch_slot &s)
                 gp::AxisTables &a = s.conv[mode][k];
                 gp::fill_tables(a, m, mode == 0 ? kap : 0.0, mode == 0 ? 0.0 : kap, cp.data(), mult.data(),
                                 c32.data(), m32.data());
+                // dropped window terms below the storage rounding: 2^-32
+                // (complex64, 24-bit significands), 2^-56 (complex128)
+                double cmax = 0.0;
+                for (int i = 0; i < m; ++i) cmax = std::max(cmax, std::hypot(cp[i].x, cp[i].y));
+                s.win[mode][k] = seg_window(cmax, std::ldexp(1.0, b->prec == GP_C128 ? -56 : -32));
                 if (b->prec == GP_C128) {
                     put(L.cp[mode][k], cp.data(), m * sizeof(double2));
                     put(L.mult[mode][k], mult.data(), m * sizeof(double2));
@@ -753,6 +835,8 @@ Inst make_inst(const gp_batch_slot &s, int prec)
     I.last_axis = axes_of(s.grid) - 1;
     for (int k = 0; k < 3; ++k) {
         I.tiles[k] = tiles_of(s.grid, k);
+        I.rows[k] = tile_rows(edge_of(s.grid, k));
+        I.win[k] = s.win[s.mode][k];
         I.kap[k] = k < axes_of(s.grid) ? s.dt / (4.0 * s.h[k] * s.h[k]) : 0.0;
         I.cp[k] = s.cp[s.mode][k];
         I.mult[k] = s.mult[s.mode][k];
@@ -780,22 +864,28 @@ Inst make_inst(const gp_batch_slot &s, int prec)
     return I;
 }
 
+// Bytes of the subset staging block for up to cap instances.
+size_t sub_bytes(size_t cap) { return (cap + 1) * sizeof(long long) + cap * sizeof(int); }
+
 int ensure_capacity(gp_batch *b, size_t n_inst)
 {
     if (n_inst <= b->inst_cap && b->d_inst) return GP_OK;
     const size_t cap = std::max<size_t>(64, n_inst * 2);
     if (b->d_inst) cudaFreeAsync(b->d_inst, b->stream);
-    if (b->d_line_pref) cudaFreeAsync(b->d_line_pref, b->stream);
+    if (b->d_sub) cudaFreeAsync(b->d_sub, b->stream);
     if (b->d_sums) cudaFreeAsync(b->d_sums, b->stream);
-    if (b->h_sums) {
+    if (b->h_sums || b->h_sub) {
         cudaStreamSynchronize(b->stream);
-        cudaFreeHost(b->h_sums);
+        if (b->h_sums) cudaFreeHost(b->h_sums);
+        if (b->h_sub) cudaFreeHost(b->h_sub);
         b->h_sums = nullptr;
+        b->h_sub = nullptr;
     }
     GP_BCK(b, cudaMallocAsync((void **)&b->d_inst, cap * sizeof(Inst), b->stream));
-    GP_BCK(b, cudaMallocAsync((void **)&b->d_line_pref, (cap + 1) * sizeof(long long), b->stream));
+    GP_BCK(b, cudaMallocAsync((void **)&b->d_sub, sub_bytes(cap), b->stream));
     GP_BCK(b, cudaMallocAsync((void **)&b->d_sums, cap * gp::kObsWidth * sizeof(double), b->stream));
     GP_BCK(b, cudaMallocHost((void **)&b->h_sums, cap * gp::kObsWidth * sizeof(double)));
+    GP_BCK(b, cudaMallocHost((void **)&b->h_sub, sub_bytes(cap)));
     b->inst_cap = cap;
     return GP_OK;
 }
@@ -816,9 +906,8 @@ int prepare(gp_batch *b)
     if (rc) return rc;
     std::vector<Inst> inst(N);
     std::vector<int> pref(4 * (N + 1), 0), cum(4 * N, 0), tot(N, 0);
-    std::vector<long long> lpref(N + 1, 0);
     long long ptot[4] = {0, 0, 0, 0};
-    int maxP = 1;
+    size_t max_elems = 1;
     for (int a = 0; a < N; ++a) {
         const gp_batch_slot &s = b->slots[b->active[a]];
         inst[a] = make_inst(s, b->prec);
@@ -833,8 +922,7 @@ int prepare(gp_batch *b)
             ptot[p] += items[p];
         }
         tot[a] = c;
-        lpref[a + 1] = lpref[a] + lines_of(s.grid, 0);
-        for (int k = 0; k < axes_of(s.grid); ++k) maxP = std::max(maxP, edge_of(s.grid, k) | 1);
+        for (int k = 0; k < axes_of(s.grid); ++k) max_elems = std::max(max_elems, tile_elems(s.grid, k));
     }
     const size_t nints = pref.size() + cum.size() + tot.size() + N;
     if (nints > b->ints_cap) {
@@ -848,8 +936,6 @@ int prepare(gp_batch *b)
     ints.insert(ints.end(), tot.begin(), tot.end());
     GP_BCK(b, cudaMemcpyAsync(b->d_inst, inst.data(), N * sizeof(Inst), cudaMemcpyHostToDevice, b->stream));
     GP_BCK(b, cudaMemcpyAsync(b->d_ints, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
-    GP_BCK(b, cudaMemcpyAsync(b->d_line_pref, lpref.data(), (N + 1) * sizeof(long long),
-                              cudaMemcpyHostToDevice, b->stream));
     GP_BCK(b, cudaStreamSynchronize(b->stream));
     LaunchArgs &A = b->args;
     A.inst = b->d_inst;
@@ -863,8 +949,7 @@ int prepare(gp_batch *b)
     A.err = b->d_err;
     A.abort_flag = b->d_err + 1;
     A.head = b->d_head;
-    b->smem = (size_t)kTileLines * maxP * elem(b->prec);
-    b->obs_lines = lpref[N];
+    b->smem = max_elems * elem(b->prec);
     int per_sm = 0, sms = 0, dev = 0;
     GP_BCK(b, cudaGetDevice(&dev));
     GP_BCK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -921,6 +1006,60 @@ int materialize(gp_batch *b, gp_batch_slot &s)
 bool valid_slot(gp_batch *b, int slot)
 {
     return b && slot >= 0 && slot < (int)b->slots.size() && b->slots[slot].used;
+}
+
+// Observables of the active instances b->active[sel[i]] into out[i]
+// (prepared batch); synchronises.  Each instance's sums run over its own
+// rows in a fixed order, so a result does not depend on the subset.
+int observe(gp_batch *b, const std::vector<int> &sel, gp_obs *out)
+{
+    const int M = (int)sel.size();
+    if (M == 0) return GP_OK;
+    long long *pref = reinterpret_cast<long long *>(b->h_sub);
+    int *idx = reinterpret_cast<int *>(pref + M + 1);
+    pref[0] = 0;
+    for (int i = 0; i < M; ++i) {
+        idx[i] = sel[i];
+        const gp_grid &g = b->slots[b->active[sel[i]]].grid;
+        pref[i + 1] = pref[i] + obs_groups(g.ny, g.nz);
+    }
+    const size_t bytes = (M + 1) * sizeof(long long) + M * sizeof(int);
+    GP_BCK(b, cudaMemcpyAsync(b->d_sub, b->h_sub, bytes, cudaMemcpyHostToDevice, b->stream));
+    const long long *d_pref = reinterpret_cast<const long long *>(b->d_sub);
+    const int *d_idx = reinterpret_cast<const int *>(d_pref + M + 1);
+    const unsigned blocks = (unsigned)((pref[M] * 32 + 255) / 256);
+    if (b->prec == GP_C128) k_batch_obs<double><<<blocks, 256, 0, b->stream>>>(b->d_inst, d_idx, d_pref, M);
+    else k_batch_obs<float><<<blocks, 256, 0, b->stream>>>(b->d_inst, d_idx, d_pref, M);
+    GP_BCK(b, cudaGetLastError());
+    k_batch_obs_finish<<<M, 256, 0, b->stream>>>(b->d_inst, d_idx, b->d_sums);
+    GP_BCK(b, cudaGetLastError());
+    GP_BCK(b, cudaMemcpyAsync(b->h_sums, b->d_sums, M * gp::kObsWidth * sizeof(double),
+                              cudaMemcpyDeviceToHost, b->stream));
+    const int rc = batch_sync_errors(b);     // (also makes h_sub reusable)
+    int bad = 0;
+    for (int i = 0; i < M; ++i) {
+        const gp_batch_slot &s = b->slots[b->active[sel[i]]];
+        const double *q = b->h_sums + (size_t)i * gp::kObsWidth;
+        const double w = s.h[0] * s.h[1] * (s.grid.nz > 1 ? s.h[2] : 1.0);
+        const double nrm = w * q[0];
+        double kin = 0.5 * (q[6] / (s.h[0] * s.h[0]) + q[7] / (s.h[1] * s.h[1]));
+        if (s.grid.nz > 1) kin += 0.5 * q[8] / (s.h[2] * s.h[2]);
+        gp_obs &o = out[i];
+        std::memset(&o, 0, sizeof(gp_obs));
+        o.norm = nrm;
+        o.mu = w * (kin + q[4] + s.g * q[5]) / nrm;
+        o.energy = w * (kin + q[4] + 0.5 * s.g * q[5]) / nrm;
+        o.rms_x = std::sqrt(q[1] / q[0]);
+        o.rms_y = std::sqrt(q[2] / q[0]);
+        o.rms_z = std::sqrt(q[3] / q[0]);
+        o.rms_r = std::sqrt((q[1] + q[2] + q[3]) / q[0]);
+        o.step = s.step;
+        o.t = s.step * s.dt;
+        if (!std::isfinite(o.mu) || !std::isfinite(o.norm)) bad = 1;
+    }
+    if (rc) return rc;
+    if (bad) return bfail(b, GP_ENONFINITE, "gp_batch_observables: non-finite result");
+    return GP_OK;
 }
 
 }  // namespace
@@ -1143,43 +1282,28 @@ int gp_batch_observables(gp_batch *b, gp_obs *out, int capacity)
         std::memset(&out[i], 0, sizeof(gp_obs));
         out[i].step = -1;
     }
-    if (b->active.empty()) return GP_OK;
-    const int N = b->args.N;
-    const long long warps = b->obs_lines;
-    const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
-    if (b->prec == GP_C128) k_batch_obs<double><<<blocks, 256, 0, b->stream>>>(b->d_inst, b->d_line_pref, N);
-    else k_batch_obs<float><<<blocks, 256, 0, b->stream>>>(b->d_inst, b->d_line_pref, N);
-    GP_BCK(b, cudaGetLastError());
-    k_batch_obs_finish<<<N, 256, 0, b->stream>>>(b->d_inst, b->d_sums);
-    GP_BCK(b, cudaGetLastError());
-    GP_BCK(b, cudaMemcpyAsync(b->h_sums, b->d_sums, N * gp::kObsWidth * sizeof(double),
-                              cudaMemcpyDeviceToHost, b->stream));
-    rc = batch_sync_errors(b);
-    int bad = 0;
-    for (int a = 0; a < N; ++a) {
-        const int id = b->active[a];
-        if (id >= capacity) continue;
-        const gp_batch_slot &s = b->slots[id];
-        const double *q = b->h_sums + (size_t)a * gp::kObsWidth;
-        const double w = s.h[0] * s.h[1] * (s.grid.nz > 1 ? s.h[2] : 1.0);
-        const double nrm = w * q[0];
-        double kin = 0.5 * (q[6] / (s.h[0] * s.h[0]) + q[7] / (s.h[1] * s.h[1]));
-        if (s.grid.nz > 1) kin += 0.5 * q[8] / (s.h[2] * s.h[2]);
-        gp_obs &o = out[id];
-        o.norm = nrm;
-        o.mu = w * (kin + q[4] + s.g * q[5]) / nrm;
-        o.energy = w * (kin + q[4] + 0.5 * s.g * q[5]) / nrm;
-        o.rms_x = std::sqrt(q[1] / q[0]);
-        o.rms_y = std::sqrt(q[2] / q[0]);
-        o.rms_z = std::sqrt(q[3] / q[0]);
-        o.rms_r = std::sqrt((q[1] + q[2] + q[3]) / q[0]);
-        o.step = s.step;
-        o.t = s.step * s.dt;
-        if (!std::isfinite(o.mu) || !std::isfinite(o.norm)) bad = 1;
-    }
+    const int N = (int)b->active.size();
+    std::vector<int> all(N);
+    for (int a = 0; a < N; ++a) all[a] = a;
+    std::vector<gp_obs> got(N);
+    rc = observe(b, all, got.data());
+    for (int a = 0; a < N; ++a)
+        if (b->active[a] < capacity) out[b->active[a]] = got[a];
+    return rc;
+}
+
+int gp_batch_observables_of(gp_batch *b, const int *slots, int count, gp_obs *out)
+{
+    if (!b || count < 0 || (count > 0 && (!slots || !out)))
+        return bfail(b, GP_EINVAL, "gp_batch_observables_of: null argument or count < 0");
+    for (int i = 0; i < count; ++i)
+        if (!valid_slot(b, slots[i])) return bfail(b, GP_EINVAL, "gp_batch_observables_of: bad slot");
+    int rc = prepare(b);
     if (rc) return rc;
-    if (bad) return bfail(b, GP_ENONFINITE, "gp_batch_observables: non-finite result");
-    return GP_OK;
+    std::vector<int> pos(b->slots.size(), -1), sel(count);
+    for (size_t a = 0; a < b->active.size(); ++a) pos[b->active[a]] = (int)a;
+    for (int i = 0; i < count; ++i) sel[i] = pos[slots[i]];
+    return observe(b, sel, out);
 }
 
 int gp_batch_info(gp_batch *b, int *active, int *slots, size_t *used_bytes)
@@ -1215,12 +1339,13 @@ void gp_batch_destroy(gp_batch *b)
     }
     if (b->d_inst) cudaFreeAsync(b->d_inst, b->stream);
     if (b->d_ints) cudaFreeAsync(b->d_ints, b->stream);
-    if (b->d_line_pref) cudaFreeAsync(b->d_line_pref, b->stream);
+    if (b->d_sub) cudaFreeAsync(b->d_sub, b->stream);
     if (b->d_sums) cudaFreeAsync(b->d_sums, b->stream);
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->d_head) cudaFree(b->d_head);
     if (b->d_err) cudaFree(b->d_err);
     if (b->h_sums) cudaFreeHost(b->h_sums);
+    if (b->h_sub) cudaFreeHost(b->h_sub);
     if (b->h_err) cudaFreeHost(b->h_err);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;

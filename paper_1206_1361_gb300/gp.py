@@ -106,6 +106,7 @@ SIGNATURES = {
     "gp_batch_step": (_int, [_vp, _i64]),
     "gp_batch_set_wait_ns": (_int, [_vp, _i64]),
     "gp_batch_observables": (_int, [_vp, ctypes.POINTER(gp_obs), _int]),
+    "gp_batch_observables_of": (_int, [_vp, ctypes.POINTER(_int), _int, ctypes.POINTER(gp_obs)]),
     "gp_batch_remove": (_int, [_vp, _int]),
     "gp_batch_info": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int),
                              ctypes.POINTER(ctypes.c_size_t)]),
@@ -597,6 +598,15 @@ def gp_batch_observables(b, capacity, slots=None):
     return [arr[i].as_dict() for i in range(capacity)]
 
 
+def gp_batch_observables_of(b, slots):
+    """Dict slot -> observables of the given slots only."""
+    slots = [int(v) for v in slots]
+    ids = (_int * max(1, len(slots)))(*slots)
+    arr = (gp_obs * max(1, len(slots)))()
+    _berr(b, load_library().gp_batch_observables_of(b, ids, len(slots), arr))
+    return {s: arr[i].as_dict() for i, s in enumerate(slots)}
+
+
 def gp_batch_remove(b, slot):
     _berr(b, load_library().gp_batch_remove(b, int(slot)))
 
@@ -643,7 +653,10 @@ class Batch:
         gp_batch_set_wait_ns(self.b, ns)
         return self
 
-    def observables(self):
+    def observables(self, slots=None):
+        """Dict slot -> observables: of every instance, or of `slots` only."""
+        if slots is not None:
+            return gp_batch_observables_of(self.b, slots)
         cap = max(self.shapes) + 1 if self.shapes else 0
         return gp_batch_observables(self.b, cap, list(self.shapes))
 

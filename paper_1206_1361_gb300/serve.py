@@ -201,7 +201,7 @@ class Server:
                    or j.total_steps >= max_steps]
             if not due:
                 continue
-            obs = self.batch.observables()
+            obs = self.batch.observables([j.slot for j in due])
             now = time.perf_counter() - t0
             done = []
             for j in due:

@@ -20,6 +20,15 @@ INSTANCES = [
     ((48, 48, 48), (0.25, 0.25, 0.25), 0.003, (1.0, 1.0, 1.0), 0.0, 0),
     # odd nx: y tiles move point by point, z tiles as 16-byte column pieces
     ((33, 20, 18), (0.3, 0.3, 0.35), 0.004, (1.2, 1.0, 1.4), 6.0, 1),
+    # lines of 96 points or more take the 4-segment solve on 8-line tiles:
+    # kappa_x = 1 (windows wider than a segment, clipped at the line's ends)
+    ((100, 20, 1), (0.05, 0.3, 1.0), 0.01, (1.0, 1.0, 0.0), 5.0, 0),
+    # 96-point y lines with odd nx (point by point), 96-point z lines (column
+    # pieces), x rows of 130 points (pitch 130) and 98-point y lines in real
+    # time
+    ((33, 96, 20), (0.3, 0.1, 0.35), 0.002, (1.2, 1.0, 1.4), 6.0, 1),
+    ((24, 20, 96), (0.3, 0.3, 0.08), 0.003, (1.0, 1.0, 1.5), 4.0, 0),
+    ((130, 98, 1), (0.08, 0.1, 1.0), 5e-4, (1.0, 1.5, 0.0), 20.0, 1),
 ]
 
 
@@ -74,10 +83,11 @@ def test_batch_instances_match_oracle(precision, dtype, tol):
 
 
 @pytest.mark.parametrize("precision", [gp.GP_C128, gp.GP_C64])
-def test_alone_and_in_the_mix_are_identical(precision):
+@pytest.mark.parametrize("which", [2, 3, 9])
+def test_alone_and_in_the_mix_are_identical(precision, which):
     require_gpu()
     dtype = np.complex128 if precision == gp.GP_C128 else np.complex64
-    spec = INSTANCES[2]
+    spec = INSTANCES[which]
     psi0 = rand_state(spec[0], 7).astype(dtype)
     with gp.Batch(precision) as alone:
         s = add(alone, spec, psi0)
@@ -120,9 +130,12 @@ def test_continuous_batching_leaves_running_instances_untouched():
     assert rel_l2(got1, want) <= 1e-12
 
 
-def test_batch_quench_matches_oracle():
+@pytest.mark.parametrize("which", [0, 3])
+def test_batch_quench_matches_oracle(which):
+    """Ground state, then real time from it: the mode switch swaps the
+    tables (and the segment-solve windows) of a running instance."""
     require_gpu()
-    spec = INSTANCES[0]
+    spec = INSTANCES[which]
     with gp.Batch(gp.GP_C128) as b:
         s = add(b, spec, mode=gp.GP_IMAG)
         b.step(30)
@@ -136,6 +149,27 @@ def test_batch_quench_matches_oracle():
     pr = oracle_params(shape, h, dt, w, 6.5, 1)
     oracle.step(pr, want, 20)
     assert rel_l2(got, want) <= 1e-12
+
+
+def test_observables_of_a_subset_equal_the_full_pass():
+    """gp_batch_observables_of: the listed slots only, each identical to its
+    entry of the pass over every instance."""
+    require_gpu()
+    with gp.Batch(gp.GP_C64) as b:
+        slots = [add(b, spec, rand_state(spec[0], 30 + n).astype(np.complex64))
+                 for n, spec in enumerate(INSTANCES)]
+        b.step(4)
+        full = b.observables()
+        pick = [slots[5], slots[0], slots[9]]
+        part = b.observables(pick)
+        assert list(part) == pick
+        for s in pick:
+            assert part[s] == full[s]
+        assert b.observables([]) == {}
+        b.remove(slots[2])
+        with pytest.raises(gp.GPError) as e:
+            b.observables([slots[1], slots[2]])
+        assert e.value.code == gp.GP_EINVAL
 
 
 def test_batch_cap_and_limits():
