@@ -564,25 +564,90 @@ __global__ void k_ff_from_c128(float4 *__restrict__ dst, const double2 *__restri
 
 __global__ void k_ff_set_one(double *x) { *x = 1.0; }
 
+// split(v) -- hi = v rounded to FP32, lo = v - hi (exact in FP64) rounded to
+// FP32 -- from the bits of v with integer and FP32 operations only: the grid
+// conversion streams whole grids, and GB300 runs FP64 arithmetic and FP64
+// conversions on its narrow FP64 pipe.  With v = s m 2^(e-52) (m the 53-bit
+// significand) and -97 <= e <= 126, hi = s r 2^(e-23) for r = m / 2^29
+// rounded to nearest, ties to even, and v - hi = s d 2^(e-52) with the
+// integer d = m - r 2^29, |d| <= 2^28: lo = RN(s d) 2^-52 2^e, whose two
+// power-of-two scalings are exact (a subnormal lo is a multiple of 2^-149,
+// and then |d| < 2^24): bit-identical to split.
+__device__ __forceinline__ float2 split_bits_normal(unsigned long long b, int e)
+{
+    const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;
+    unsigned long long r = m >> 29;
+    const unsigned long long rem = m & 0x1fffffffull;
+    if (rem > 0x10000000ull || (rem == 0x10000000ull && (r & 1ull))) ++r;
+    const int d = (int)((long long)m - (long long)(r << 29));
+    int eh = e;
+    if (r == 0x1000000ull) {        // rounded up to the next power of two
+        r >>= 1;
+        ++eh;
+    }
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const float hi = __uint_as_float(sign | ((unsigned)(eh + 127) << 23) | ((unsigned)r & 0x7fffffu));
+    // (the sign on d: an exact remainder of zero gives lo = +0, as v - hi does)
+    const float lo = __int2float_rn(sign ? -d : d) * 0x1p-52f * __uint_as_float((unsigned)(e + 127) << 23);
+    return f2(hi, lo);
+}
+
+// split(v) for every v: bit-identical for 2^-97 <= |v| < 2^127 (above, where
+// hi may overflow, it calls split).  Below 2^-97 -- far under anything the
+// float-float sweeps resolve next to an O(1) state -- it splits 2^100 v and
+// scales both halves back in FP32, each rounded once more into FP32's
+// subnormal range (within 2^-147 of v), and below 2^-180 it returns zeros
+// carrying the sign of v, as split does.
+__device__ __forceinline__ float2 split_bits(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (e > 126) return split(v);
+    if (e >= -97) return split_bits_normal(b, e);
+    if (e < -180) {
+        const float z = (b >> 63) ? -0.f : 0.f;
+        return f2(z, z);
+    }
+    const float2 t = split_bits_normal(b + (100ull << 52), e + 100);
+    return f2(t.x * 0x1p-100f, t.y * 0x1p-100f);
+}
+
 // complex128 psi of an nx * ny * nz grid into pairs, the Dirichlet nodes
-// (index 0 of each bounded axis) set to zero: blocks walk the x-lines, threads
-// the points of a line.
+// (index 0 of each bounded axis) set to zero: blocks walk groups of kFromLines
+// x-lines, threads the points of a line, each thread's loads of the group's
+// lines issued together.  A line's (j, k) is found once per group (a 64-bit
+// division per point, with one load in flight per thread, held this pass to
+// 2 TB/s).
+constexpr int kFromLines = 4;
 __global__ void k_ff_from_c128_grid(float4 *__restrict__ dst, const double2 *__restrict__ src, int nx,
                                     int ny, int nz)
 {
-    const long long lines = (long long)ny * nz;
-    for (long long line = blockIdx.x; line < lines; line += gridDim.x) {
-        const int j = (int)(line % ny), k = (int)(line / ny);
-        const bool edge = j == 0 || (nz > 1 && k == 0);
-        const double2 *row = src + line * nx;
-        float4 *out = dst + line * nx;
+    const int lines = ny * nz;             // <= 8192^2
+    for (int l0 = blockIdx.x * kFromLines; l0 < lines; l0 += gridDim.x * kFromLines) {
+        bool keep[kFromLines];             // line inside the grid and off the Dirichlet planes
+        int j = l0 % ny, k = l0 / ny;
+#pragma unroll
+        for (int u = 0; u < kFromLines; ++u) {
+            keep[u] = l0 + u < lines && j > 0 && (nz == 1 || k > 0);
+            if (++j == ny) {
+                j = 0;
+                ++k;
+            }
+        }
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            if (edge || i == 0) {
-                out[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            } else {
-                const double2 v = row[i];
-                const float2 r = split(v.x), im = split(v.y);
-                out[i] = make_float4(r.x, im.x, r.y, im.y);
+            double2 v[kFromLines];
+#pragma unroll
+            for (int u = 0; u < kFromLines; ++u)
+                v[u] = l0 + u < lines ? src[(long long)(l0 + u) * nx + i] : make_double2(0.0, 0.0);
+#pragma unroll
+            for (int u = 0; u < kFromLines; ++u) {
+                if (l0 + u >= lines) break;
+                float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i > 0 && keep[u]) {
+                    const float2 r = split_bits(v[u].x), im = split_bits(v[u].y);
+                    o = make_float4(r.x, im.x, r.y, im.y);
+                }
+                dst[(long long)(l0 + u) * nx + i] = o;
             }
         }
     }
@@ -858,8 +923,8 @@ cudaError_t launch_ff_from_c128(void *dst, const void *src, long long count, con
 cudaError_t launch_ff_from_c128_grid(void *dst, const void *src, int nx, int ny, int nz,
                                      cudaStream_t st)
 {
-    const long long lines = (long long)ny * nz;
-    const int blocks = (int)(lines < 152 * 16 ? lines : 152 * 16);
+    const int groups = (ny * nz + kFromLines - 1) / kFromLines;
+    const int blocks = groups < 152 * 16 ? groups : 152 * 16;
     k_ff_from_c128_grid<<<blocks, 256, 0, st>>>((float4 *)dst, (const double2 *)src, nx, ny, nz);
     return cudaGetLastError();
 }

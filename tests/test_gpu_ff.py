@@ -153,26 +153,77 @@ def test_ff_store_load_roundtrip_and_device_view():
         assert s.observables()["step"] == 7
 
 
-def test_ff_load_from_a_device_buffer_zeroes_the_dirichlet_nodes():
+@pytest.mark.parametrize("shape", [(37, 20, 9), (37, 21, 9), (31, 23, 1)])
+def test_ff_load_from_a_device_buffer_zeroes_the_dirichlet_nodes(shape):
     """gp_load from a caller's device buffer splits it in place (the buffer is
     only read): the Dirichlet nodes come out zero, every other point within
-    2^-47 of its complex128 value, and the caller's buffer is unchanged."""
+    2^-47 of its complex128 value, and the caller's buffer is unchanged (line
+    counts that fill the conversion's 4-line groups, a ragged last group, 2D)."""
     require_gpu()
     import torch
-    shape, h = (37, 20, 9), (0.4, 0.4, 0.4)
+    nx, ny, nz = shape
+    h = (0.4, 0.4, 0.4 if nz > 1 else 1.0)
+    w = W3 if nz > 1 else (W3[0], W3[1], 0.0)
     rng = np.random.default_rng(12)
-    a = rng.standard_normal((9, 20, 37)) + 1j * rng.standard_normal((9, 20, 37))
+    a = rng.standard_normal((nz, ny, nx)) + 1j * rng.standard_normal((nz, ny, nx))
     dev = torch.from_numpy(a.copy()).cuda()
-    with gp.Solver(shape, h, 0.01, *W3, 1.0, gp.GP_REAL, gp.GP_CFF) as s:
+    with gp.Solver(shape, h, 0.01, *w, 1.0, gp.GP_REAL, gp.GP_CFF) as s:
         s.load(dev)
         back = s.psi()
         assert np.array_equal(dev.cpu().numpy(), a)
     want = a.copy()
     want[:, :, 0] = 0
     want[:, 0, :] = 0
-    want[0] = 0
+    if nz > 1:
+        want[0] = 0
     assert np.max(np.abs(back - want)) <= 2.0 ** -47 * np.max(np.abs(a))
-    assert not back[:, :, 0].any() and not back[:, 0, :].any() and not back[0].any()
+    assert not back[:, :, 0].any() and not back[:, 0, :].any()
+    if nz > 1:
+        assert not back[0].any()
+
+
+def test_ff_load_split_is_bit_exact():
+    """The split of a complex128 input into float-float pairs (integer
+    arithmetic on the bits): for 2^-97 <= |v| hi is the FP32 rounding of each
+    component and lo the FP32 rounding of the exact remainder, bit for bit as
+    numpy computes them -- over magnitudes up to 1e30, ties to even, values
+    that round up to the next power of two and exact FP32 values; smaller
+    values (down to 1e-300, and zeros) come within 2^-146 of v."""
+    require_gpu()
+    import torch
+    shape, h = (33, 18, 10), (0.4, 0.4, 0.4)
+    rng = np.random.default_rng(21)
+    n = 10 * 18 * 33
+    mag = 10.0 ** rng.uniform(-40, 30, 2 * n)
+    v = rng.choice([-1.0, 1.0], 2 * n) * mag
+    special = []
+    for e in (-97, -96, -60, -1, 0, 1, 40, 99):
+        b = 2.0 ** e
+        special += [b, -b, b * (1 + 2.0 ** -24), b * (1 + 3 * 2.0 ** -24), b * (2 - 2.0 ** -53),
+                    b * (1 + 2.0 ** -24 + 2.0 ** -52), -b * (1.5 + 2.0 ** -25), b * (1.75 - 2.0 ** -30)]
+    special += [0.0, -0.0, 1e-300, -3e-39]
+    a = (v[0::2] + 1j * v[1::2]).reshape(10, 18, 33)
+    sp = np.array(special)
+    for t in range(0, len(sp), 32):               # interior points (x, y, z >= 1)
+        part = sp[t:t + 32]
+        a.real[5, 7 + t // 32, 1:1 + len(part)] = part
+        a.imag[6, 7 + t // 32, 1:1 + len(part)] = part
+    a[:, :, 0] = 0
+    a[:, 0, :] = 0
+    a[0] = 0
+    with gp.Solver(shape, h, 0.01, *W3, 1.0, gp.GP_REAL, gp.GP_CFF) as s:
+        s.load(torch.from_numpy(a.copy()).cuda())
+        view = s.device_view().cpu().numpy()
+    assert (np.abs(a) < 2.0 ** -97).any() and (np.abs(a) >= 2.0 ** -97).any()
+    for k, comp in ((0, a.real), (1, a.imag)):
+        with np.errstate(under="ignore"):
+            hi = comp.astype(np.float32)
+            lo = (comp - hi.astype(np.float64)).astype(np.float32)
+        big = np.abs(comp) >= 2.0 ** -97
+        assert np.array_equal(view[..., k].view(np.uint32)[big], hi.view(np.uint32)[big])
+        assert np.array_equal(view[..., k + 2].view(np.uint32)[big], lo.view(np.uint32)[big])
+        got = view[..., k].astype(np.float64) + view[..., k + 2].astype(np.float64)
+        assert np.max(np.abs(got - comp)[~big]) <= 2.0 ** -146
 
 
 def test_ff_rejections():
