@@ -142,7 +142,10 @@ k_sweep_rho(double2 *__restrict__ psi, double2 *__restrict__ work, const RadialT
 }
 
 // calcnu of every point into pbuf (the radial windows overlap, so the
-// pointwise step is taken once per point before them).
+// pointwise step is taken once per point before them).  Blocks walk the
+// radial lines (z index k), threads the points of a line: the line's factor
+// P_z[k] and coefficients are set up once per line, not per point (FP64 work
+// on GB300's narrow FP64 pipe, as was a 64-bit division per point).
 template <int MODE>
 __global__ void __launch_bounds__(256)
 k_calcnu_axial(const double2 *__restrict__ in, double2 *__restrict__ pbuf, int nr, int nz,
@@ -150,13 +153,12 @@ k_calcnu_axial(const double2 *__restrict__ in, double2 *__restrict__ pbuf, int n
                const double2 *__restrict__ one, StepG sg, const double *__restrict__ scale)
 {
     const double G = sg.value();
-    const long long count = (long long)nr * nz;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(p % nr), k = (int)(p / nr);
+    for (int k = blockIdx.x; k < nz; k += gridDim.x) {
         Calcnu<double, MODE> nl{};
         nl.setup(pr, pz, one, nullptr, nullptr, nullptr, k, 0, G, scale);
-        pbuf[p] = nl.apply(in[p], i);
+        const double2 *row = in + (long long)k * nr;
+        double2 *out = pbuf + (long long)k * nr;
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) out[i] = nl.apply(row[i], i);
     }
 }
 
@@ -458,11 +460,10 @@ cudaError_t launch_sweep_rho_win(int mode, const void *in, void *out, void *pbuf
                                  const SegWindow &sw, int nr, int nz, const NonlinArgs &nl,
                                  cudaStream_t st)
 {
-    long long pb = ((long long)nr * nz + 255) / 256;
-    if (pb > 4 * kReduceBlocks) pb = 4 * kReduceBlocks;
+    const int pb = nz < 16 * 152 ? nz : 16 * 152;    // one radial line per block at a time
     auto kc = mode == 0 ? k_calcnu_axial<0> : k_calcnu_axial<1>;
-    kc<<<(int)pb, 256, 0, st>>>((const double2 *)in, (double2 *)pbuf, nr, nz, nl.px, nl.py, nl.pz,
-                                nl.g, nl.scale);
+    kc<<<pb, 256, 0, st>>>((const double2 *)in, (double2 *)pbuf, nr, nz, nl.px, nl.py, nl.pz, nl.g,
+                           nl.scale);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const long long threads = (long long)sw.nseg_r * nz;
